@@ -1,0 +1,171 @@
+/*
+ * enuf.h -- C ABI of the ENUF library: Ewald summation with the
+ * reciprocal-space sum evaluated by non-uniform FFTs, on one NVIDIA B300.
+ *
+ * Method: Yang, Li, Zhu, Laaksonen, Wang, "The ENUF method -- Ewald summation
+ * based on non-uniform fast Fourier transform: implementation,
+ * parallelization, and application" (arXiv:2004.12484).
+ *
+ * Problem statement (Sec. 2.1): N point charges q_j at positions r_j in a
+ * periodic orthorhombic box L_x x L_y x L_z.  The library returns the total
+ * electrostatic energy
+ *     E = E_real (Eq. 17) + E_recip (Eq. 22 / 38) + E_self (Eq. 24)
+ *         [+ E_background = -k pi Q^2 / (2 V alpha^2) when Q = sum q != 0],
+ * the forces F_i = -dE/dr_i (real part Eq. 29 in textbook form, reciprocal
+ * part Eq. 41-42), optionally the potentials phi_i = dE/dq_i (Eq. 5) and the
+ * virial W_ab = -dE/d eps_ab.  The reciprocal part follows Sec. 3.1:
+ * spread (Gaussian window) -> 3D FFT -> scale -> energy (Eq. 38); subdivide ->
+ * inverse FFT (the three force components packed in one pass) -> interpolate.
+ *
+ * Conventions
+ *   - Every array argument of the compute calls is a DEVICE pointer unless
+ *     its name ends in _host.  Positions are N x 3 row-major (x, y, z per
+ *     particle), charges N, forces N x 3, potentials N.  Element type is
+ *     float for ENUF_MIXED plans and double for ENUF_FP64 plans.
+ *   - Positions may lie anywhere; they are wrapped into the box.
+ *   - Energies and the virial are always double.
+ *   - The caller owns every input and output buffer.  A plan owns its device
+ *     workspace (or borrows one given with enuf_plan_set_workspace) and a
+ *     private CUDA stream used only to capture CUDA graphs.
+ *   - Calls are ordered on the stream given at plan creation (or
+ *     enuf_plan_set_stream); asynchronous calls return before the work ends.
+ *   - Return value: 0 on success, a negative ENUF_E* code on failure; the
+ *     message of the last failure on the calling thread is returned by
+ *     enuf_last_error().  Outputs are undefined after a failure.
+ *   - A plan is not thread safe: one host thread at a time per plan.
+ */
+#ifndef ENUF_H
+#define ENUF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* precision */
+#define ENUF_FP64 0   /* every step in IEEE double                                  */
+#define ENUF_MIXED 1  /* spread, FFT, interpolate, real-space pairs in float;       */
+                      /* energy/virial reductions, self, background terms in double */
+
+/* flags (per call; OR-ed) */
+#define ENUF_WANT_VIRIAL 1       /* fill the 3x3 virial                              */
+#define ENUF_WANT_PHI 2          /* fill phi_i = dE/dq_i (a 4th inverse transform)    */
+#define ENUF_REMOVE_NET_FORCE 4  /* subtract (1/N) sum_i F_i from every force         */
+#define ENUF_KSPACE_ONLY 8       /* reciprocal part only (no real-space, self, bg)    */
+
+/* error codes */
+#define ENUF_OK 0
+#define ENUF_EINVAL -1       /* invalid argument                                */
+#define ENUF_EUNSUPPORTED -2 /* size or option outside what the plan supports   */
+#define ENUF_ENOMEM -3       /* device allocation failed                        */
+#define ENUF_ECUDA -4        /* a CUDA call failed                              */
+#define ENUF_ENONFINITE -5   /* a position or charge was NaN or infinite        */
+#define ENUF_EDEVICE -6      /* a kernel reported an internal error             */
+
+/* Layout of the results vector (ENUF_NOUT doubles) written by enuf_compute. */
+#define ENUF_OUT_E 0         /* total energy                      */
+#define ENUF_OUT_E_REAL 1    /* Eq. 17                            */
+#define ENUF_OUT_E_RECIP 2   /* Eq. 38                            */
+#define ENUF_OUT_E_SELF 3    /* Eq. 24                            */
+#define ENUF_OUT_E_BG 4      /* neutralising background           */
+#define ENUF_OUT_Q 5         /* net charge sum_i q_i              */
+#define ENUF_OUT_VIRIAL 6    /* 9 entries, row-major W_ab         */
+#define ENUF_OUT_STATUS 15   /* 0 ok, else the kernels' status bits (as a double) */
+#define ENUF_NOUT 16
+
+typedef struct enuf_params {
+    double L[3];       /* box edges (> 0)                                        */
+    int64_t N;         /* number of particles, 1 <= N < 2^31                     */
+    double alpha;      /* Ewald splitting parameter alpha = 1/(sqrt(2) sigma)    */
+    double r_c;        /* real-space cutoff, 0 < r_c <= min(L)/2                 */
+    int M;             /* FFT grid edge, a power of two in [8, 512]              */
+    int p;             /* window support points per dimension, even, 2..12, <= M */
+    int n_c;           /* reciprocal cutoff |n_t| <= n_c; 0 selects M/4;         */
+                       /* must satisfy 1 <= n_c < M/2                            */
+    int precision;     /* ENUF_FP64 or ENUF_MIXED                                */
+    double coulomb_k;  /* 1/(4 pi eps0) in the caller's units; 0 selects 1.0     */
+    int flags;         /* reserved, must be 0                                    */
+} enuf_params;
+
+typedef struct enuf_plan enuf_plan;
+
+/* Device bytes the plan's workspace needs (lets the caller's allocator own
+ * the memory; see enuf_plan_set_workspace).  Validates the parameters. */
+int enuf_plan_workspace_bytes(const enuf_params* params, size_t* bytes);
+
+/* Creates a plan.  `cuda_stream` is a cudaStream_t (NULL = legacy default
+ * stream).  If `allocate` is nonzero the plan allocates its workspace with
+ * cudaMalloc; otherwise enuf_plan_set_workspace must be called before the
+ * first compute call.  Window constants, twiddle tables and reciprocal
+ * tables are computed here in double on the host and copied to the device
+ * (this call synchronises the stream). */
+int enuf_plan_create(const enuf_params* params, void* cuda_stream, int allocate, enuf_plan** out);
+
+/* Gives the plan a caller-owned device workspace of at least
+ * enuf_plan_workspace_bytes() bytes, 256-byte aligned.  The plan does not
+ * free it.  Drops captured graphs. */
+int enuf_plan_set_workspace(enuf_plan* plan, void* dev_ptr, size_t bytes);
+
+/* Changes the stream later calls are ordered on. */
+int enuf_plan_set_stream(enuf_plan* plan, void* cuda_stream);
+
+/* Reads back the parameters the plan resolved (n_c, coulomb_k defaults). */
+int enuf_plan_get_params(const enuf_plan* plan, enuf_params* out);
+
+/* Frees the plan, its own workspace and its graphs.  NULL is accepted. */
+int enuf_plan_destroy(enuf_plan* plan);
+
+/* Asynchronous evaluation on the plan's stream; every step of the method
+ * runs in the library's kernels.  pos, q: inputs (device).  F: N x 3 output
+ * (device; NULL gives the energy only).  phi: N output (device; required when
+ * ENUF_WANT_PHI is set, else ignored).  out: ENUF_NOUT doubles (device, may
+ * be NULL).  With ENUF_KSPACE_ONLY, F and phi hold the reciprocal parts only
+ * and out[ENUF_OUT_E] is E_recip.  The work is replayed from a CUDA graph
+ * captured on the first call with the same pointers and flags (set the
+ * environment variable ENUF_NO_GRAPH=1 before plan creation to launch the
+ * kernels directly).  Non-finite inputs and internal errors are reported in
+ * out[ENUF_OUT_STATUS] and by the synchronous wrappers. */
+int enuf_compute(enuf_plan* plan, const void* pos, const void* q, void* F, void* phi, double* out, int flags);
+
+/* Synchronous wrapper of enuf_compute: device inputs/outputs, energy parts
+ * returned to host memory (E_host: 1 double or NULL; virial_host: 9 doubles
+ * or NULL; parts_host: ENUF_NOUT doubles or NULL).  Synchronises the plan's
+ * stream and checks the status word (ENUF_ENONFINITE / ENUF_EDEVICE). */
+int enuf_energy_forces(enuf_plan* plan, const void* pos, const void* q, double* E_host, void* F,
+                       double* virial_host, void* phi, double* parts_host, int flags);
+
+/* End-to-end call with HOST buffers: copies pos_host and q_host (N x 3 and N
+ * elements of the plan's type, ideally page-locked) to plan-owned device
+ * buffers, computes, and copies F (and phi when ENUF_WANT_PHI is set) back
+ * into F_host / phi_host.  Synchronises. */
+int enuf_energy_forces_host(enuf_plan* plan, const void* pos_host, const void* q_host, double* E_host,
+                            void* F_host, double* virial_host, void* phi_host, int flags);
+
+/* Backward pass of E with respect to the inputs (Eq. 27 and Eq. 5):
+ * dpos = gE * (-F), dq = gE * phi, where gE points to one double on the
+ * device (NULL means 1).  Recomputes the grids instead of reading stored
+ * state.  dpos: N x 3, dq: N (device; either may be NULL).  Asynchronous. */
+int enuf_backward(enuf_plan* plan, const void* pos, const void* q, const double* gE, void* dpos, void* dq);
+
+/* Per-kernel device times (milliseconds) of the last enuf_compute, measured
+ * with CUDA events when ENUF_PROFILE=1 was set at plan creation (graphs are
+ * then not used).  Fills up to `cap` entries; returns the count. */
+int enuf_last_timings(enuf_plan* plan, const char** names, float* times_ms, int cap);
+
+/* Number of kernel launches one enuf_compute call with `flags` performs
+ * (memset nodes not counted). */
+int enuf_launch_count(enuf_plan* plan, int flags, int with_forces);
+
+/* Thread-local description of the last failure ("" if none). */
+const char* enuf_last_error(void);
+
+/* Library version string. */
+const char* enuf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ENUF_H */

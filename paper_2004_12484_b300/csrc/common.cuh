@@ -1,0 +1,69 @@
+// common.cuh -- small device types and helpers shared by the ENUF kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace enuf {
+
+// complex value types
+template <typename R> struct Cpx;
+template <> struct Cpx<float> { using T = float2; };
+template <> struct Cpx<double> { using T = double2; };
+
+// sorted particle record: offset inside its bin (x, y, z) and charge
+struct __align__(16) f4 { float x, y, z, w; };
+struct __align__(32) d4 { double x, y, z, w; };
+template <typename R> struct Rec;
+template <> struct Rec<float> { using T = f4; };
+template <> struct Rec<double> { using T = d4; };
+
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return V{a.x + b.x, a.y + b.y}; }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return V{a.x - b.x, a.y - b.y}; }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b)
+{
+    return V{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename V> __device__ __forceinline__ V cconj(V a) { return V{a.x, -a.y}; }
+
+__device__ __forceinline__ float dexp(float x) { return expf(x); }
+__device__ __forceinline__ double dexp(double x) { return exp(x); }
+__device__ __forceinline__ float derfc(float x) { return erfcf(x); }
+__device__ __forceinline__ double derfc(double x) { return erfc(x); }
+__device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
+
+template <typename R> __device__ __forceinline__ R warp_sum(R v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Status bits written by kernels into the workspace status word.
+enum : int {
+    ST_NONFINITE = 1,  // a non-finite position or charge was seen
+    ST_WORKLIST = 2,   // the bin work list overflowed its bound (internal error)
+};
+
+// Block reduction of NV values per thread.  Each warp sums in type R, the
+// warp totals are added in double; threads 0..NV-1 write out[0..NV).
+// Must be called by every thread of the block.
+template <typename R, int NV>
+__device__ __forceinline__ void block_reduce_to_double(R (&v)[NV], double* out, double* smem /* 32*NV */)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        R s = warp_sum(v[k]);
+        if (lane == 0) smem[warp * NV + k] = (double)s;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double t = 0.0;
+        for (int w = 0; w < nw; w++) t += smem[w * NV + threadIdx.x];
+        out[threadIdx.x] = t;
+    }
+    __syncthreads();
+}
+
+}  // namespace enuf
