@@ -1,0 +1,846 @@
+// enuf.cu -- host side of the ENUF library: parameter checks, workspace
+// layout, window / twiddle / reciprocal tables, the launch sequence of one
+// evaluation, CUDA-graph replay, and the C ABI declared in include/enuf.h.
+//
+// One evaluation (Sec. 3.1-3.2 of the paper, everything on the device):
+//   bin keys -> scan -> scatter        counting sort into grid tiles (a1, a2)
+//   spread                             window spreading (a3)
+//   fx, fy, fz                         forward FFT; fz fuses scaling, the
+//                                      energy/virial (Eq. 38) and subdividing
+//   iy, ix                             inverse FFT of 3 or 4 fields packed
+//                                      into one pass (a6)
+//   gather                             interpolation, F = q E (a7)
+//   real-space sort + pair kernel      erfc sum (a8)
+//   finalize                           FP64 assembly of E and the virial (a9)
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/enuf.h"
+#include "common.cuh"
+#include "fft.cuh"
+#include "realspace.cuh"
+#include "sort.cuh"
+#include "spread_gather.cuh"
+
+using namespace enuf;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg)
+{
+    g_err = msg;
+    return code;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(ENUF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));      \
+    } while (0)
+
+constexpr int kWorkCap = 512;  // particles per work item of spread / gather
+constexpr int kMaxSmem = 227 * 1024;
+constexpr double kPi = 3.14159265358979323846;
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+struct Resolved {
+    enuf_params prm;
+    bool fp64;
+    size_t rsz;    // sizeof(real)
+    int nc, Kx, Kb, P;
+    int T, nbt[3], nbins, max_work;
+    bool cells;    // linked cells (else all pairs)
+    int ncell[3], nrbins;
+    double h[3];
+    FftGeom gfx, gy, gz;
+};
+
+int ffthreads(int n) { return n >= 8 ? n / 8 : 1; }
+
+int resolve(const enuf_params* in, Resolved& r)
+{
+    if (!in) return fail(ENUF_EINVAL, "params is NULL");
+    r.prm = *in;
+    enuf_params& p = r.prm;
+    for (int t = 0; t < 3; t++)
+        if (!(p.L[t] > 0.0) || !std::isfinite(p.L[t])) return fail(ENUF_EINVAL, "box edges must be positive");
+    if (p.N < 1 || p.N >= (int64_t(1) << 31)) return fail(ENUF_EINVAL, "N must be in [1, 2^31)");
+    if (!(p.alpha > 0.0)) return fail(ENUF_EINVAL, "alpha must be positive");
+    if (!is_pow2(p.M) || p.M < 8 || p.M > 512) return fail(ENUF_EUNSUPPORTED, "M must be a power of two in [8, 512]");
+    if (p.p < 2 || p.p > 12 || (p.p & 1) || p.p > p.M) return fail(ENUF_EUNSUPPORTED, "p must be even, 2..12, <= M");
+    if (p.n_c == 0) p.n_c = p.M / 4;
+    if (p.n_c < 1 || 2 * p.n_c >= p.M) return fail(ENUF_EINVAL, "n_c must satisfy 1 <= n_c < M/2");
+    if (p.precision != ENUF_FP64 && p.precision != ENUF_MIXED) return fail(ENUF_EINVAL, "unknown precision");
+    if (p.coulomb_k == 0.0) p.coulomb_k = 1.0;
+    if (p.flags != 0) return fail(ENUF_EINVAL, "params.flags is reserved and must be 0");
+    const double Lmin = std::min(p.L[0], std::min(p.L[1], p.L[2]));
+    if (!(p.r_c > 0.0) || p.r_c > 0.5 * Lmin) return fail(ENUF_EINVAL, "r_c must satisfy 0 < r_c <= min(L)/2");
+
+    r.fp64 = p.precision == ENUF_FP64;
+    r.rsz = r.fp64 ? 8 : 4;
+    r.nc = p.n_c;
+    r.Kx = r.nc + 1;
+    r.Kb = 2 * r.nc + 1;
+    r.P = r.Kb * r.Kx;
+    // tile edge: 16 where the gather's shared-memory box of 4 fields fits
+    const int pt16 = 16 + p.p - 1;
+    r.T = (!r.fp64 && p.M >= 256 && 4ull * pt16 * pt16 * pt16 * 4 <= (size_t)kMaxSmem) ? 16 : 8;
+    for (int t = 0; t < 3; t++) r.nbt[t] = p.M / r.T;
+    r.nbins = r.nbt[0] * r.nbt[1] * r.nbt[2];
+    r.max_work = r.nbins + (int)(p.N / kWorkCap) + 1;
+    // linked cells of edge >= r_c, at least 3 per dimension
+    r.cells = true;
+    for (int t = 0; t < 3; t++) {
+        r.ncell[t] = (int)std::floor(p.L[t] / p.r_c);
+        if (r.ncell[t] > 256) r.ncell[t] = 256;
+        if (r.ncell[t] < 3) r.cells = false;
+    }
+    if (!r.cells) r.ncell[0] = r.ncell[1] = r.ncell[2] = 1;
+    for (int t = 0; t < 3; t++) r.h[t] = p.L[t] / r.ncell[t];
+    r.nrbins = r.ncell[0] * r.ncell[1] * r.ncell[2];
+
+    const size_t vsz = 2 * r.rsz;
+    const int M = p.M;
+    // k_fx / k_ix rows per block
+    r.gfx = FftGeom{r.nc, r.Kx, r.Kb, r.P, 0, 256 / ffthreads(M / 2)};
+    const int NT = ffthreads(M), gran = std::max(1, 32 / NT);
+    auto round_up = [](int v, int g) { return (v + g - 1) / g * g; };
+    // k_fy / k_iy: columns per block, about 16 but balanced over Kx
+    {
+        int nch = (r.Kx + 15) / 16;
+        int W = round_up((r.Kx + nch - 1) / nch, gran);
+        while (W * NT > 1024) W -= gran;
+        while ((size_t)W * (M + 1) * vsz > (size_t)kMaxSmem) W -= gran;
+        r.gy = FftGeom{r.nc, r.Kx, r.Kb, r.P, W, 0};
+    }
+    // k_fz: pencils per block
+    {
+        int W = round_up(16, gran);
+        while (W * NT > 1024) W -= gran;
+        while ((size_t)2 * W * (M + 1) * vsz + 32 * 7 * 8 > (size_t)kMaxSmem) W -= gran;
+        r.gz = FftGeom{r.nc, r.Kx, r.Kb, r.P, W, 0};
+    }
+    if (r.gy.W < 1 || r.gz.W < 1) return fail(ENUF_EUNSUPPORTED, "FFT block shape does not fit");
+    return ENUF_OK;
+}
+
+// ------------------------------------------------------------------ workspace
+struct Layout {
+    size_t status, out, mean;
+    size_t counts, offsets, work, nwork;
+    size_t key, rank, rec_tmp, rec, perm;
+    size_t rcounts, roffsets, rrec, rperm, rcell;
+    size_t qpart, kpart, rpart, fpart;
+    size_t twid, tk, te, td;
+    size_t grid, C1, C2, C3, C4, fld;
+    size_t s_pos, s_q, s_F, s_phi;
+    size_t total;
+};
+
+Layout layout(const Resolved& r)
+{
+    Layout L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align256(o + std::max<size_t>(bytes, 1));
+        return at;
+    };
+    const size_t N = (size_t)r.prm.N, M = (size_t)r.prm.M, rs = r.rsz, vs = 2 * r.rsz;
+    const size_t recsz = r.fp64 ? sizeof(d4) : sizeof(f4);
+    const size_t nblkN = (N + 255) / 256;
+    const size_t nblkZ = ((size_t)r.P + r.gz.W - 1) / r.gz.W;
+    L.status = take(16);
+    L.out = take(ENUF_NOUT * 8);
+    L.mean = take(4 * 8);
+    L.counts = take((r.nbins + 1) * 4);
+    L.offsets = take((r.nbins + 1) * 4);
+    L.work = take((size_t)r.max_work * 16);
+    L.nwork = take(4);
+    L.key = take(N * 4);
+    L.rank = take(N * 4);
+    L.rec_tmp = take(N * recsz);
+    L.rec = take(N * recsz);
+    L.perm = take(N * 4);
+    L.rcounts = take((r.nrbins + 1) * 4);
+    L.roffsets = take((r.nrbins + 1) * 4);
+    L.rrec = take(N * recsz);
+    L.rperm = take(N * 4);
+    L.rcell = take(N * 4);
+    L.qpart = take(nblkN * 2 * 8);
+    L.kpart = take(nblkZ * 8 * 8);
+    L.rpart = take(nblkN * 8 * 8);
+    L.fpart = take(nblkN * 4 * 8);
+    L.twid = take(M * vs);
+    L.tk = take(3 * r.Kb * rs);
+    L.te = take(3 * r.Kb * rs);
+    L.td = take(3 * r.Kb * rs);
+    L.grid = take(M * M * M * rs);
+    L.C1 = take(M * M * r.Kx * vs);
+    L.C2 = take(M * (size_t)r.P * vs);
+    L.C3 = take(4 * M * (size_t)r.P * vs);
+    L.C4 = take(4 * M * M * r.Kx * vs);
+    L.fld = take(4 * M * M * M * rs);
+    L.s_pos = take(3 * N * rs);
+    L.s_q = take(N * rs);
+    L.s_F = take(3 * N * rs);
+    L.s_phi = take(N * rs);
+    L.total = o;
+    return L;
+}
+
+struct GraphEntry {
+    const void *pos, *q;
+    void *F, *phi;
+    double* out;
+    int flags;
+    cudaGraphExec_t exec;
+    unsigned long long stamp;
+};
+
+}  // namespace
+
+struct enuf_plan {
+    Resolved r;
+    Layout lay;
+    char* ws = nullptr;
+    bool own_ws = false;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    bool use_graph = true;
+    bool profile = false;
+    bool attrs_done = false;
+    std::vector<GraphEntry> graphs;
+    unsigned long long stamp = 0;
+    // derived constants
+    double b = 0, inv_b = 0, cnorm3 = 0;
+    // profiling
+    std::vector<std::string> tnames;
+    std::vector<cudaEvent_t> tevents;
+    std::vector<float> ttimes;
+    int nrec = 0;
+};
+
+namespace {
+
+template <typename T> T* at(enuf_plan* pl, size_t off) { return reinterpret_cast<T*>(pl->ws + off); }
+
+// ------------------------------------------------------------------ launching
+struct Launcher {
+    enuf_plan* pl;
+    cudaStream_t st;
+    bool attr_only;
+    int count = 0;
+
+    template <typename... KArgs, typename... Args>
+    int go(const char* name, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, Args... args)
+    {
+        if (smem > 48 * 1024 && attr_only) {
+            cudaError_t e = cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return fail(ENUF_ECUDA, std::string("cudaFuncSetAttribute(") + name + "): " + cudaGetErrorString(e));
+        }
+        if (attr_only) { count++; return ENUF_OK; }
+        if (pl->profile) {
+            cudaEvent_t e0;
+            cudaEventCreate(&e0);
+            cudaEventRecord(e0, st);
+            pl->tevents.push_back(e0);
+            pl->tnames.push_back(name);
+        }
+        k<<<grid, block, smem, st>>>(args...);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(ENUF_ECUDA, std::string("launch ") + name + ": " + cudaGetErrorString(e));
+        count++;
+        return ENUF_OK;
+    }
+    int memset(void* p, size_t bytes)
+    {
+        if (attr_only) return ENUF_OK;
+        CK(cudaMemsetAsync(p, 0, bytes, st));
+        return ENUF_OK;
+    }
+};
+
+#define LCHK(x)                      \
+    do {                             \
+        int rc_ = (x);               \
+        if (rc_ != ENUF_OK) return rc_; \
+    } while (0)
+
+template <typename R, int P, int T>
+int launch_spread_t(Launcher& L, enuf_plan* pl)
+{
+    const Resolved& r = pl->r;
+    const Layout& y = pl->lay;
+    constexpr int PT = T + P - 1;
+    return L.go("spread", k_spread<R, P, T>, dim3(r.max_work), dim3(256), (size_t)PT * PT * PT * sizeof(R),
+                at<const int4>(pl, y.work), at<const int>(pl, y.nwork), at<const typename Rec<R>::T>(pl, y.rec),
+                r.prm.M, r.nbt[0], r.nbt[1], (R)pl->inv_b, (R)pl->cnorm3, at<R>(pl, y.grid));
+}
+
+template <typename R, int P, int T>
+int launch_gather_t(Launcher& L, enuf_plan* pl, int nf, R* F, R* phi)
+{
+    const Resolved& r = pl->r;
+    const Layout& y = pl->lay;
+    constexpr int PT = T + P - 1;
+    const size_t smem = (size_t)nf * PT * PT * PT * sizeof(R);
+    if (nf == 4)
+        return L.go("gather", k_gather<R, P, T, 4>, dim3(r.max_work), dim3(256), smem, at<const int4>(pl, y.work),
+                    at<const int>(pl, y.nwork), at<const typename Rec<R>::T>(pl, y.rec), at<const uint32_t>(pl, y.perm),
+                    r.prm.M, r.nbt[0], r.nbt[1], (R)pl->inv_b, (R)pl->cnorm3, at<const R>(pl, y.fld), F, phi);
+    return L.go("gather", k_gather<R, P, T, 3>, dim3(r.max_work), dim3(256), smem, at<const int4>(pl, y.work),
+                at<const int>(pl, y.nwork), at<const typename Rec<R>::T>(pl, y.rec), at<const uint32_t>(pl, y.perm),
+                r.prm.M, r.nbt[0], r.nbt[1], (R)pl->inv_b, (R)pl->cnorm3, at<const R>(pl, y.fld), F, phi);
+}
+
+#define DISPATCH_P(T_, FN, ...)                                           \
+    switch (pl->r.prm.p) {                                                \
+    case 2: return FN<R, 2, T_>(__VA_ARGS__);                             \
+    case 4: return FN<R, 4, T_>(__VA_ARGS__);                             \
+    case 6: return FN<R, 6, T_>(__VA_ARGS__);                             \
+    case 8: return FN<R, 8, T_>(__VA_ARGS__);                             \
+    case 10: return FN<R, 10, T_>(__VA_ARGS__);                           \
+    case 12: return FN<R, 12, T_>(__VA_ARGS__);                           \
+    default: return fail(ENUF_EUNSUPPORTED, "unsupported p");             \
+    }
+
+template <typename R> int launch_spread(Launcher& L, enuf_plan* pl)
+{
+    if (pl->r.T == 16) { DISPATCH_P(16, launch_spread_t, L, pl) }
+    DISPATCH_P(8, launch_spread_t, L, pl)
+}
+
+template <typename R> int launch_gather(Launcher& L, enuf_plan* pl, int nf, R* F, R* phi)
+{
+    if (pl->r.T == 16) { DISPATCH_P(16, launch_gather_t, L, pl, nf, F, phi) }
+    DISPATCH_P(8, launch_gather_t, L, pl, nf, F, phi)
+}
+
+template <typename R, int M>
+int launch_fft_chain_m(Launcher& L, enuf_plan* pl, int nf)
+{
+    using V = typename Cpx<R>::T;
+    const Resolved& r = pl->r;
+    const Layout& y = pl->lay;
+    const V* W = at<const V>(pl, y.twid);
+    const size_t vs = sizeof(V);
+    // forward x
+    {
+        const int NT = ffthreads(M / 2), rows = r.gfx.rows;
+        const int nblk = (M * M + rows - 1) / rows;
+        LCHK(L.go("fft_x", k_fx<R, M>, dim3(nblk), dim3(rows * NT), (size_t)rows * (M / 2) * vs, at<const R>(pl, y.grid),
+                  at<V>(pl, y.C1), r.gfx, W));
+    }
+    const int NT = ffthreads(M);
+    // forward y
+    {
+        const int Wc = r.gy.W;
+        LCHK(L.go("fft_y", k_fy<R, M>, dim3((r.Kx + Wc - 1) / Wc, M), dim3(Wc * NT), (size_t)Wc * (M + 1) * vs,
+                  at<const V>(pl, y.C1), at<V>(pl, y.C2), r.gy, W));
+    }
+    // z + reciprocal-space step + inverse z
+    {
+        const int Wc = r.gz.W;
+        const size_t smem = (size_t)2 * Wc * (M + 1) * vs + 32 * 7 * 8;
+        KTables<R> kt;
+        kt.tk = at<const R>(pl, y.tk);
+        kt.te = at<const R>(pl, y.te);
+        kt.td = at<const R>(pl, y.td);
+        const double V3 = r.prm.L[0] * r.prm.L[1] * r.prm.L[2];
+        kt.cE = (R)(r.prm.coulomb_k * 2.0 * kPi / V3);
+        kt.cF = (R)(r.prm.coulomb_k * 4.0 * kPi / V3);
+        kt.inv4a2 = (R)(1.0 / (4.0 * r.prm.alpha * r.prm.alpha));
+        const dim3 g((r.P + Wc - 1) / Wc);
+        if (nf == 0)
+            LCHK(L.go("fft_z_kspace", k_fz<R, M, 0>, g, dim3(Wc * NT), smem, at<const V>(pl, y.C2), at<V>(pl, y.C3), r.gz,
+                      W, kt, at<double>(pl, y.kpart)));
+        else if (nf == 3)
+            LCHK(L.go("fft_z_kspace", k_fz<R, M, 3>, g, dim3(Wc * NT), smem, at<const V>(pl, y.C2), at<V>(pl, y.C3), r.gz,
+                      W, kt, at<double>(pl, y.kpart)));
+        else
+            LCHK(L.go("fft_z_kspace", k_fz<R, M, 4>, g, dim3(Wc * NT), smem, at<const V>(pl, y.C2), at<V>(pl, y.C3), r.gz,
+                      W, kt, at<double>(pl, y.kpart)));
+    }
+    if (nf == 0) return ENUF_OK;
+    // inverse y
+    {
+        const int Wc = r.gy.W;
+        LCHK(L.go("ifft_y", k_iy<R, M>, dim3((r.Kx + Wc - 1) / Wc, M, nf), dim3(Wc * NT), (size_t)Wc * (M + 1) * vs,
+                  at<const V>(pl, y.C3), at<V>(pl, y.C4), r.gy, W));
+    }
+    // inverse x (complex to real)
+    {
+        const int NTh = ffthreads(M / 2), rows = r.gfx.rows;
+        const int nrows = nf * M * M;
+        LCHK(L.go("ifft_x", k_ix<R, M>, dim3((nrows + rows - 1) / rows), dim3(rows * NTh), (size_t)rows * (M / 2) * vs,
+                  at<const V>(pl, y.C4), at<R>(pl, y.fld), r.gfx, nrows, W));
+    }
+    return ENUF_OK;
+}
+
+template <typename R> int launch_fft_chain(Launcher& L, enuf_plan* pl, int nf)
+{
+    switch (pl->r.prm.M) {
+    case 8: return launch_fft_chain_m<R, 8>(L, pl, nf);
+    case 16: return launch_fft_chain_m<R, 16>(L, pl, nf);
+    case 32: return launch_fft_chain_m<R, 32>(L, pl, nf);
+    case 64: return launch_fft_chain_m<R, 64>(L, pl, nf);
+    case 128: return launch_fft_chain_m<R, 128>(L, pl, nf);
+    case 256: return launch_fft_chain_m<R, 256>(L, pl, nf);
+    case 512: return launch_fft_chain_m<R, 512>(L, pl, nf);
+    default: return fail(ENUF_EUNSUPPORTED, "unsupported M");
+    }
+}
+
+BinGeom make_geom(const int S[3], int T, const double L3[3], bool grid_units)
+{
+    BinGeom g{};
+    for (int t = 0; t < 3; t++) {
+        g.S[t] = S[t];
+        g.nb[t] = S[t] / T;
+        g.scale[t] = (double)S[t] / L3[t];
+        g.scale_hi[t] = (float)g.scale[t];
+        g.scale_lo[t] = (float)(g.scale[t] - (double)g.scale_hi[t]);
+        g.unit[t] = grid_units ? 1.0 : L3[t] / S[t];
+    }
+    g.T = T;
+    return g;
+}
+
+// The whole evaluation on stream L.st.
+template <typename R>
+int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, R* phi, double* out, int flags)
+{
+    const Resolved& r = pl->r;
+    const Layout& y = pl->lay;
+    const int N = (int)r.prm.N;
+    const int nblkN = (N + 255) / 256;
+    const bool want_phi = (flags & ENUF_WANT_PHI) && phi;
+    const bool konly = flags & ENUF_KSPACE_ONLY;
+    const int nf = want_phi ? 4 : (F ? 3 : 0);
+    using RecT = typename Rec<R>::T;
+
+    LCHK(L.memset(at<void>(pl, y.status), 16));
+    // (a1, a2) counting sort into grid tiles
+    LCHK(L.memset(at<void>(pl, y.counts), (size_t)(r.nbins + 1) * 4));
+    const int Sg[3] = {r.prm.M, r.prm.M, r.prm.M};
+    const BinGeom gg = make_geom(Sg, r.T, r.prm.L, true);
+    LCHK(L.go("bin_keys", k_bin_keys<R>, dim3(nblkN), dim3(256), 0, N, pos, q, gg, at<uint32_t>(pl, y.key),
+              at<uint32_t>(pl, y.rank), at<RecT>(pl, y.rec_tmp), at<uint32_t>(pl, y.counts), at<int>(pl, y.status),
+              at<double>(pl, y.qpart)));
+    LCHK(L.go("scan_bins", k_scan_bins, dim3(1), dim3(1024), 0, r.nbins, at<const uint32_t>(pl, y.counts),
+              at<uint32_t>(pl, y.offsets), kWorkCap, at<int4>(pl, y.work), at<int>(pl, y.nwork), r.max_work,
+              at<int>(pl, y.status)));
+    LCHK(L.go("scatter", k_scatter<R>, dim3(nblkN), dim3(256), 0, N, at<const uint32_t>(pl, y.key),
+              at<const uint32_t>(pl, y.rank), at<const uint32_t>(pl, y.offsets), at<const RecT>(pl, y.rec_tmp),
+              at<RecT>(pl, y.rec), at<uint32_t>(pl, y.perm), (uint32_t*)nullptr));
+    // (a3) spread
+    const size_t M3 = (size_t)r.prm.M * r.prm.M * r.prm.M;
+    LCHK(L.memset(at<void>(pl, y.grid), M3 * sizeof(R)));
+    LCHK(launch_spread<R>(L, pl));
+    // (a4-a6) FFT chain with the fused reciprocal step
+    LCHK(launch_fft_chain<R>(L, pl, nf));
+    // (a7) interpolation
+    if (nf > 0) LCHK(launch_gather<R>(L, pl, nf, F, want_phi ? phi : (R*)nullptr));
+    // (a8) real space
+    int nr = 0;
+    if (!konly) {
+        LCHK(L.memset(at<void>(pl, y.rcounts), (size_t)(r.nrbins + 1) * 4));
+        const BinGeom gr = make_geom(r.ncell, 1, r.prm.L, false);
+        LCHK(L.go("real_bin_keys", k_bin_keys<R>, dim3(nblkN), dim3(256), 0, N, pos, q, gr, at<uint32_t>(pl, y.key),
+                  at<uint32_t>(pl, y.rank), at<RecT>(pl, y.rec_tmp), at<uint32_t>(pl, y.rcounts), at<int>(pl, y.status),
+                  (double*)nullptr));
+        LCHK(L.go("real_scan", k_scan_bins, dim3(1), dim3(1024), 0, r.nrbins, at<const uint32_t>(pl, y.rcounts),
+                  at<uint32_t>(pl, y.roffsets), kWorkCap, (int4*)nullptr, (int*)nullptr, 0, at<int>(pl, y.status)));
+        LCHK(L.go("real_scatter", k_scatter<R>, dim3(nblkN), dim3(256), 0, N, at<const uint32_t>(pl, y.key),
+                  at<const uint32_t>(pl, y.rank), at<const uint32_t>(pl, y.roffsets), at<const RecT>(pl, y.rec_tmp),
+                  at<RecT>(pl, y.rrec), at<uint32_t>(pl, y.rperm), at<uint32_t>(pl, y.rcell)));
+        RealParams<R> rp;
+        for (int t = 0; t < 3; t++) {
+            rp.nc[t] = r.ncell[t];
+            rp.h[t] = (R)r.h[t];
+            rp.L[t] = (R)r.prm.L[t];
+        }
+        rp.rc2 = (R)(r.prm.r_c * r.prm.r_c);
+        rp.alpha = (R)r.prm.alpha;
+        rp.two_a_sqpi = (R)(2.0 * r.prm.alpha / std::sqrt(kPi));
+        rp.ke = (R)r.prm.coulomb_k;
+        rp.self_phi = (R)(-2.0 * r.prm.alpha / std::sqrt(kPi));
+        R* Fo = F;
+        R* po = want_phi ? phi : nullptr;
+        if (r.cells)
+            LCHK(L.go("realspace", k_realspace_cells<R>, dim3(nblkN), dim3(256), 0, N, at<const RecT>(pl, y.rrec),
+                      at<const uint32_t>(pl, y.rcell), at<const uint32_t>(pl, y.roffsets), at<const uint32_t>(pl, y.rperm),
+                      rp, Fo, po, at<double>(pl, y.rpart)));
+        else
+            LCHK(L.go("realspace", k_realspace_allpairs<R>, dim3(nblkN), dim3(256), 0, N, at<const RecT>(pl, y.rrec),
+                      at<const uint32_t>(pl, y.rperm), rp, Fo, po, at<double>(pl, y.rpart)));
+        nr = nblkN;
+    }
+    // (a9) assembly
+    FinalParams fp;
+    fp.nq = nblkN;
+    fp.nk = (r.P + r.gz.W - 1) / r.gz.W;
+    fp.nr = nr;
+    fp.ke = r.prm.coulomb_k;
+    fp.alpha = r.prm.alpha;
+    fp.V = r.prm.L[0] * r.prm.L[1] * r.prm.L[2];
+    fp.sqrt_pi = std::sqrt(kPi);
+    fp.kspace_only = konly ? 1 : 0;
+    double* o = out ? out : at<double>(pl, y.out);
+    LCHK(L.go("finalize", k_finalize, dim3(1), dim3(256), 0, at<const double>(pl, y.qpart), at<const double>(pl, y.kpart),
+              at<const double>(pl, y.rpart), fp, at<const int>(pl, y.status), o));
+    if (want_phi && !konly)
+        LCHK(L.go("phi_background", k_phi_background<R>, dim3(nblkN), dim3(256), 0, N, (const double*)o,
+                  -r.prm.coulomb_k * kPi / (fp.V * r.prm.alpha * r.prm.alpha), phi));
+    if ((flags & ENUF_REMOVE_NET_FORCE) && F) {
+        LCHK(L.go("force_sum", k_force_sum<R>, dim3(nblkN), dim3(256), 0, N, (const R*)F, at<double>(pl, y.fpart)));
+        LCHK(L.go("force_mean", k_force_mean, dim3(1), dim3(256), 0, nblkN, N, at<const double>(pl, y.fpart),
+                  at<double>(pl, y.mean)));
+        LCHK(L.go("force_shift", k_force_shift<R>, dim3(nblkN), dim3(256), 0, N, at<const double>(pl, y.mean), F));
+    }
+    return ENUF_OK;
+}
+
+int run_sequence(enuf_plan* pl, cudaStream_t st, bool attr_only, const void* pos, const void* q, void* F, void* phi,
+                 double* out, int flags, int* count = nullptr)
+{
+    Launcher L{pl, st, attr_only};
+    int rc;
+    if (pl->r.fp64)
+        rc = launch_sequence<double>(L, pl, (const double*)pos, (const double*)q, (double*)F, (double*)phi, out, flags);
+    else
+        rc = launch_sequence<float>(L, pl, (const float*)pos, (const float*)q, (float*)F, (float*)phi, out, flags);
+    if (count) *count = L.count;
+    return rc;
+}
+
+int prepare_attrs(enuf_plan* pl)
+{
+    if (pl->attrs_done) return ENUF_OK;
+    // walk every variant once in attribute-only mode (no launches)
+    int flags[3] = {ENUF_WANT_PHI, 0, ENUF_REMOVE_NET_FORCE};
+    for (int k = 0; k < 3; k++) {
+        void* dummy = (void*)pl->ws;
+        int rc = run_sequence(pl, pl->stream, true, dummy, dummy, dummy, dummy, nullptr, flags[k]);
+        if (rc != ENUF_OK) return rc;
+    }
+    int rc = run_sequence(pl, pl->stream, true, pl->ws, pl->ws, nullptr, nullptr, nullptr, 0);
+    if (rc != ENUF_OK) return rc;
+    pl->attrs_done = true;
+    return ENUF_OK;
+}
+
+int upload_tables(enuf_plan* pl)
+{
+    const Resolved& r = pl->r;
+    const int M = r.prm.M, Kb = r.Kb, nc = r.nc;
+    std::vector<double> tw(2 * M), tk(3 * Kb), te(3 * Kb), td(3 * Kb);
+    for (int k = 0; k < M; k++) {
+        double a = -2.0 * kPi * (double)k / (double)M;
+        tw[2 * k] = std::cos(a);
+        tw[2 * k + 1] = std::sin(a);
+    }
+    for (int t = 0; t < 3; t++)
+        for (int n = -nc; n <= nc; n++) {
+            const double kk = 2.0 * kPi * n / r.prm.L[t];
+            const double s = kPi * n / (double)M;
+            tk[t * Kb + n + nc] = kk;
+            te[t * Kb + n + nc] = std::exp(-kk * kk / (4.0 * r.prm.alpha * r.prm.alpha));
+            td[t * Kb + n + nc] = std::exp(2.0 * pl->b * s * s);
+        }
+    auto put = [&](size_t off, const std::vector<double>& v) -> int {
+        if (r.fp64) {
+            CK(cudaMemcpy(pl->ws + off, v.data(), v.size() * 8, cudaMemcpyHostToDevice));
+        } else {
+            std::vector<float> f(v.begin(), v.end());
+            CK(cudaMemcpy(pl->ws + off, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
+        }
+        return ENUF_OK;
+    };
+    LCHK(put(pl->lay.twid, tw));
+    LCHK(put(pl->lay.tk, tk));
+    LCHK(put(pl->lay.te, te));
+    LCHK(put(pl->lay.td, td));
+    return ENUF_OK;
+}
+
+void drop_graphs(enuf_plan* pl)
+{
+    for (auto& g : pl->graphs) cudaGraphExecDestroy(g.exec);
+    pl->graphs.clear();
+}
+
+int bind_workspace(enuf_plan* pl, void* ptr)
+{
+    drop_graphs(pl);
+    pl->ws = (char*)ptr;
+    LCHK(upload_tables(pl));
+    pl->attrs_done = false;
+    return prepare_attrs(pl);
+}
+
+int compute_impl(enuf_plan* pl, const void* pos, const void* q, void* F, void* phi, double* out, int flags)
+{
+    if (!pl) return fail(ENUF_EINVAL, "plan is NULL");
+    if (!pl->ws) return fail(ENUF_EINVAL, "plan has no workspace");
+    if (!pos || !q) return fail(ENUF_EINVAL, "pos and q are required");
+    if ((flags & ENUF_WANT_PHI) && !phi) return fail(ENUF_EINVAL, "ENUF_WANT_PHI needs a phi buffer");
+    if (flags & ~(ENUF_WANT_VIRIAL | ENUF_WANT_PHI | ENUF_REMOVE_NET_FORCE | ENUF_KSPACE_ONLY))
+        return fail(ENUF_EINVAL, "unknown flag bits");
+    if (!(flags & ENUF_WANT_PHI)) phi = nullptr;
+    if (pl->profile || !pl->use_graph) {
+        for (auto e : pl->tevents) cudaEventDestroy(e);
+        pl->tevents.clear();
+        pl->tnames.clear();
+        int rc = run_sequence(pl, pl->stream, false, pos, q, F, phi, out, flags);
+        if (pl->profile) {
+            cudaEvent_t e1;
+            cudaEventCreate(&e1);
+            cudaEventRecord(e1, pl->stream);
+            pl->tevents.push_back(e1);
+        }
+        return rc;
+    }
+    for (auto& g : pl->graphs) {
+        if (g.pos == pos && g.q == q && g.F == F && g.phi == phi && g.out == out && g.flags == flags) {
+            g.stamp = ++pl->stamp;
+            CK(cudaGraphLaunch(g.exec, pl->stream));
+            return ENUF_OK;
+        }
+    }
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = run_sequence(pl, pl->cap_stream, false, pos, q, F, phi, out, flags);
+    cudaError_t e = cudaStreamEndCapture(pl->cap_stream, &graph);
+    if (rc != ENUF_OK) {
+        if (e == cudaSuccess) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(ENUF_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+    GraphEntry ge{pos, q, F, phi, out, flags, nullptr, ++pl->stamp};
+    e = cudaGraphInstantiate(&ge.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(ENUF_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    if (pl->graphs.size() >= 8) {
+        auto old = std::min_element(pl->graphs.begin(), pl->graphs.end(),
+                                    [](const GraphEntry& a, const GraphEntry& b) { return a.stamp < b.stamp; });
+        cudaGraphExecDestroy(old->exec);
+        pl->graphs.erase(old);
+    }
+    pl->graphs.push_back(ge);
+    CK(cudaGraphLaunch(ge.exec, pl->stream));
+    return ENUF_OK;
+}
+
+int check_status(const double* parts)
+{
+    const int st = (int)parts[ENUF_OUT_STATUS];
+    if (st & ST_NONFINITE) return fail(ENUF_ENONFINITE, "a position or charge is NaN or infinite");
+    if (st) return fail(ENUF_EDEVICE, "a kernel reported internal status " + std::to_string(st));
+    return ENUF_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* enuf_last_error(void) { return g_err.c_str(); }
+
+const char* enuf_version(void) { return "enuf-b300 0.1 (sm_103a)"; }
+
+int enuf_plan_workspace_bytes(const enuf_params* params, size_t* bytes)
+{
+    Resolved r;
+    LCHK(resolve(params, r));
+    if (!bytes) return fail(ENUF_EINVAL, "bytes is NULL");
+    *bytes = layout(r).total;
+    return ENUF_OK;
+}
+
+int enuf_plan_create(const enuf_params* params, void* cuda_stream, int allocate, enuf_plan** out)
+{
+    g_err.clear();
+    if (!out) return fail(ENUF_EINVAL, "out is NULL");
+    *out = nullptr;
+    Resolved r;
+    LCHK(resolve(params, r));
+    enuf_plan* pl = new enuf_plan();
+    pl->r = r;
+    pl->lay = layout(r);
+    pl->stream = (cudaStream_t)cuda_stream;
+    const double sigma = (double)r.prm.M / (2.0 * r.nc), m = 0.5 * r.prm.p;
+    pl->b = 2.0 * sigma * m / ((2.0 * sigma - 1.0) * kPi);
+    pl->inv_b = 1.0 / pl->b;
+    pl->cnorm3 = std::pow(kPi * pl->b, -1.5);
+    const char* ev = std::getenv("ENUF_NO_GRAPH");
+    pl->use_graph = !(ev && ev[0] == '1');
+    ev = std::getenv("ENUF_PROFILE");
+    pl->profile = ev && ev[0] == '1';
+    cudaError_t e = cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete pl;
+        return fail(ENUF_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+    }
+    if (allocate) {
+        void* p = nullptr;
+        e = cudaMalloc(&p, pl->lay.total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cudaStreamDestroy(pl->cap_stream);
+            delete pl;
+            return fail(ENUF_ENOMEM, "cudaMalloc of " + std::to_string(pl->lay.total) + " bytes failed");
+        }
+        pl->own_ws = true;
+        int rc = bind_workspace(pl, p);
+        if (rc != ENUF_OK) {
+            std::string msg = g_err;
+            enuf_plan_destroy(pl);
+            return fail(rc, msg);
+        }
+    }
+    *out = pl;
+    return ENUF_OK;
+}
+
+int enuf_plan_set_workspace(enuf_plan* pl, void* dev_ptr, size_t bytes)
+{
+    if (!pl || !dev_ptr) return fail(ENUF_EINVAL, "plan or pointer is NULL");
+    if (bytes < pl->lay.total) return fail(ENUF_EINVAL, "workspace too small");
+    if (((uintptr_t)dev_ptr) & 255) return fail(ENUF_EINVAL, "workspace must be 256-byte aligned");
+    if (pl->own_ws && pl->ws) {
+        cudaFree(pl->ws);
+        pl->own_ws = false;
+    }
+    return bind_workspace(pl, dev_ptr);
+}
+
+int enuf_plan_set_stream(enuf_plan* pl, void* cuda_stream)
+{
+    if (!pl) return fail(ENUF_EINVAL, "plan is NULL");
+    pl->stream = (cudaStream_t)cuda_stream;
+    return ENUF_OK;
+}
+
+int enuf_plan_get_params(const enuf_plan* pl, enuf_params* out)
+{
+    if (!pl || !out) return fail(ENUF_EINVAL, "NULL argument");
+    *out = pl->r.prm;
+    return ENUF_OK;
+}
+
+int enuf_plan_destroy(enuf_plan* pl)
+{
+    if (!pl) return ENUF_OK;
+    drop_graphs(pl);
+    for (auto e : pl->tevents) cudaEventDestroy(e);
+    if (pl->own_ws && pl->ws) cudaFree(pl->ws);
+    if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+    delete pl;
+    return ENUF_OK;
+}
+
+int enuf_compute(enuf_plan* pl, const void* pos, const void* q, void* F, void* phi, double* out, int flags)
+{
+    return compute_impl(pl, pos, q, F, phi, out, flags);
+}
+
+int enuf_energy_forces(enuf_plan* pl, const void* pos, const void* q, double* E_host, void* F, double* virial_host,
+                       void* phi, double* parts_host, int flags)
+{
+    if (!pl) return fail(ENUF_EINVAL, "plan is NULL");
+    double* dout = at<double>(pl, pl->lay.out);
+    LCHK(compute_impl(pl, pos, q, F, phi, dout, flags));
+    double h[ENUF_NOUT];
+    CK(cudaMemcpyAsync(h, dout, sizeof(h), cudaMemcpyDeviceToHost, pl->stream));
+    CK(cudaStreamSynchronize(pl->stream));
+    if (E_host) *E_host = h[ENUF_OUT_E];
+    if (virial_host) std::memcpy(virial_host, h + ENUF_OUT_VIRIAL, 9 * sizeof(double));
+    if (parts_host) std::memcpy(parts_host, h, sizeof(h));
+    return check_status(h);
+}
+
+int enuf_energy_forces_host(enuf_plan* pl, const void* pos_host, const void* q_host, double* E_host, void* F_host,
+                            double* virial_host, void* phi_host, int flags)
+{
+    if (!pl || !pl->ws) return fail(ENUF_EINVAL, "plan is NULL or has no workspace");
+    if (!pos_host || !q_host) return fail(ENUF_EINVAL, "pos_host and q_host are required");
+    const size_t N = (size_t)pl->r.prm.N, rs = pl->r.rsz;
+    const Layout& y = pl->lay;
+    CK(cudaMemcpyAsync(pl->ws + y.s_pos, pos_host, 3 * N * rs, cudaMemcpyHostToDevice, pl->stream));
+    CK(cudaMemcpyAsync(pl->ws + y.s_q, q_host, N * rs, cudaMemcpyHostToDevice, pl->stream));
+    void* F = F_host ? (void*)(pl->ws + y.s_F) : nullptr;
+    void* phi = (phi_host && (flags & ENUF_WANT_PHI)) ? (void*)(pl->ws + y.s_phi) : nullptr;
+    if ((flags & ENUF_WANT_PHI) && !phi) flags &= ~ENUF_WANT_PHI;
+    double* dout = at<double>(pl, y.out);
+    LCHK(compute_impl(pl, pl->ws + y.s_pos, pl->ws + y.s_q, F, phi, dout, flags));
+    double h[ENUF_NOUT];
+    CK(cudaMemcpyAsync(h, dout, sizeof(h), cudaMemcpyDeviceToHost, pl->stream));
+    if (F_host) CK(cudaMemcpyAsync(F_host, F, 3 * N * rs, cudaMemcpyDeviceToHost, pl->stream));
+    if (phi) CK(cudaMemcpyAsync(phi_host, phi, N * rs, cudaMemcpyDeviceToHost, pl->stream));
+    CK(cudaStreamSynchronize(pl->stream));
+    if (E_host) *E_host = h[ENUF_OUT_E];
+    if (virial_host) std::memcpy(virial_host, h + ENUF_OUT_VIRIAL, 9 * sizeof(double));
+    return check_status(h);
+}
+
+int enuf_backward(enuf_plan* pl, const void* pos, const void* q, const double* gE, void* dpos, void* dq)
+{
+    if (!pl || !pl->ws) return fail(ENUF_EINVAL, "plan is NULL or has no workspace");
+    const Layout& y = pl->lay;
+    void* F = pl->ws + y.s_F;
+    void* phi = pl->ws + y.s_phi;
+    LCHK(compute_impl(pl, pos, q, F, phi, at<double>(pl, y.out), ENUF_WANT_PHI));
+    const int N = (int)pl->r.prm.N, nb = (N + 255) / 256;
+    if (pl->r.fp64)
+        k_backward_scale<double><<<nb, 256, 0, pl->stream>>>(N, (const double*)F, (const double*)phi, gE, (double*)dpos,
+                                                             (double*)dq);
+    else
+        k_backward_scale<float><<<nb, 256, 0, pl->stream>>>(N, (const float*)F, (const float*)phi, gE, (float*)dpos,
+                                                           (float*)dq);
+    CK(cudaGetLastError());
+    return ENUF_OK;
+}
+
+int enuf_last_timings(enuf_plan* pl, const char** names, float* times_ms, int cap)
+{
+    if (!pl) return fail(ENUF_EINVAL, "plan is NULL");
+    if (!pl->profile || pl->tevents.size() < 2) return 0;
+    CK(cudaEventSynchronize(pl->tevents.back()));
+    const int n = (int)pl->tnames.size();
+    pl->ttimes.assign(n, 0.f);
+    for (int i = 0; i < n; i++) cudaEventElapsedTime(&pl->ttimes[i], pl->tevents[i], pl->tevents[i + 1]);
+    const int m = std::min(n, cap);
+    for (int i = 0; i < m; i++) {
+        if (names) names[i] = pl->tnames[i].c_str();
+        if (times_ms) times_ms[i] = pl->ttimes[i];
+    }
+    return m;
+}
+
+int enuf_launch_count(enuf_plan* pl, int flags, int with_forces)
+{
+    if (!pl || !pl->ws) return fail(ENUF_EINVAL, "plan is NULL or has no workspace");
+    int n = 0;
+    void* d = pl->ws;
+    int rc = run_sequence(pl, pl->stream, true, d, d, with_forces ? d : nullptr, (flags & ENUF_WANT_PHI) ? d : nullptr,
+                          nullptr, flags, &n);
+    return rc == ENUF_OK ? n : rc;
+}
+
+}  // extern "C"

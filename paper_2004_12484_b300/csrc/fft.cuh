@@ -1,0 +1,378 @@
+// fft.cuh -- hand-written 3D FFT of the ENUF grid, pruned to the retained
+// frequency cube |n_t| <= n_c, with the reciprocal-space step fused into the
+// middle (z) pass.
+//
+// Forward chain (Sec. 3.1, "spreading, FFT, and scaling"):
+//   k_fx  real rows along x -> half spectrum, keep kx = 0..n_c
+//   k_fy  along y for each kx, keep ky in the band (2 n_c + 1 values)
+//   k_fz  along z for each (ky, kx) pencil, then for every retained n:
+//         S(n) = D(n) ghat(n) (scaling by the window's Fourier coefficients),
+//         energy and virial (Eq. 38), and the subdivided spectra of the
+//         force field and potential (Eq. 41-42), then the inverse transform
+//         along z of each field ("subdividing" and the first inverse pass)
+// Inverse chain ("subdividing, inverse FFT, and interpolating"):
+//   k_iy  along y (band -> full length) for each field and kx
+//   k_ix  half spectrum kx = 0..n_c -> real rows (complex-to-real)
+//
+// Every 1D transform is an in-shared-memory Stockham autosort FFT: each
+// thread holds R (8, 4 or 2) elements in registers per pass, applies the
+// twiddles and a radix-R butterfly, and writes back in autosort order.  The
+// real-to-complex rows use the half-length complex transform of the packed
+// row (x_{2j} + i x_{2j+1}) and the usual even/odd split.
+// Sign conventions: forward sum_l g_l exp(-2 pi i k l / M), inverse with
+// exp(+...), both unnormalised.
+#pragma once
+#include "common.cuh"
+
+namespace enuf {
+
+// ---------------------------------------------------------------- butterflies
+template <typename V, bool INV> __device__ __forceinline__ void dft2(V* v)
+{
+    V a = v[0];
+    v[0] = cadd(a, v[1]);
+    v[1] = csub(a, v[1]);
+}
+
+// multiply by -i (forward) or +i (inverse)
+template <typename V, bool INV> __device__ __forceinline__ V mul_mi(V d)
+{
+    return INV ? V{-d.y, d.x} : V{d.y, -d.x};
+}
+
+template <typename V, bool INV> __device__ __forceinline__ void dft4(V* v)
+{
+    V t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]), t2 = cadd(v[1], v[3]);
+    V t3 = mul_mi<V, INV>(csub(v[1], v[3]));
+    v[0] = cadd(t0, t2);
+    v[2] = csub(t0, t2);
+    v[1] = cadd(t1, t3);
+    v[3] = csub(t1, t3);
+}
+
+template <typename V, bool INV> __device__ __forceinline__ void dft8(V* v)
+{
+    using R = decltype(v[0].x);
+    V e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+    dft4<V, INV>(e);
+    dft4<V, INV>(o);
+    const R s = (R)0.70710678118654752440;
+    // o[k] *= exp(-+ 2 pi i k / 8)
+    V o1 = o[1], o3 = o[3];
+    if (!INV) {
+        o[1] = V{(o1.x + o1.y) * s, (o1.y - o1.x) * s};
+        o[3] = V{(o3.y - o3.x) * s, -(o3.x + o3.y) * s};
+    } else {
+        o[1] = V{(o1.x - o1.y) * s, (o1.x + o1.y) * s};
+        o[3] = V{-(o3.x + o3.y) * s, (o3.x - o3.y) * s};
+    }
+    o[2] = mul_mi<V, INV>(o[2]);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        v[k] = cadd(e[k], o[k]);
+        v[k + 4] = csub(e[k], o[k]);
+    }
+}
+
+template <typename V, int R, bool INV> __device__ __forceinline__ void dftR(V* v)
+{
+    if constexpr (R == 8) dft8<V, INV>(v);
+    else if constexpr (R == 4) dft4<V, INV>(v);
+    else dft2<V, INV>(v);
+}
+
+template <int N> struct FftThreads {
+    static constexpr int NT = N >= 8 ? N / 8 : 1;
+};
+
+// One Stockham pass of radix R on a contiguous transform of length N in
+// shared memory, served by NT = max(1, N/8) threads (t = 0..NT-1).  All
+// threads of the CTA must call it (it contains barriers).  W is the table
+// exp(-2 pi i k / Mtab), k < Mtab, and ws = Mtab / N.
+template <typename V, int N, int R, int Ns, bool INV>
+__device__ __forceinline__ void stockham_pass(V* x, int t, const V* __restrict__ W, int ws)
+{
+    constexpr int NT = FftThreads<N>::NT;
+    constexpr int NB = N / R;
+    constexpr int PER = NB / NT;
+    V v[PER][R];
+#pragma unroll
+    for (int b = 0; b < PER; b++) {
+        const int j = t + b * NT;
+        const int k = j & (Ns - 1);
+#pragma unroll
+        for (int r = 0; r < R; r++) v[b][r] = x[j + r * NB];
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; r++) {
+                V tw = W[(r * k * (N / (Ns * R))) * ws];
+                if (INV) tw.y = -tw.y;
+                v[b][r] = cmul(v[b][r], tw);
+            }
+        }
+        dftR<V, R, INV>(v[b]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < PER; b++) {
+        const int j = t + b * NT;
+        const int k = j & (Ns - 1);
+        const int d = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; r++) x[d + r * Ns] = v[b][r];
+    }
+    __syncthreads();
+}
+
+template <typename V, int N, int Ns, bool INV> struct FftPasses {
+    static __device__ __forceinline__ void run(V* x, int t, const V* __restrict__ W, int ws)
+    {
+        constexpr int R = (Ns * 8 <= N) ? 8 : ((Ns * 4 <= N) ? 4 : 2);
+        stockham_pass<V, N, R, Ns, INV>(x, t, W, ws);
+        FftPasses<V, N, Ns * R, INV>::run(x, t, W, ws);
+    }
+};
+template <typename V, int N, bool INV> struct FftPasses<V, N, N, INV> {
+    static __device__ __forceinline__ void run(V*, int, const V* __restrict__, int) {}
+};
+
+template <typename V, int N, bool INV>
+__device__ __forceinline__ void fft_smem(V* x, int t, const V* __restrict__ W, int ws)
+{
+    FftPasses<V, N, 1, INV>::run(x, t, W, ws);
+}
+
+// ---------------------------------------------------------------- geometry
+struct FftGeom {
+    int nc;    // retained cutoff
+    int Kx;    // nc + 1 stored kx values
+    int Kb;    // 2 nc + 1 band values along y and z
+    int P;     // Kb * Kx pencils along z
+    int W;     // transforms (columns / pencils) per CTA in k_fy / k_fz / k_iy
+    int rows;  // rows per CTA in k_fx / k_ix
+};
+
+// ---------------------------------------------------------------- k_fx
+// grid: ceil(M*M / rows) blocks, rows * NT(M/2) threads.
+template <typename R, int M>
+__global__ void k_fx(const R* __restrict__ grid, typename Cpx<R>::T* __restrict__ C1, FftGeom g,
+                     const typename Cpx<R>::T* __restrict__ W)
+{
+    using V = typename Cpx<R>::T;
+    constexpr int MH = M / 2, NT = FftThreads<MH>::NT;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* s = reinterpret_cast<V*>(smraw);
+    const int rows = g.rows, row0 = blockIdx.x * rows, nrows = M * M;
+    const V* gin = reinterpret_cast<const V*>(grid);
+    for (int i = threadIdx.x; i < rows * MH; i += blockDim.x) {
+        const int r = i / MH, j = i % MH, row = row0 + r;
+        s[i] = row < nrows ? gin[(size_t)row * MH + j] : V{R(0), R(0)};
+    }
+    __syncthreads();
+    fft_smem<V, MH, false>(s + (threadIdx.x / NT) * MH, threadIdx.x % NT, W, 2);
+    const int Kx = g.Kx;
+    for (int i = threadIdx.x; i < rows * Kx; i += blockDim.x) {
+        const int r = i / Kx, k = i % Kx, row = row0 + r;
+        if (row >= nrows) continue;
+        const V zk = s[r * MH + (k % MH)];
+        const V zc = cconj(s[r * MH + ((MH - k) % MH)]);
+        const V fe = V{R(0.5) * (zk.x + zc.x), R(0.5) * (zk.y + zc.y)};
+        const V d = csub(zk, zc);
+        const V fo = V{R(0.5) * d.y, R(-0.5) * d.x};  // -i/2 (zk - zc)
+        C1[(size_t)row * Kx + k] = cadd(fe, cmul(W[k], fo));
+    }
+}
+
+// ---------------------------------------------------------------- k_fy
+// grid: (ceil(Kx / W), M) blocks, W * NT(M) threads.
+template <typename R, int M>
+__global__ void k_fy(const typename Cpx<R>::T* __restrict__ C1, typename Cpx<R>::T* __restrict__ C2, FftGeom g,
+                     const typename Cpx<R>::T* __restrict__ W)
+{
+    using V = typename Cpx<R>::T;
+    constexpr int NT = FftThreads<M>::NT, LD = M + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* s = reinterpret_cast<V*>(smraw);
+    const int Wc = g.W, Kx = g.Kx, Kb = g.Kb, nc = g.nc;
+    const int kx0 = blockIdx.x * Wc, z = blockIdx.y;
+    for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
+        const int w = i % Wc, y = i / Wc, kx = kx0 + w;
+        s[w * LD + y] = kx < Kx ? C1[((size_t)z * M + y) * Kx + kx] : V{R(0), R(0)};
+    }
+    __syncthreads();
+    fft_smem<V, M, false>(s + (threadIdx.x / NT) * LD, threadIdx.x % NT, W, 1);
+    for (int i = threadIdx.x; i < Wc * Kb; i += blockDim.x) {
+        const int w = i % Wc, kb = i / Wc, kx = kx0 + w;
+        if (kx >= Kx) continue;
+        const int ky = kb <= nc ? kb : M - Kb + kb;
+        C2[((size_t)z * Kb + kb) * Kx + kx] = s[w * LD + ky];
+    }
+}
+
+// ---------------------------------------------------------------- k_fz
+// Reciprocal-space tables (per dimension t, index n + n_c):
+//   tk[t][.] = k_t = 2 pi n / L_t,  te[t][.] = exp(-k_t^2 / (4 alpha^2)),
+//   td[t][.] = D_t(n)^2 = exp(2 b pi^2 n^2 / M^2)  (square of the scaling).
+template <typename R> struct KTables {
+    const R* tk;  // 3 * Kb
+    const R* te;
+    const R* td;
+    R cE;        // coulomb_k * 2 pi / V   (energy prefactor, Eq. 22)
+    R cF;        // coulomb_k * 4 pi / V   (field prefactor, Eq. 41)
+    R inv4a2;    // 1 / (4 alpha^2)
+};
+
+// grid: ceil(P / W) blocks, W * NT(M) threads (a multiple of 32).
+// Writes NF inverse-z-transformed field spectra C3[f][z][kb][kx] and the
+// block's energy/virial partials part[blockIdx][0..6] =
+// (E, Wxx, Wyy, Wzz, Wxy, Wxz, Wyz).  NF = 0 gives the energy only.
+template <typename R, int M, int NF>
+__global__ void k_fz(const typename Cpx<R>::T* __restrict__ C2, typename Cpx<R>::T* __restrict__ C3, FftGeom g,
+                     const typename Cpx<R>::T* __restrict__ W, KTables<R> kt, double* __restrict__ part)
+{
+    using V = typename Cpx<R>::T;
+    constexpr int NT = FftThreads<M>::NT, LD = M + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* X = reinterpret_cast<V*>(smraw);
+    const int Wc = g.W, Kx = g.Kx, Kb = g.Kb, nc = g.nc, P = g.P;
+    V* Y = X + Wc * LD;
+    double* red = reinterpret_cast<double*>(Y + Wc * LD);
+    const int p0 = blockIdx.x * Wc;
+    for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
+        const int w = i % Wc, z = i / Wc, p = p0 + w;
+        X[w * LD + z] = p < P ? C2[(size_t)z * P + p] : V{R(0), R(0)};
+    }
+    __syncthreads();
+    fft_smem<V, M, false>(X + (threadIdx.x / NT) * LD, threadIdx.x % NT, W, 1);
+
+    // scaling, energy / virial, subdivided field spectrum (common factor)
+    R acc[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+    for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
+        const int w = i / M, z = i % M, p = p0 + w;
+        V val = V{R(0), R(0)};
+        const int nz = z <= nc ? z : (z >= M - nc ? z - M : (1 << 20));
+        if (p < P && nz != (1 << 20)) {
+            const int kx = p % Kx, kb = p / Kx;
+            const int nx = kx, ny = kb <= nc ? kb : kb - Kb;
+            if (nx != 0 || ny != 0 || nz != 0) {
+                const R kxv = kt.tk[nx + nc], kyv = kt.tk[Kb + ny + nc], kzv = kt.tk[2 * Kb + nz + nc];
+                const R k2 = kxv * kxv + kyv * kyv + kzv * kzv;
+                const R G = kt.te[nx + nc] * kt.te[Kb + ny + nc] * kt.te[2 * Kb + nz + nc] / k2;
+                const R D2 = kt.td[nx + nc] * kt.td[Kb + ny + nc] * kt.td[2 * Kb + nz + nc];
+                const V gh = X[w * LD + z];
+                const R s2 = D2 * (gh.x * gh.x + gh.y * gh.y);  // |S(n)|^2
+                const R e = (nx == 0 ? R(1) : R(2)) * kt.cE * G * s2;
+                const R c = R(2) * (R(1) / k2 + kt.inv4a2);
+                acc[0] += e;
+                acc[1] += e * (R(1) - c * kxv * kxv);
+                acc[2] += e * (R(1) - c * kyv * kyv);
+                acc[3] += e * (R(1) - c * kzv * kzv);
+                acc[4] -= e * c * kxv * kyv;
+                acc[5] -= e * c * kxv * kzv;
+                acc[6] -= e * c * kyv * kzv;
+                const R f = kt.cF * G * D2;
+                val = V{f * gh.x, f * gh.y};
+            }
+        }
+        X[w * LD + z] = val;
+    }
+    block_reduce_to_double<R, 7>(acc, part + 8 * (size_t)blockIdx.x, red);
+
+#pragma unroll
+    for (int f = 0; f < NF; f++) {
+        for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
+            const int w = i / M, z = i % M, p = p0 + w;
+            const V v = X[w * LD + z];
+            V o;
+            if (f == 3) {
+                o = v;  // potential: cF G D^2 ghat
+            } else {
+                int n;
+                if (f == 0) n = (p < P) ? p % Kx : 0;
+                else if (f == 1) { const int kb = (p < P) ? p / Kx : 0; n = kb <= nc ? kb : kb - Kb; }
+                else n = z <= nc ? z : (z >= M - nc ? z - M : 0);
+                const R kf = kt.tk[f * Kb + n + nc];
+                o = V{kf * v.y, -kf * v.x};  // -i k_f v
+            }
+            Y[w * LD + z] = o;
+        }
+        __syncthreads();
+        fft_smem<V, M, true>(Y + (threadIdx.x / NT) * LD, threadIdx.x % NT, W, 1);
+        for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
+            const int w = i % Wc, z = i / Wc, p = p0 + w;
+            if (p < P) C3[((size_t)f * M + z) * P + p] = Y[w * LD + z];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- k_iy
+// grid: (ceil(Kx / W), M, NF) blocks, W * NT(M) threads.
+template <typename R, int M>
+__global__ void k_iy(const typename Cpx<R>::T* __restrict__ C3, typename Cpx<R>::T* __restrict__ C4, FftGeom g,
+                     const typename Cpx<R>::T* __restrict__ W)
+{
+    using V = typename Cpx<R>::T;
+    constexpr int NT = FftThreads<M>::NT, LD = M + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* s = reinterpret_cast<V*>(smraw);
+    const int Wc = g.W, Kx = g.Kx, Kb = g.Kb, nc = g.nc, P = g.P;
+    const int kx0 = blockIdx.x * Wc, z = blockIdx.y, f = blockIdx.z;
+    const V* src = C3 + ((size_t)f * M + z) * P;
+    for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
+        const int w = i % Wc, y = i / Wc, kx = kx0 + w;
+        V v = V{R(0), R(0)};
+        if (kx < Kx) {
+            int kb = -1;
+            if (y <= nc) kb = y;
+            else if (y >= M - nc) kb = y - (M - Kb);
+            if (kb >= 0) v = src[(size_t)kb * Kx + kx];
+        }
+        s[w * LD + y] = v;
+    }
+    __syncthreads();
+    fft_smem<V, M, true>(s + (threadIdx.x / NT) * LD, threadIdx.x % NT, W, 1);
+    V* dst = C4 + ((size_t)f * M + z) * M * Kx;
+    for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
+        const int w = i % Wc, y = i / Wc, kx = kx0 + w;
+        if (kx < Kx) dst[(size_t)y * Kx + kx] = s[w * LD + y];
+    }
+}
+
+// ---------------------------------------------------------------- k_ix
+// grid: ceil(NF*M*M / rows) blocks, rows * NT(M/2) threads.  Complex-to-real
+// rows: X_k (k = 0..n_c, zero above) -> x_j = sum_k X_k e^{2 pi i k j/M} over
+// the Hermitian-completed spectrum.
+template <typename R, int M>
+__global__ void k_ix(const typename Cpx<R>::T* __restrict__ C4, R* __restrict__ fld, FftGeom g, int nrows,
+                     const typename Cpx<R>::T* __restrict__ W)
+{
+    using V = typename Cpx<R>::T;
+    constexpr int MH = M / 2, NT = FftThreads<MH>::NT;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* s = reinterpret_cast<V*>(smraw);
+    const int rows = g.rows, row0 = blockIdx.x * rows, Kx = g.Kx, nc = g.nc;
+    for (int i = threadIdx.x; i < rows * MH; i += blockDim.x) {
+        const int r = i / MH, k = i % MH, row = row0 + r;
+        V z = V{R(0), R(0)};
+        if (row < nrows) {
+            const V* src = C4 + (size_t)row * Kx;
+            const V a = k <= nc ? src[k] : V{R(0), R(0)};
+            const int kb = MH - k;
+            const V b = kb <= nc ? cconj(src[kb]) : V{R(0), R(0)};
+            const V fe = cadd(a, b);
+            const V fo = cmul(csub(a, b), cconj(W[k]));  // (a - b) e^{+2 pi i k / M}
+            z = V{fe.x - fo.y, fe.y + fo.x};             // fe + i fo
+        }
+        s[i] = z;
+    }
+    __syncthreads();
+    fft_smem<V, MH, true>(s + (threadIdx.x / NT) * MH, threadIdx.x % NT, W, 2);
+    V* out = reinterpret_cast<V*>(fld);
+    for (int i = threadIdx.x; i < rows * MH; i += blockDim.x) {
+        const int r = i / MH, j = i % MH, row = row0 + r;
+        if (row < nrows) out[(size_t)row * MH + j] = s[i];
+    }
+}
+
+}  // namespace enuf

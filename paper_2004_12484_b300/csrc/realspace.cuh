@@ -1,0 +1,249 @@
+// realspace.cuh -- real-space part of the Ewald sum (Sec. 2.1) and the
+// final FP64 assembly.
+//
+// Pair energy  q_i q_j erfc(alpha r) / r                        (Eq. 17)
+// Pair force   q_i q_j [erfc(alpha r)/r + 2 alpha/sqrt(pi) e^{-alpha^2 r^2}]
+//              r_ij / r^2                  (Eq. 29, textbook form)
+// Potential    phi_i += q_j erfc(alpha r) / r
+// within r < r_c.  Particles are counting-sorted into linked cells of edge
+// >= r_c (at least 3 per dimension); one thread serves one particle and
+// visits the 27 neighbouring cells (Sec. 3.2: linked-cell list).  Each ordered
+// pair is visited from both ends, so no atomics are needed; the energy and
+// virial take half of each visit.  Boxes too small for 3 cells per dimension
+// use the all-pairs kernel with the minimum image (r_c <= L/2 is required).
+#pragma once
+#include "common.cuh"
+
+namespace enuf {
+
+template <typename R> struct RealParams {
+    int nc[3];   // cells per dimension
+    R h[3];      // cell edges
+    R L[3];      // box (all-pairs kernel)
+    R rc2, alpha, two_a_sqpi, ke;
+    R self_phi;  // -2 alpha / sqrt(pi) (self term of dE/dq_i, times ke inside)
+};
+
+template <typename R>
+__device__ __forceinline__ void pair_term(R dx, R dy, R dz, R qi, R qj, const RealParams<R>& rp, R (&f)[3], R& ph,
+                                          R (&acc)[7])
+{
+    const R r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 >= rp.rc2 || r2 <= R(0)) return;
+    const R r = dsqrt(r2);
+    const R ar = rp.alpha * r;
+    const R ec = derfc(ar) / r;
+    const R fs = qi * qj * (ec + rp.two_a_sqpi * dexp(-ar * ar)) / r2;
+    f[0] += fs * dx;
+    f[1] += fs * dy;
+    f[2] += fs * dz;
+    ph += qj * ec;
+    acc[0] += R(0.5) * qi * qj * ec;
+    acc[1] += R(0.5) * fs * dx * dx;
+    acc[2] += R(0.5) * fs * dy * dy;
+    acc[3] += R(0.5) * fs * dz * dz;
+    acc[4] += R(0.5) * fs * dx * dy;
+    acc[5] += R(0.5) * fs * dx * dz;
+    acc[6] += R(0.5) * fs * dy * dz;
+}
+
+// Adds the real-space force and potential (and the self term of phi) to F
+// and phi in the caller's particle order; part[block] gets (E, W..) partials.
+template <typename R>
+__global__ void __launch_bounds__(256) k_realspace_cells(int N, const typename Rec<R>::T* __restrict__ rec,
+                                                         const uint32_t* __restrict__ cell_of,
+                                                         const uint32_t* __restrict__ offset,
+                                                         const uint32_t* __restrict__ perm, RealParams<R> rp,
+                                                         R* __restrict__ F, R* __restrict__ phi,
+                                                         double* __restrict__ part)
+{
+    __shared__ double red[32 * 7];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    R acc[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+    if (i < N) {
+        const typename Rec<R>::T ri = rec[i];
+        const uint32_t c = cell_of[i];
+        const int cx = c % rp.nc[0], cy = (c / rp.nc[0]) % rp.nc[1], cz = c / (rp.nc[0] * rp.nc[1]);
+        R f[3] = {R(0), R(0), R(0)}, ph = R(0);
+        for (int dz = -1; dz <= 1; dz++) {
+            const int nz = (cz + dz + rp.nc[2]) % rp.nc[2];
+            for (int dy = -1; dy <= 1; dy++) {
+                const int ny = (cy + dy + rp.nc[1]) % rp.nc[1];
+                for (int dx = -1; dx <= 1; dx++) {
+                    const int nx = (cx + dx + rp.nc[0]) % rp.nc[0];
+                    const uint32_t nb = nx + rp.nc[0] * (ny + rp.nc[1] * nz);
+                    const R sx = ri.x - (R)dx * rp.h[0], sy = ri.y - (R)dy * rp.h[1], sz = ri.z - (R)dz * rp.h[2];
+                    const uint32_t e = offset[nb + 1];
+                    for (uint32_t j = offset[nb]; j < e; j++) {
+                        if ((int)j == i) continue;
+                        const typename Rec<R>::T rj = rec[j];
+                        pair_term<R>(sx - rj.x, sy - rj.y, sz - rj.z, ri.w, rj.w, rp, f, ph, acc);
+                    }
+                }
+            }
+        }
+        const uint32_t oi = perm[i];
+        if (F) {
+            F[3 * (size_t)oi] += rp.ke * f[0];
+            F[3 * (size_t)oi + 1] += rp.ke * f[1];
+            F[3 * (size_t)oi + 2] += rp.ke * f[2];
+        }
+        if (phi) phi[oi] += rp.ke * (ph + rp.self_phi * ri.w);
+    }
+    block_reduce_to_double<R, 7>(acc, part + 8 * (size_t)blockIdx.x, red);
+}
+
+// All pairs with the minimum image; records hold wrapped absolute positions.
+template <typename R>
+__global__ void __launch_bounds__(256) k_realspace_allpairs(int N, const typename Rec<R>::T* __restrict__ rec,
+                                                            const uint32_t* __restrict__ perm, RealParams<R> rp,
+                                                            R* __restrict__ F, R* __restrict__ phi,
+                                                            double* __restrict__ part)
+{
+    __shared__ double red[32 * 7];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    R acc[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+    if (i < N) {
+        const typename Rec<R>::T ri = rec[i];
+        R f[3] = {R(0), R(0), R(0)}, ph = R(0);
+        for (int j = 0; j < N; j++) {
+            if (j == i) continue;
+            const typename Rec<R>::T rj = rec[j];
+            R d[3] = {ri.x - rj.x, ri.y - rj.y, ri.z - rj.z};
+#pragma unroll
+            for (int t = 0; t < 3; t++) {
+                if (d[t] > R(0.5) * rp.L[t]) d[t] -= rp.L[t];
+                else if (d[t] < R(-0.5) * rp.L[t]) d[t] += rp.L[t];
+            }
+            pair_term<R>(d[0], d[1], d[2], ri.w, rj.w, rp, f, ph, acc);
+        }
+        const uint32_t oi = perm[i];
+        if (F) {
+            F[3 * (size_t)oi] += rp.ke * f[0];
+            F[3 * (size_t)oi + 1] += rp.ke * f[1];
+            F[3 * (size_t)oi + 2] += rp.ke * f[2];
+        }
+        if (phi) phi[oi] += rp.ke * (ph + rp.self_phi * ri.w);
+    }
+    block_reduce_to_double<R, 7>(acc, part + 8 * (size_t)blockIdx.x, red);
+}
+
+// ---------------------------------------------------------------- assembly
+struct FinalParams {
+    int nq, nk, nr;      // partial counts (nr = 0: no real-space part)
+    double ke, alpha, V, sqrt_pi;
+    int kspace_only;
+};
+
+// One block of 256 threads.  Sums the per-block partials in a fixed order
+// (deterministic), adds the self energy (Eq. 24) and the background term,
+// writes the ENUF_NOUT results.
+__global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ qpart, const double* __restrict__ kpart,
+                                                  const double* __restrict__ rpart, FinalParams fp,
+                                                  const int* __restrict__ status, double* __restrict__ out)
+{
+    __shared__ double s[256][16];
+    double a[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) a[k] = 0.0;
+    for (int b = threadIdx.x; b < fp.nq; b += blockDim.x) { a[0] += qpart[2 * b]; a[1] += qpart[2 * b + 1]; }
+    for (int b = threadIdx.x; b < fp.nk; b += blockDim.x)
+        for (int k = 0; k < 7; k++) a[2 + k] += kpart[8 * b + k];
+    for (int b = threadIdx.x; b < fp.nr; b += blockDim.x)
+        for (int k = 0; k < 7; k++) a[9 + k] += rpart[8 * b + k];
+    for (int k = 0; k < 16; k++) s[threadIdx.x][k] = a[k];
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int k = 0; k < 16; k++) s[threadIdx.x][k] += s[threadIdx.x + o][k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double q2 = s[0][0], Q = s[0][1];
+        const double Ek = s[0][2];
+        const double Er = fp.nr ? fp.ke * s[0][9] : 0.0;
+        double Es = 0.0, Eb = 0.0;
+        if (!fp.kspace_only) {
+            Es = -fp.ke * fp.alpha / fp.sqrt_pi * q2;
+            Eb = -fp.ke * 3.14159265358979323846 * Q * Q / (2.0 * fp.V * fp.alpha * fp.alpha);
+        }
+        // virial components (xx, yy, zz, xy, xz, yz) -> row-major 3x3
+        double w6[6];
+        for (int k = 0; k < 6; k++) w6[k] = s[0][3 + k] + (fp.nr ? fp.ke * s[0][10 + k] : 0.0);
+        out[0] = fp.kspace_only ? Ek : (Er + Ek + Es + Eb);
+        out[1] = Er;
+        out[2] = Ek;
+        out[3] = Es;
+        out[4] = Eb;
+        out[5] = Q;
+        out[6] = w6[0] + Eb; out[7] = w6[3]; out[8] = w6[4];
+        out[9] = w6[3]; out[10] = w6[1] + Eb; out[11] = w6[5];
+        out[12] = w6[4]; out[13] = w6[5]; out[14] = w6[2] + Eb;
+        out[15] = (double)(*status);
+    }
+}
+
+// d(E_background)/dq_i = -ke pi Q / (V alpha^2), the same for every particle.
+template <typename R>
+__global__ void k_phi_background(int N, const double* __restrict__ out, double scale, R* __restrict__ phi)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) phi[i] += (R)(scale * out[5]);
+}
+
+// Net force removal: per-block sums, one-block mean, shift.
+template <typename R>
+__global__ void __launch_bounds__(256) k_force_sum(int N, const R* __restrict__ F, double* __restrict__ part)
+{
+    __shared__ double red[32 * 3];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    R v[3] = {R(0), R(0), R(0)};
+    if (i < N) { v[0] = F[3 * (size_t)i]; v[1] = F[3 * (size_t)i + 1]; v[2] = F[3 * (size_t)i + 2]; }
+    block_reduce_to_double<R, 3>(v, part + 4 * (size_t)blockIdx.x, red);
+}
+
+__global__ void __launch_bounds__(256) k_force_mean(int nb, int N, const double* __restrict__ part,
+                                                    double* __restrict__ mean)
+{
+    __shared__ double s[256][3];
+    double a[3] = {0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+        for (int k = 0; k < 3; k++) a[k] += part[4 * b + k];
+    for (int k = 0; k < 3; k++) s[threadIdx.x][k] = a[k];
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int k = 0; k < 3; k++) s[threadIdx.x][k] += s[threadIdx.x + o][k];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) mean[threadIdx.x] = s[0][threadIdx.x] / (double)N;
+}
+
+template <typename R>
+__global__ void k_force_shift(int N, const double* __restrict__ mean, R* __restrict__ F)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) {
+        F[3 * (size_t)i] -= (R)mean[0];
+        F[3 * (size_t)i + 1] -= (R)mean[1];
+        F[3 * (size_t)i + 2] -= (R)mean[2];
+    }
+}
+
+// Backward: dpos = -gE F, dq = gE phi.
+template <typename R>
+__global__ void k_backward_scale(int N, const R* __restrict__ F, const R* __restrict__ phi,
+                                 const double* __restrict__ gE, R* __restrict__ dpos, R* __restrict__ dq)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const R g = gE ? (R)(*gE) : R(1);
+    if (dpos) {
+        dpos[3 * (size_t)i] = -g * F[3 * (size_t)i];
+        dpos[3 * (size_t)i + 1] = -g * F[3 * (size_t)i + 1];
+        dpos[3 * (size_t)i + 2] = -g * F[3 * (size_t)i + 2];
+    }
+    if (dq) dq[i] = g * phi[i];
+}
+
+}  // namespace enuf

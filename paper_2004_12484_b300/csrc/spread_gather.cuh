@@ -1,0 +1,183 @@
+// spread_gather.cuh -- the two non-equispaced steps of the NFFT (Sec. 3.1):
+//
+//   spreading:      g_l = sum_j q_j prod_t phi(u_{j,t} - l_t)           (a3)
+//   interpolating:  v_j = sum_l prod_t phi(u_{j,t} - l_t) w_l           (a7)
+//
+// with the Gaussian window phi(u) = (pi b)^(-1/2) exp(-u^2/b) on the p grid
+// points l = floor(u) - p/2 + 1 ... floor(u) + p/2 of each dimension.  The
+// window values are computed in registers (Sec. 3.2: "values of window
+// functions ... computed in local memory").
+//
+// Both kernels process one work item = (tile, particle range) per CTA.  A
+// tile is T^3 grid cells; its particles were counting-sorted into it.  The
+// CTA owns a padded shared-memory box of (T+p-1)^3 cells covering every cell
+// the tile's particles touch.  Spreading accumulates into that box with
+// shared-memory atomics and flushes it with one global atomic add per
+// non-zero cell.  Interpolation stages the box of every field once and then
+// reads only shared memory.  Inside a CTA, a group of G >= p lanes serves one
+// particle: lane a takes the x-offset a, so a group reads or writes p
+// consecutive cells of one grid row per step (no bank conflicts inside the
+// group); the group's partial sums are combined with shuffles.
+#pragma once
+#include "common.cuh"
+
+namespace enuf {
+
+template <int P> struct GroupOf {
+    static constexpr int G = P <= 2 ? 2 : (P <= 4 ? 4 : (P <= 8 ? 8 : 16));
+};
+
+// Window weights of one dimension for the in-cell fraction d in [0, 1]:
+// w[a] = exp(-(d + m - 1 - a)^2 / b), a = 0..P-1 (normalisation applied by
+// the caller).
+template <typename R, int P>
+__device__ __forceinline__ void window_weights(R d, R inv_b, R (&w)[P])
+{
+    constexpr int m = P / 2;
+#pragma unroll
+    for (int a = 0; a < P; a++) {
+        R u = d + (R)(m - 1 - a);
+        w[a] = dexp(-u * u * inv_b);
+    }
+}
+
+template <typename R, int T>
+__device__ __forceinline__ void split_offset(R o, int& i, R& d)
+{
+    int c = (int)o;          // o >= 0
+    if (c > T - 1) c = T - 1; // float rounding can give o == T
+    i = c;
+    d = o - (R)c;
+}
+
+template <typename R, int P, int T>
+__global__ void __launch_bounds__(256) k_spread(const int4* __restrict__ work, const int* __restrict__ nwork,
+                                                const typename Rec<R>::T* __restrict__ rec, int M, int nbx,
+                                                int nby, R inv_b, R cnorm3, R* __restrict__ grid)
+{
+    constexpr int PT = T + P - 1, m = P / 2, G = GroupOf<P>::G;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    R* acc = reinterpret_cast<R*>(smraw);
+    if ((int)blockIdx.x >= *nwork) return;  // uniform for the whole CTA
+    const int4 w = work[blockIdx.x];
+    for (int i = threadIdx.x; i < PT * PT * PT; i += blockDim.x) acc[i] = R(0);
+    __syncthreads();
+
+    const int lane = threadIdx.x % G, grp = threadIdx.x / G, ngrp = blockDim.x / G;
+    for (int j = w.y + grp; j < w.z; j += ngrp) {
+        const typename Rec<R>::T r = rec[j];
+        int ix, iy, iz;
+        R dx, dy, dz;
+        split_offset<R, T>(r.x, ix, dx);
+        split_offset<R, T>(r.y, iy, dy);
+        split_offset<R, T>(r.z, iz, dz);
+        R wy[P], wz[P];
+        window_weights<R, P>(dy, inv_b, wy);
+        window_weights<R, P>(dz, inv_b, wz);
+        if (lane < P) {
+            R u = dx + (R)(m - 1 - lane);
+            const R wx = r.w * cnorm3 * dexp(-u * u * inv_b);
+            R* base = acc + (iz * PT + iy) * PT + ix + lane;
+#pragma unroll
+            for (int c = 0; c < P; c++) {
+                const R wxz = wx * wz[c];
+#pragma unroll
+                for (int b = 0; b < P; b++) atomicAdd(base + (c * PT + b) * PT, wxz * wy[b]);
+            }
+        }
+    }
+    __syncthreads();
+
+    const int tile = w.x;
+    const int tx = tile % nbx, ty = (tile / nbx) % nby, tz = tile / (nbx * nby);
+    const int ox = tx * T - (m - 1), oy = ty * T - (m - 1), oz = tz * T - (m - 1);
+    const int mask = M - 1;  // M is a power of two
+    for (int i = threadIdx.x; i < PT * PT * PT; i += blockDim.x) {
+        const R v = acc[i];
+        if (v != R(0)) {
+            const int lx = i % PT, ly = (i / PT) % PT, lz = i / (PT * PT);
+            const int gx = (ox + lx) & mask, gy = (oy + ly) & mask, gz = (oz + lz) & mask;
+            atomicAdd(grid + ((size_t)gz * M + gy) * M + gx, v);
+        }
+    }
+}
+
+// Interpolation of NF real fields (planes of M^3, plane stride M^3).  Fields
+// 0..2 give the force per unit charge (F_i = q_i * value), field 3 (when
+// NF = 4) the potential phi_i.  F is written (not accumulated) in the
+// caller's particle order through perm.
+template <typename R, int P, int T, int NF>
+__global__ void __launch_bounds__(256) k_gather(const int4* __restrict__ work, const int* __restrict__ nwork,
+                                                const typename Rec<R>::T* __restrict__ rec,
+                                                const uint32_t* __restrict__ perm, int M, int nbx, int nby,
+                                                R inv_b, R cnorm3, const R* __restrict__ fld, R* __restrict__ F,
+                                                R* __restrict__ phi)
+{
+    constexpr int PT = T + P - 1, PT3 = PT * PT * PT, m = P / 2, G = GroupOf<P>::G;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    R* s = reinterpret_cast<R*>(smraw);
+    if ((int)blockIdx.x >= *nwork) return;
+    const int4 w = work[blockIdx.x];
+    const int tile = w.x;
+    const int tx = tile % nbx, ty = (tile / nbx) % nby, tz = tile / (nbx * nby);
+    const int ox = tx * T - (m - 1), oy = ty * T - (m - 1), oz = tz * T - (m - 1);
+    const int mask = M - 1;
+    const size_t M3 = (size_t)M * M * M;
+    for (int i = threadIdx.x; i < PT3; i += blockDim.x) {
+        const int lx = i % PT, ly = (i / PT) % PT, lz = i / (PT * PT);
+        const size_t gi = ((size_t)((oz + lz) & mask) * M + ((oy + ly) & mask)) * M + ((ox + lx) & mask);
+#pragma unroll
+        for (int f = 0; f < NF; f++) s[f * PT3 + i] = fld[f * M3 + gi];
+    }
+    __syncthreads();
+
+    const int lane = threadIdx.x % G, grp = threadIdx.x / G, ngrp = blockDim.x / G;
+    const unsigned gmask = (G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G)));
+    for (int j = w.y + grp; j < w.z; j += ngrp) {
+        const typename Rec<R>::T r = rec[j];
+        int ix, iy, iz;
+        R dx, dy, dz;
+        split_offset<R, T>(r.x, ix, dx);
+        split_offset<R, T>(r.y, iy, dy);
+        split_offset<R, T>(r.z, iz, dz);
+        R wy[P], wz[P];
+        window_weights<R, P>(dy, inv_b, wy);
+        window_weights<R, P>(dz, inv_b, wz);
+        R acc[NF];
+#pragma unroll
+        for (int f = 0; f < NF; f++) acc[f] = R(0);
+        if (lane < P) {
+            R u = dx + (R)(m - 1 - lane);
+            const R wx = dexp(-u * u * inv_b);
+            const R* base = s + (iz * PT + iy) * PT + ix + lane;
+#pragma unroll
+            for (int c = 0; c < P; c++) {
+                const R wxz = wx * wz[c];
+#pragma unroll
+                for (int b = 0; b < P; b++) {
+                    const R ww = wxz * wy[b];
+                    const int o = (c * PT + b) * PT;
+#pragma unroll
+                    for (int f = 0; f < NF; f++) acc[f] += ww * base[f * PT3 + o];
+                }
+            }
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+#pragma unroll
+            for (int f = 0; f < NF; f++) acc[f] += __shfl_xor_sync(gmask, acc[f], o, G);
+        }
+        if (lane == 0) {
+            const uint32_t oi = perm[j];
+            if (F) {
+                const R qc = r.w * cnorm3;
+                F[3 * (size_t)oi] = qc * acc[0];
+                F[3 * (size_t)oi + 1] = qc * acc[1];
+                F[3 * (size_t)oi + 2] = qc * acc[2];
+            }
+            if (NF == 4 && phi) phi[oi] = cnorm3 * acc[NF - 1];
+        }
+    }
+}
+
+}  // namespace enuf
