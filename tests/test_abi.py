@@ -1,0 +1,56 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every function include/enuf.h declares, and validates plan parameters."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2004_12484_b300 as P
+
+HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "enuf.h")
+
+
+def declared_functions():
+    text = open(HDR).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(enuf_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = P.lib()
+    names = declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_params_struct_matches_header_layout():
+    # double L[3]; int64 N; double alpha, r_c; int M, p, n_c, precision; double coulomb_k; int flags
+    assert ctypes.sizeof(P.EnufParams) == 80
+    assert P.EnufParams.coulomb_k.offset == 64
+
+
+def base(**kw):
+    d = dict(L=(20.0, 20.0, 20.0), N=100, alpha=0.3, r_c=9.0, M=32, p=4, n_c=0, precision="mixed")
+    d.update(kw)
+    return d
+
+
+def test_workspace_bytes_scales_with_grid():
+    a = P.workspace_bytes(**base(M=32))
+    b = P.workspace_bytes(**base(M=64))
+    assert b > 6 * a
+
+
+@pytest.mark.parametrize("bad", [dict(M=48), dict(M=4), dict(M=1024), dict(p=5), dict(p=14), dict(p=0),
+                                 dict(n_c=16), dict(n_c=-1), dict(r_c=11.0), dict(r_c=0.0), dict(alpha=0.0),
+                                 dict(N=0), dict(L=(20.0, -1.0, 20.0)), dict(precision=7)])
+def test_invalid_parameters_are_rejected(bad):
+    with pytest.raises(P.EnufError):
+        P.workspace_bytes(**base(**bad))
+
+
+def test_error_message_is_reported():
+    with pytest.raises(P.EnufError, match="power of two"):
+        P.workspace_bytes(**base(M=48))

@@ -1,0 +1,74 @@
+"""The differentiable energy: backward returns dE/dr = -F and dE/dq = phi,
+checked against the forward outputs, the oracle, and central differences."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2004_12484_b300 as P  # noqa: E402
+
+DEV = torch.device("cuda", 0)
+
+
+def test_backward_matches_forces_and_oracle_fp64():
+    g = np.random.default_rng(31)
+    N, L = 400, np.array([14.0, 15.0, 16.0])
+    pos = g.uniform(0, 15, size=(N, 3))
+    q = g.normal(size=N)
+    q -= q.mean()
+    kw = dict(alpha=0.45, r_c=6.0, M=32, p=8, n_c=8)
+    plan = P.Plan(L=L, N=N, precision="fp64", device=DEV, **kw)
+    tp = torch.tensor(pos, dtype=torch.float64, device=DEV, requires_grad=True)
+    tq = torch.tensor(q, dtype=torch.float64, device=DEV, requires_grad=True)
+    E = P.EnufEnergy.apply(tp, tq, plan)
+    (2.5 * E).backward()
+    ref = O.nfft_ewald(pos, q, L, kw["alpha"], kw["r_c"], kw["M"], kw["p"], kw["n_c"])
+    assert abs(float(E) / ref.E - 1) < 1e-12
+    assert np.abs(tp.grad.cpu().numpy() - (-2.5 * ref.F)).max() < 1e-11 * np.abs(ref.F).max()
+    assert np.abs(tq.grad.cpu().numpy() - 2.5 * ref.phi).max() < 1e-11 * np.abs(ref.phi).max()
+
+
+def test_dE_dq_central_difference_fp64():
+    """E is quadratic in q: the central difference equals phi up to rounding."""
+    d = W.rpm(N=2048, seed=32, M=32, p=6, r_c=9.0, alpha=0.35)
+    plan = P.Plan(L=d["L"], N=2048, alpha=0.35, r_c=9.0, M=32, p=6, precision="fp64", device=DEV)
+    tp = torch.tensor(d["pos"], dtype=torch.float64, device=DEV)
+    tq = torch.tensor(d["q"], dtype=torch.float64, device=DEV)
+    _, dq = plan.backward(tp, tq)
+    dq = dq.cpu().numpy()
+    h = 1e-3
+    for i in [0, 17, 2047]:
+        qp = tq.clone(); qp[i] += h
+        qm = tq.clone(); qm[i] -= h
+        ep = float(P.EnufEnergy.apply(tp, qp, plan))
+        em = float(P.EnufEnergy.apply(tp, qm, plan))
+        assert abs((ep - em) / (2 * h) - dq[i]) < 1e-9 * (1 + abs(dq[i]))
+
+
+def test_dE_dr_central_difference_polyelectrolyte_like():
+    """Central differences in positions (h = 1e-4 sigma) on 64 random beads of
+    a polyelectrolyte-like system; the ik forces equal -dE/dr only up to the
+    NFFT accuracy, so the bound is a small multiple of that error."""
+    d = W.polyelectrolyte(n_beads=8000, seed=33, M=32, p=6, alpha=0.739)
+    N = len(d["q"])
+    plan = P.Plan(L=d["L"], N=N, alpha=d["alpha"], r_c=3.0, M=32, p=6, precision="fp64", device=DEV)
+    tp = torch.tensor(d["pos"], dtype=torch.float64, device=DEV)
+    tq = torch.tensor(d["q"], dtype=torch.float64, device=DEV)
+    dpos, _ = plan.backward(tp, tq)
+    dpos = dpos.cpu().numpy()
+    beads = np.random.default_rng(34).choice(np.nonzero(d["q"][: d["n_beads"]] != 0)[0], 64, replace=False)
+    h = 1e-4
+    fd = np.zeros((64, 3))
+    for k, i in enumerate(beads):
+        for t in range(3):
+            pp = tp.clone(); pp[i, t] += h
+            pm = tp.clone(); pm[i, t] -= h
+            fd[k, t] = (float(P.EnufEnergy.apply(pp, tq, plan)) - float(P.EnufEnergy.apply(pm, tq, plan))) / (2 * h)
+    err = np.sqrt(((fd - dpos[beads]) ** 2).sum() / (dpos[beads] ** 2).sum())
+    assert err < 1e-3, err

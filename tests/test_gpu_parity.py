@@ -1,0 +1,212 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (relative): FP64 plans 1e-12 for E, F, phi and the virial;
+mixed plans 1e-6 for E and 1e-5 for the RMS of F (and phi, virial).  Mixed
+plans receive float32 inputs and the oracle the same float32 values.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2004_12484_b300 as P  # noqa: E402
+
+DEV = torch.device("cuda", 0)
+TOL = {"fp64": dict(E=1e-12, F=1e-12, phi=1e-12, W=1e-12), "mixed": dict(E=1e-6, F=1e-5, phi=1e-5, W=1e-5)}
+
+
+def rel_rms(a, b):
+    return float(np.sqrt(((a - b) ** 2).sum() / max((b ** 2).sum(), 1e-300)))
+
+
+def run(pos, q, L, alpha, rc, M, p, nc, precision, phi=True, kspace_only=False):
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    plan = P.Plan(L=L, N=len(q), alpha=alpha, r_c=rc, M=M, p=p, n_c=nc, precision=precision, device=DEV)
+    tp = torch.tensor(pos, dtype=dt, device=DEV)
+    tq = torch.tensor(q, dtype=dt, device=DEV)
+    parts, F, Wv, ph = plan.energy_forces(tp, tq, phi=phi, kspace_only=kspace_only)
+    return parts, F.cpu().double().numpy(), Wv, (ph.cpu().double().numpy() if ph is not None else None)
+
+
+def inputs(pos, q, precision):
+    return W.as_fp32(pos, q) if precision == "mixed" else (pos, q)
+
+
+def check_full(pos, q, L, alpha, rc, M, p, nc, precision):
+    pos, q = inputs(pos, q, precision)
+    parts, F, Wv, ph = run(pos, q, L, alpha, rc, M, p, nc, precision)
+    ref = O.nfft_ewald(pos, q, L, alpha, rc, M, p, nc)
+    t = TOL[precision]
+    assert abs(parts["E"] / ref.E - 1) < t["E"], (parts["E"], ref.E)
+    assert abs(parts["E_recip"] / ref.E_recip - 1) < t["E"] * max(1.0, abs(ref.E / ref.E_recip))
+    assert rel_rms(F, ref.F) < t["F"]
+    assert rel_rms(ph, ref.phi) < t["phi"]
+    assert np.abs(Wv - ref.virial).max() < t["W"] * np.abs(ref.virial).max()
+    return parts, ref
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_nacl_config(precision):
+    """512-ion rock salt, grid 32^3, p = 4 (the FP64 parity workload)."""
+    d = W.nacl()
+    check_full(d["pos"], d["q"], d["L"], d["alpha"], d["r_c"], d["M"], d["p"], d["n_c"], precision)
+
+
+CASES = [
+    # (N, L, alpha, rc, M, p, nc, seed)
+    (300, (12.0, 13.0, 14.0), 0.5, 5.5, 16, 2, 0, 1),
+    (300, (12.0, 13.0, 14.0), 0.5, 5.5, 32, 6, 7, 2),
+    (700, (20.0, 20.0, 20.0), 0.35, 6.5, 32, 8, 10, 3),
+    (1000, (25.0, 18.0, 30.0), 0.3, 8.0, 64, 10, 16, 4),
+    (517, (16.0, 16.0, 16.0), 0.45, 5.0, 64, 12, 0, 5),
+    (2000, (40.0, 40.0, 40.0), 0.3, 9.0, 8, 4, 3, 6),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_random_systems(case, precision):
+    """Random neutral systems across grid sizes, window widths, cutoffs and
+    anisotropic boxes, with positions outside the box (wrapping)."""
+    N, L, alpha, rc, M, p, nc, seed = case
+    g = np.random.default_rng(seed)
+    L = np.array(L)
+    pos = g.uniform(-1.0, 2.0, size=(N, 3)) * L
+    q = g.normal(size=N)
+    q -= q.mean()
+    check_full(pos, q, L, alpha, rc, M, p, nc or M // 4, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_non_neutral_and_single_ion(precision):
+    """Net charge: background term (and its potential shift); a single ion
+    (Wigner lattice) is the degenerate N = 1 case."""
+    g = np.random.default_rng(8)
+    L = np.full(3, 15.0)
+    pos = g.uniform(0, 15, size=(200, 3))
+    q = g.normal(size=200) + 0.3
+    check_full(pos, q, L, 0.5, 6.0, 32, 6, 8, precision)
+    parts, _ = check_full(np.array([[1.0, 2.0, 3.0]]), np.array([1.0]), np.full(3, 10.0), 0.6, 4.9, 32, 8, 8,
+                          precision)
+    assert abs(parts["E"] / (-2.837297 / 20.0) - 1) < 2e-4
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_all_particles_in_one_tile(precision):
+    """Heavy-bin splitting: 3000 particles inside one 8^3 tile."""
+    g = np.random.default_rng(9)
+    L = np.full(3, 32.0)
+    pos = 1.0 + g.uniform(0, 7.0, size=(3000, 3))
+    q = g.normal(size=3000)
+    q -= q.mean()
+    check_full(pos, q, L, 0.4, 7.0, 32, 6, 8, precision)
+
+
+def test_rpm_config_kspace_full_size():
+    """RPM electrolyte at full size (N = 65,536, grid 128^3, p = 6, mixed):
+    reciprocal part element by element against the oracle."""
+    d = W.rpm()
+    pos, q = W.as_fp32(d["pos"], d["q"])
+    parts, F, Wv, ph = run(pos, q, d["L"], d["alpha"], d["r_c"], d["M"], d["p"], d["n_c"], "mixed",
+                           kspace_only=True)
+    Ek, Fk, phik, Wk = O.kspace_nfft(pos, q, d["L"], d["alpha"], d["M"], d["p"], d["n_c"])
+    assert abs(parts["E"] / Ek - 1) < 1e-6
+    assert rel_rms(F, Fk) < 1e-5
+    assert rel_rms(ph, phik) < 1e-5
+    assert np.abs(Wv - Wk).max() < 1e-5 * np.abs(Wk).max()
+
+
+def test_rpm_config_real_space_sampled():
+    """Full RPM step: the real-space part on sampled particles (the oracle
+    sums every pair for each sampled particle)."""
+    d = W.rpm()
+    pos, q = W.as_fp32(d["pos"], d["q"])
+    parts, F, Wv, ph = run(pos, q, d["L"], d["alpha"], d["r_c"], d["M"], d["p"], d["n_c"], "mixed")
+    _, Fk, phik, _ = run(pos, q, d["L"], d["alpha"], d["r_c"], d["M"], d["p"], d["n_c"], "mixed", kspace_only=True)
+    idx = np.random.default_rng(22).choice(len(q), 256, replace=False)
+    _, Fr, phir, _ = O.real_space(pos, q, d["L"], d["alpha"], d["r_c"], idx=idx)
+    assert rel_rms(F[idx] - Fk[idx], Fr) < 1e-5
+    self_phi = -2 * d["alpha"] / np.sqrt(np.pi) * q[idx]
+    assert rel_rms(ph[idx] - phik[idx], phir + self_phi) < 1e-5
+    # E_real = 1/2 sum_i q_i phi_real,i (checked on the device output)
+    phir_all = ph - phik - (-2 * d["alpha"] / np.sqrt(np.pi) * q)
+    assert abs(0.5 * (q * phir_all).sum() / parts["E_real"] - 1) < 1e-5
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_invariants_translation_and_net_force(precision):
+    """Shift by whole grid cells leaves the result unchanged; the sum of the
+    reciprocal forces vanishes (momentum conservation)."""
+    d = W.rpm(N=4096, seed=12, M=32, p=6, r_c=10.0, alpha=0.3)
+    pos, q = inputs(d["pos"], d["q"], precision)
+    L = d["L"]
+    a = run(pos, q, L, d["alpha"], d["r_c"], 32, 6, 8, precision, kspace_only=True)
+    h = L[0] / 32
+    b = run(pos + np.array([2, -3, 5]) * h, q, L, d["alpha"], d["r_c"], 32, 6, 8, precision, kspace_only=True)
+    tol = 1e-12 if precision == "fp64" else 2e-5
+    assert abs(a[0]["E"] / b[0]["E"] - 1) < tol
+    assert rel_rms(a[1], b[1]) < tol * 10
+    Fsum = np.abs(a[1].sum(0)).max()
+    assert Fsum < (1e-12 if precision == "fp64" else 1e-6) * np.abs(a[1]).sum()
+
+
+def test_remove_net_force_flag():
+    d = W.rpm(N=4096, seed=13, M=32, p=6, r_c=10.0, alpha=0.3)
+    plan = P.Plan(L=d["L"], N=4096, alpha=0.3, r_c=10.0, M=32, p=6, precision="fp64", device=DEV)
+    tp = torch.tensor(d["pos"], dtype=torch.float64, device=DEV)
+    tq = torch.tensor(d["q"], dtype=torch.float64, device=DEV)
+    _, F0, _, _ = plan.energy_forces(tp, tq)
+    _, F1, _, _ = plan.energy_forces(tp, tq, remove_net_force=True)
+    F0 = F0.cpu().numpy(); F1 = F1.cpu().numpy()
+    assert np.abs(F1.sum(0)).max() < 1e-10 * np.abs(F1).sum()
+    assert np.abs((F0 - F1) - F0.mean(0)).max() < 1e-12 * np.abs(F0).max()
+
+
+def test_fp64_determinism_and_graph_replay():
+    """Two replays of the captured graph agree to rounding (atomics reorder
+    sums), and a fresh capture for new buffers gives the same values."""
+    d = W.rpm(N=8192, seed=14, M=64, p=8, r_c=10.0, alpha=0.3)
+    plan = P.Plan(L=d["L"], N=8192, alpha=0.3, r_c=10.0, M=64, p=8, precision="fp64", device=DEV)
+    tp = torch.tensor(d["pos"], dtype=torch.float64, device=DEV)
+    tq = torch.tensor(d["q"], dtype=torch.float64, device=DEV)
+    F = torch.empty((8192, 3), dtype=torch.float64, device=DEV)
+    out = torch.empty(16, dtype=torch.float64, device=DEV)
+    plan.compute(tp, tq, F=F, out=out)
+    e1, f1 = out.clone(), F.clone()
+    plan.compute(tp, tq, F=F, out=out)
+    assert abs(float(out[0] / e1[0]) - 1) < 1e-13
+    assert float((F - f1).abs().max() / f1.abs().max()) < 1e-13
+    o2, F2, _ = plan.compute(tp.clone(), tq.clone())
+    assert abs(float(o2[0] / e1[0]) - 1) < 1e-13
+
+
+def test_nonfinite_input_is_reported():
+    plan = P.Plan(L=(20.0,) * 3, N=64, alpha=0.4, r_c=8.0, M=16, p=4, precision="mixed", device=DEV)
+    tp = torch.rand((64, 3), device=DEV) * 20
+    tq = torch.ones(64, device=DEV)
+    tp[5, 1] = float("nan")
+    with pytest.raises(P.EnufError, match="NaN"):
+        plan.energy_forces(tp, tq)
+    # the plan stays usable
+    tp[5, 1] = 1.0
+    plan.energy_forces(tp, tq)
+
+
+def test_host_buffer_entry_point_matches_device_call():
+    d = W.rpm(N=4096, seed=15, M=32, p=6, r_c=10.0, alpha=0.3)
+    pos, q = W.as_fp32(d["pos"], d["q"])
+    plan = P.Plan(L=d["L"], N=4096, alpha=0.3, r_c=10.0, M=32, p=6, precision="mixed", device=DEV)
+    ph = torch.tensor(pos, dtype=torch.float32).pin_memory()
+    qh = torch.tensor(q, dtype=torch.float32).pin_memory()
+    Fh = torch.empty((4096, 3), dtype=torch.float32).pin_memory()
+    E, Wv = plan.energy_forces_host(ph, qh, F_host=Fh)
+    parts, F, W2, _ = plan.energy_forces(ph.to(DEV), qh.to(DEV))
+    assert abs(E / parts["E"] - 1) < 1e-12
+    assert float((Fh - F.cpu()).abs().max()) < 1e-6 * float(F.abs().max())
