@@ -95,9 +95,16 @@ int resolve(const enuf_params* in, Resolved& r)
     r.Kx = r.nc + 1;
     r.Kb = 2 * r.nc + 1;
     r.P = r.Kb * r.Kx;
-    // tile edge: 16 where the gather's shared-memory box of 4 fields fits
-    const int pt16 = 16 + p.p - 1;
-    r.T = (!r.fp64 && p.M >= 256 && 4ull * pt16 * pt16 * pt16 * 4 <= (size_t)kMaxSmem) ? 16 : 8;
+    // tile edge: 16 for float grids of edge >= 128, else 8, else 4 -- the
+    // largest for which the interpolation box of 4 fields fits in shared
+    // memory (the same box geometry as Box<P, T> in spread_gather.cuh)
+    auto box_bytes = [&](int T) {
+        const int m = p.p / 2, XA = (m - 1 + 3) / 4 * 4, BX = (XA + T + m + 3) / 4 * 4, PT = T + p.p - 1;
+        return (size_t)BX * PT * PT * 4 * r.rsz;
+    };
+    r.T = (!r.fp64 && p.M >= 128) ? 16 : 8;
+    while (r.T > 4 && box_bytes(r.T) > (size_t)kMaxSmem) r.T /= 2;
+    if (box_bytes(r.T) > (size_t)kMaxSmem) return fail(ENUF_EUNSUPPORTED, "window too wide for the tile box");
     for (int t = 0; t < 3; t++) r.nbt[t] = p.M / r.T;
     r.nbins = r.nbt[0] * r.nbt[1] * r.nbt[2];
     r.max_work = r.nbins + (int)(p.N / kWorkCap) + 1;
@@ -123,14 +130,14 @@ int resolve(const enuf_params* in, Resolved& r)
         int nch = (r.Kx + 15) / 16;
         int W = round_up((r.Kx + nch - 1) / nch, gran);
         while (W * NT > 1024) W -= gran;
-        while ((size_t)W * (M + 1) * vsz > (size_t)kMaxSmem) W -= gran;
+        while ((size_t)(W * (M + 1) + M) * vsz > (size_t)kMaxSmem) W -= gran;
         r.gy = FftGeom{r.nc, r.Kx, r.Kb, r.P, W, 0};
     }
     // k_fz: pencils per block
     {
         int W = round_up(16, gran);
         while (W * NT > 1024) W -= gran;
-        while ((size_t)2 * W * (M + 1) * vsz + 32 * 7 * 8 > (size_t)kMaxSmem) W -= gran;
+        while ((size_t)(2 * W * (M + 1) + M) * vsz + 32 * 7 * 8 + (size_t)9 * r.Kb * r.rsz > (size_t)kMaxSmem) W -= gran;
         r.gz = FftGeom{r.nc, r.Kx, r.Kb, r.P, W, 0};
     }
     if (r.gy.W < 1 || r.gz.W < 1) return fail(ENUF_EUNSUPPORTED, "FFT block shape does not fit");
@@ -285,8 +292,7 @@ int launch_spread_t(Launcher& L, enuf_plan* pl)
 {
     const Resolved& r = pl->r;
     const Layout& y = pl->lay;
-    constexpr int PT = T + P - 1;
-    return L.go("spread", k_spread<R, P, T>, dim3(r.max_work), dim3(256), (size_t)PT * PT * PT * sizeof(R),
+    return L.go("spread", k_spread<R, P, T>, dim3(r.max_work), dim3(256), (size_t)Box<P, T>::CELLS * sizeof(R),
                 at<const int4>(pl, y.work), at<const int>(pl, y.nwork), at<const typename Rec<R>::T>(pl, y.rec),
                 r.prm.M, r.nbt[0], r.nbt[1], (R)pl->inv_b, (R)pl->cnorm3, at<R>(pl, y.grid));
 }
@@ -296,8 +302,7 @@ int launch_gather_t(Launcher& L, enuf_plan* pl, int nf, R* F, R* phi)
 {
     const Resolved& r = pl->r;
     const Layout& y = pl->lay;
-    constexpr int PT = T + P - 1;
-    const size_t smem = (size_t)nf * PT * PT * PT * sizeof(R);
+    const size_t smem = (size_t)nf * Box<P, T>::CELLS * sizeof(R);
     if (nf == 4)
         return L.go("gather", k_gather<R, P, T, 4>, dim3(r.max_work), dim3(256), smem, at<const int4>(pl, y.work),
                     at<const int>(pl, y.nwork), at<const typename Rec<R>::T>(pl, y.rec), at<const uint32_t>(pl, y.perm),
@@ -321,12 +326,14 @@ int launch_gather_t(Launcher& L, enuf_plan* pl, int nf, R* F, R* phi)
 template <typename R> int launch_spread(Launcher& L, enuf_plan* pl)
 {
     if (pl->r.T == 16) { DISPATCH_P(16, launch_spread_t, L, pl) }
+    if (pl->r.T == 4) { DISPATCH_P(4, launch_spread_t, L, pl) }
     DISPATCH_P(8, launch_spread_t, L, pl)
 }
 
 template <typename R> int launch_gather(Launcher& L, enuf_plan* pl, int nf, R* F, R* phi)
 {
     if (pl->r.T == 16) { DISPATCH_P(16, launch_gather_t, L, pl, nf, F, phi) }
+    if (pl->r.T == 4) { DISPATCH_P(4, launch_gather_t, L, pl, nf, F, phi) }
     DISPATCH_P(8, launch_gather_t, L, pl, nf, F, phi)
 }
 
@@ -342,20 +349,20 @@ int launch_fft_chain_m(Launcher& L, enuf_plan* pl, int nf)
     {
         const int NT = ffthreads(M / 2), rows = r.gfx.rows;
         const int nblk = (M * M + rows - 1) / rows;
-        LCHK(L.go("fft_x", k_fx<R, M>, dim3(nblk), dim3(rows * NT), (size_t)rows * (M / 2) * vs, at<const R>(pl, y.grid),
+        LCHK(L.go("fft_x", k_fx<R, M>, dim3(nblk), dim3(rows * NT), (size_t)(rows * (M / 2) + M) * vs, at<const R>(pl, y.grid),
                   at<V>(pl, y.C1), r.gfx, W));
     }
     const int NT = ffthreads(M);
     // forward y
     {
         const int Wc = r.gy.W;
-        LCHK(L.go("fft_y", k_fy<R, M>, dim3((r.Kx + Wc - 1) / Wc, M), dim3(Wc * NT), (size_t)Wc * (M + 1) * vs,
+        LCHK(L.go("fft_y", k_fy<R, M>, dim3((r.Kx + Wc - 1) / Wc, M), dim3(Wc * NT), (size_t)(Wc * (M + 1) + M) * vs,
                   at<const V>(pl, y.C1), at<V>(pl, y.C2), r.gy, W));
     }
     // z + reciprocal-space step + inverse z
     {
         const int Wc = r.gz.W;
-        const size_t smem = (size_t)2 * Wc * (M + 1) * vs + 32 * 7 * 8;
+        const size_t smem = (size_t)(2 * Wc * (M + 1) + M) * vs + 32 * 7 * 8 + (size_t)9 * r.Kb * sizeof(R);
         KTables<R> kt;
         kt.tk = at<const R>(pl, y.tk);
         kt.te = at<const R>(pl, y.te);
@@ -379,14 +386,14 @@ int launch_fft_chain_m(Launcher& L, enuf_plan* pl, int nf)
     // inverse y
     {
         const int Wc = r.gy.W;
-        LCHK(L.go("ifft_y", k_iy<R, M>, dim3((r.Kx + Wc - 1) / Wc, M, nf), dim3(Wc * NT), (size_t)Wc * (M + 1) * vs,
+        LCHK(L.go("ifft_y", k_iy<R, M>, dim3((r.Kx + Wc - 1) / Wc, M, nf), dim3(Wc * NT), (size_t)(Wc * (M + 1) + M) * vs,
                   at<const V>(pl, y.C3), at<V>(pl, y.C4), r.gy, W));
     }
     // inverse x (complex to real)
     {
         const int NTh = ffthreads(M / 2), rows = r.gfx.rows;
         const int nrows = nf * M * M;
-        LCHK(L.go("ifft_x", k_ix<R, M>, dim3((nrows + rows - 1) / rows), dim3(rows * NTh), (size_t)rows * (M / 2) * vs,
+        LCHK(L.go("ifft_x", k_ix<R, M>, dim3((nrows + rows - 1) / rows), dim3(rows * NTh), (size_t)(rows * (M / 2) + M) * vs,
                   at<const V>(pl, y.C4), at<R>(pl, y.fld), r.gfx, nrows, W));
     }
     return ENUF_OK;
@@ -502,7 +509,7 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
     fp.sqrt_pi = std::sqrt(kPi);
     fp.kspace_only = konly ? 1 : 0;
     double* o = out ? out : at<double>(pl, y.out);
-    LCHK(L.go("finalize", k_finalize, dim3(1), dim3(256), 0, at<const double>(pl, y.qpart), at<const double>(pl, y.kpart),
+    LCHK(L.go("finalize", k_finalize, dim3(1), dim3(512), 0, at<const double>(pl, y.qpart), at<const double>(pl, y.kpart),
               at<const double>(pl, y.rpart), fp, at<const int>(pl, y.status), o));
     if (want_phi && !konly)
         LCHK(L.go("phi_background", k_phi_background<R>, dim3(nblkN), dim3(256), 0, N, (const double*)o,

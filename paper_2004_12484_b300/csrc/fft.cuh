@@ -142,6 +142,14 @@ __device__ __forceinline__ void fft_smem(V* x, int t, const V* __restrict__ W, i
     FftPasses<V, N, 1, INV>::run(x, t, W, ws);
 }
 
+// Copies the twiddle table exp(-2 pi i k / M), k < M, into shared memory.
+template <typename V>
+__device__ __forceinline__ const V* stage_twiddles(V* dst, const V* __restrict__ src, int M)
+{
+    for (int i = threadIdx.x; i < M; i += blockDim.x) dst[i] = src[i];
+    return dst;
+}
+
 // ---------------------------------------------------------------- geometry
 struct FftGeom {
     int nc;    // retained cutoff
@@ -156,20 +164,21 @@ struct FftGeom {
 // grid: ceil(M*M / rows) blocks, rows * NT(M/2) threads.
 template <typename R, int M>
 __global__ void k_fx(const R* __restrict__ grid, typename Cpx<R>::T* __restrict__ C1, FftGeom g,
-                     const typename Cpx<R>::T* __restrict__ W)
+                     const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
     constexpr int MH = M / 2, NT = FftThreads<MH>::NT;
     extern __shared__ __align__(16) unsigned char smraw[];
     V* s = reinterpret_cast<V*>(smraw);
     const int rows = g.rows, row0 = blockIdx.x * rows, nrows = M * M;
+    const V* sW = stage_twiddles(s + rows * MH, Wg, M);
     const V* gin = reinterpret_cast<const V*>(grid);
     for (int i = threadIdx.x; i < rows * MH; i += blockDim.x) {
         const int r = i / MH, j = i % MH, row = row0 + r;
         s[i] = row < nrows ? gin[(size_t)row * MH + j] : V{R(0), R(0)};
     }
     __syncthreads();
-    fft_smem<V, MH, false>(s + (threadIdx.x / NT) * MH, threadIdx.x % NT, W, 2);
+    fft_smem<V, MH, false>(s + (threadIdx.x / NT) * MH, threadIdx.x % NT, sW, 2);
     const int Kx = g.Kx;
     for (int i = threadIdx.x; i < rows * Kx; i += blockDim.x) {
         const int r = i / Kx, k = i % Kx, row = row0 + r;
@@ -179,7 +188,7 @@ __global__ void k_fx(const R* __restrict__ grid, typename Cpx<R>::T* __restrict_
         const V fe = V{R(0.5) * (zk.x + zc.x), R(0.5) * (zk.y + zc.y)};
         const V d = csub(zk, zc);
         const V fo = V{R(0.5) * d.y, R(-0.5) * d.x};  // -i/2 (zk - zc)
-        C1[(size_t)row * Kx + k] = cadd(fe, cmul(W[k], fo));
+        C1[(size_t)row * Kx + k] = cadd(fe, cmul(sW[k], fo));
     }
 }
 
@@ -187,7 +196,7 @@ __global__ void k_fx(const R* __restrict__ grid, typename Cpx<R>::T* __restrict_
 // grid: (ceil(Kx / W), M) blocks, W * NT(M) threads.
 template <typename R, int M>
 __global__ void k_fy(const typename Cpx<R>::T* __restrict__ C1, typename Cpx<R>::T* __restrict__ C2, FftGeom g,
-                     const typename Cpx<R>::T* __restrict__ W)
+                     const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
     constexpr int NT = FftThreads<M>::NT, LD = M + 1;
@@ -195,12 +204,13 @@ __global__ void k_fy(const typename Cpx<R>::T* __restrict__ C1, typename Cpx<R>:
     V* s = reinterpret_cast<V*>(smraw);
     const int Wc = g.W, Kx = g.Kx, Kb = g.Kb, nc = g.nc;
     const int kx0 = blockIdx.x * Wc, z = blockIdx.y;
+    const V* sW = stage_twiddles(s + Wc * LD, Wg, M);
     for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
         const int w = i % Wc, y = i / Wc, kx = kx0 + w;
         s[w * LD + y] = kx < Kx ? C1[((size_t)z * M + y) * Kx + kx] : V{R(0), R(0)};
     }
     __syncthreads();
-    fft_smem<V, M, false>(s + (threadIdx.x / NT) * LD, threadIdx.x % NT, W, 1);
+    fft_smem<V, M, false>(s + (threadIdx.x / NT) * LD, threadIdx.x % NT, sW, 1);
     for (int i = threadIdx.x; i < Wc * Kb; i += blockDim.x) {
         const int w = i % Wc, kb = i / Wc, kx = kx0 + w;
         if (kx >= Kx) continue;
@@ -228,7 +238,7 @@ template <typename R> struct KTables {
 // (E, Wxx, Wyy, Wzz, Wxy, Wxz, Wyz).  NF = 0 gives the energy only.
 template <typename R, int M, int NF>
 __global__ void k_fz(const typename Cpx<R>::T* __restrict__ C2, typename Cpx<R>::T* __restrict__ C3, FftGeom g,
-                     const typename Cpx<R>::T* __restrict__ W, KTables<R> kt, double* __restrict__ part)
+                     const typename Cpx<R>::T* __restrict__ Wg, KTables<R> ktg, double* __restrict__ part)
 {
     using V = typename Cpx<R>::T;
     constexpr int NT = FftThreads<M>::NT, LD = M + 1;
@@ -237,6 +247,19 @@ __global__ void k_fz(const typename Cpx<R>::T* __restrict__ C2, typename Cpx<R>:
     const int Wc = g.W, Kx = g.Kx, Kb = g.Kb, nc = g.nc, P = g.P;
     V* Y = X + Wc * LD;
     double* red = reinterpret_cast<double*>(Y + Wc * LD);
+    V* sW = reinterpret_cast<V*>(red + 32 * 7);
+    stage_twiddles(sW, Wg, M);
+    R* stab = reinterpret_cast<R*>(sW + M);
+    for (int i = threadIdx.x; i < 3 * Kb; i += blockDim.x) {
+        stab[i] = ktg.tk[i];
+        stab[3 * Kb + i] = ktg.te[i];
+        stab[6 * Kb + i] = ktg.td[i];
+    }
+    KTables<R> kt = ktg;
+    kt.tk = stab;
+    kt.te = stab + 3 * Kb;
+    kt.td = stab + 6 * Kb;
+    const V* W = sW;
     const int p0 = blockIdx.x * Wc;
     for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
         const int w = i % Wc, z = i / Wc, p = p0 + w;
@@ -310,7 +333,7 @@ __global__ void k_fz(const typename Cpx<R>::T* __restrict__ C2, typename Cpx<R>:
 // grid: (ceil(Kx / W), M, NF) blocks, W * NT(M) threads.
 template <typename R, int M>
 __global__ void k_iy(const typename Cpx<R>::T* __restrict__ C3, typename Cpx<R>::T* __restrict__ C4, FftGeom g,
-                     const typename Cpx<R>::T* __restrict__ W)
+                     const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
     constexpr int NT = FftThreads<M>::NT, LD = M + 1;
@@ -318,6 +341,7 @@ __global__ void k_iy(const typename Cpx<R>::T* __restrict__ C3, typename Cpx<R>:
     V* s = reinterpret_cast<V*>(smraw);
     const int Wc = g.W, Kx = g.Kx, Kb = g.Kb, nc = g.nc, P = g.P;
     const int kx0 = blockIdx.x * Wc, z = blockIdx.y, f = blockIdx.z;
+    const V* W = stage_twiddles(s + Wc * LD, Wg, M);
     const V* src = C3 + ((size_t)f * M + z) * P;
     for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
         const int w = i % Wc, y = i / Wc, kx = kx0 + w;
@@ -345,13 +369,15 @@ __global__ void k_iy(const typename Cpx<R>::T* __restrict__ C3, typename Cpx<R>:
 // the Hermitian-completed spectrum.
 template <typename R, int M>
 __global__ void k_ix(const typename Cpx<R>::T* __restrict__ C4, R* __restrict__ fld, FftGeom g, int nrows,
-                     const typename Cpx<R>::T* __restrict__ W)
+                     const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
     constexpr int MH = M / 2, NT = FftThreads<MH>::NT;
     extern __shared__ __align__(16) unsigned char smraw[];
     V* s = reinterpret_cast<V*>(smraw);
     const int rows = g.rows, row0 = blockIdx.x * rows, Kx = g.Kx, nc = g.nc;
+    const V* W = stage_twiddles(s + rows * MH, Wg, M);
+    __syncthreads();
     for (int i = threadIdx.x; i < rows * MH; i += blockDim.x) {
         const int r = i / MH, k = i % MH, row = row0 + r;
         V z = V{R(0), R(0)};

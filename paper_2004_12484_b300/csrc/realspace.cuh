@@ -135,33 +135,32 @@ struct FinalParams {
     int kspace_only;
 };
 
-// One block of 256 threads.  Sums the per-block partials in a fixed order
-// (deterministic), adds the self energy (Eq. 24) and the background term,
-// writes the ENUF_NOUT results.
-__global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ qpart, const double* __restrict__ kpart,
+// One block of 512 threads (16 warps): warp w sums quantity w over all
+// per-block partials in a fixed order (lane-strided, then a fixed shuffle
+// tree), so the result is deterministic.  Adds the self energy (Eq. 24) and
+// the background term and writes the ENUF_NOUT results.
+__global__ void __launch_bounds__(512) k_finalize(const double* __restrict__ qpart, const double* __restrict__ kpart,
                                                   const double* __restrict__ rpart, FinalParams fp,
                                                   const int* __restrict__ status, double* __restrict__ out)
 {
-    __shared__ double s[256][16];
-    double a[16];
-#pragma unroll
-    for (int k = 0; k < 16; k++) a[k] = 0.0;
-    for (int b = threadIdx.x; b < fp.nq; b += blockDim.x) { a[0] += qpart[2 * b]; a[1] += qpart[2 * b + 1]; }
-    for (int b = threadIdx.x; b < fp.nk; b += blockDim.x)
-        for (int k = 0; k < 7; k++) a[2 + k] += kpart[8 * b + k];
-    for (int b = threadIdx.x; b < fp.nr; b += blockDim.x)
-        for (int k = 0; k < 7; k++) a[9 + k] += rpart[8 * b + k];
-    for (int k = 0; k < 16; k++) s[threadIdx.x][k] = a[k];
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o)
-            for (int k = 0; k < 16; k++) s[threadIdx.x][k] += s[threadIdx.x + o][k];
-        __syncthreads();
+    __shared__ double s[16];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double a = 0.0;
+    if (w < 2) {
+        for (int b = lane; b < fp.nq; b += 32) a += qpart[2 * b + w];
+    } else if (w < 9) {
+        for (int b = lane; b < fp.nk; b += 32) a += kpart[8 * b + (w - 2)];
+    } else {
+        for (int b = lane; b < fp.nr; b += 32) a += rpart[8 * b + (w - 9)];
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) s[w] = a;
+    __syncthreads();
     if (threadIdx.x == 0) {
-        const double q2 = s[0][0], Q = s[0][1];
-        const double Ek = s[0][2];
-        const double Er = fp.nr ? fp.ke * s[0][9] : 0.0;
+        const double q2 = s[0], Q = s[1];
+        const double Ek = s[2];
+        const double Er = fp.nr ? fp.ke * s[9] : 0.0;
         double Es = 0.0, Eb = 0.0;
         if (!fp.kspace_only) {
             Es = -fp.ke * fp.alpha / fp.sqrt_pi * q2;
@@ -169,7 +168,7 @@ __global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ qpa
         }
         // virial components (xx, yy, zz, xy, xz, yz) -> row-major 3x3
         double w6[6];
-        for (int k = 0; k < 6; k++) w6[k] = s[0][3 + k] + (fp.nr ? fp.ke * s[0][10 + k] : 0.0);
+        for (int k = 0; k < 6; k++) w6[k] = s[3 + k] + (fp.nr ? fp.ke * s[10 + k] : 0.0);
         out[0] = fp.kspace_only ? Ek : (Er + Ek + Es + Eb);
         out[1] = Er;
         out[2] = Ek;

@@ -10,11 +10,12 @@
 //
 // Both kernels process one work item = (tile, particle range) per CTA.  A
 // tile is T^3 grid cells; its particles were counting-sorted into it.  The
-// CTA owns a padded shared-memory box of (T+p-1)^3 cells covering every cell
-// the tile's particles touch.  Spreading accumulates into that box with
-// shared-memory atomics and flushes it with one global atomic add per
-// non-zero cell.  Interpolation stages the box of every field once and then
-// reads only shared memory.  Inside a CTA, a group of G >= p lanes serves one
+// CTA owns a padded shared-memory box covering every cell the tile's
+// particles touch (T+p-1 cells in y and z; in x widened to 16-byte aligned
+// rows).  Spreading accumulates into that box with shared-memory atomics and
+// flushes it with one global vector atomic per non-zero aligned group of four
+// cells (scalar atomics in double).  Interpolation stages the box of every
+// field with 16-byte loads and then reads only shared memory.  Inside a CTA, a group of G >= p lanes serves one
 // particle: lane a takes the x-offset a, so a group reads or writes p
 // consecutive cells of one grid row per step (no bank conflicts inside the
 // group); the group's partial sums are combined with shuffles.
@@ -50,17 +51,31 @@ __device__ __forceinline__ void split_offset(R o, int& i, R& d)
     d = o - (R)c;
 }
 
+// Shared-memory box of a tile: x from tile_x0 - XA to tile_x0 - XA + BX
+// (XA >= m - 1 and BX multiples of 4 so that rows start on 16-byte
+// boundaries in global memory), y and z from tile origin - (m - 1) over
+// PT = T + p - 1 cells.
+template <int P, int T> struct Box {
+    static constexpr int m = P / 2;
+    static constexpr int XA = (m - 1 + 3) / 4 * 4;
+    static constexpr int BX = (XA + T + m + 3) / 4 * 4;
+    static constexpr int PT = T + P - 1;
+    static constexpr int CELLS = BX * PT * PT;
+    static constexpr int XOFF = XA - (m - 1);  // box x of window point 0 minus floor(u)
+};
+
 template <typename R, int P, int T>
 __global__ void __launch_bounds__(256) k_spread(const int4* __restrict__ work, const int* __restrict__ nwork,
                                                 const typename Rec<R>::T* __restrict__ rec, int M, int nbx,
                                                 int nby, R inv_b, R cnorm3, R* __restrict__ grid)
 {
-    constexpr int PT = T + P - 1, m = P / 2, G = GroupOf<P>::G;
+    using B = Box<P, T>;
+    constexpr int PT = B::PT, BX = B::BX, m = P / 2, G = GroupOf<P>::G;
     extern __shared__ __align__(16) unsigned char smraw[];
     R* acc = reinterpret_cast<R*>(smraw);
     if ((int)blockIdx.x >= *nwork) return;  // uniform for the whole CTA
     const int4 w = work[blockIdx.x];
-    for (int i = threadIdx.x; i < PT * PT * PT; i += blockDim.x) acc[i] = R(0);
+    for (int i = threadIdx.x; i < B::CELLS; i += blockDim.x) acc[i] = R(0);
     __syncthreads();
 
     const int lane = threadIdx.x % G, grp = threadIdx.x / G, ngrp = blockDim.x / G;
@@ -77,12 +92,12 @@ __global__ void __launch_bounds__(256) k_spread(const int4* __restrict__ work, c
         if (lane < P) {
             R u = dx + (R)(m - 1 - lane);
             const R wx = r.w * cnorm3 * dexp(-u * u * inv_b);
-            R* base = acc + (iz * PT + iy) * PT + ix + lane;
+            R* base = acc + (iz * PT + iy) * BX + ix + lane + B::XOFF;
 #pragma unroll
             for (int c = 0; c < P; c++) {
                 const R wxz = wx * wz[c];
 #pragma unroll
-                for (int b = 0; b < P; b++) atomicAdd(base + (c * PT + b) * PT, wxz * wy[b]);
+                for (int b = 0; b < P; b++) atomicAdd(base + (c * PT + b) * BX, wxz * wy[b]);
             }
         }
     }
@@ -90,14 +105,27 @@ __global__ void __launch_bounds__(256) k_spread(const int4* __restrict__ work, c
 
     const int tile = w.x;
     const int tx = tile % nbx, ty = (tile / nbx) % nby, tz = tile / (nbx * nby);
-    const int ox = tx * T - (m - 1), oy = ty * T - (m - 1), oz = tz * T - (m - 1);
-    const int mask = M - 1;  // M is a power of two
-    for (int i = threadIdx.x; i < PT * PT * PT; i += blockDim.x) {
-        const R v = acc[i];
-        if (v != R(0)) {
-            const int lx = i % PT, ly = (i / PT) % PT, lz = i / (PT * PT);
-            const int gx = (ox + lx) & mask, gy = (oy + ly) & mask, gz = (oz + lz) & mask;
-            atomicAdd(grid + ((size_t)gz * M + gy) * M + gx, v);
+    const int ox = tx * T - B::XA, oy = ty * T - (m - 1), oz = tz * T - (m - 1);
+    const int mask = M - 1;  // M is a power of two (and a multiple of 4)
+    if constexpr (sizeof(R) == 4) {
+        // one 16-byte vector atomic per aligned group of 4 cells
+        constexpr int NV = BX / 4;
+        for (int i = threadIdx.x; i < NV * PT * PT; i += blockDim.x) {
+            const int vx = i % NV, ly = (i / NV) % PT, lz = i / (NV * PT);
+            const float4 v = *reinterpret_cast<const float4*>(acc + (lz * PT + ly) * BX + 4 * vx);
+            if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) {
+                const int gx = (ox + 4 * vx) & mask, gy = (oy + ly) & mask, gz = (oz + lz) & mask;
+                atomicAdd(reinterpret_cast<float4*>(grid + ((size_t)gz * M + gy) * M + gx), v);
+            }
+        }
+    } else {
+        for (int i = threadIdx.x; i < B::CELLS; i += blockDim.x) {
+            const R v = acc[i];
+            if (v != R(0)) {
+                const int lx = i % BX, ly = (i / BX) % PT, lz = i / (BX * PT);
+                const int gx = (ox + lx) & mask, gy = (oy + ly) & mask, gz = (oz + lz) & mask;
+                atomicAdd(grid + ((size_t)gz * M + gy) * M + gx, v);
+            }
         }
     }
 }
@@ -113,21 +141,27 @@ __global__ void __launch_bounds__(256) k_gather(const int4* __restrict__ work, c
                                                 R inv_b, R cnorm3, const R* __restrict__ fld, R* __restrict__ F,
                                                 R* __restrict__ phi)
 {
-    constexpr int PT = T + P - 1, PT3 = PT * PT * PT, m = P / 2, G = GroupOf<P>::G;
+    using B = Box<P, T>;
+    constexpr int PT = B::PT, BX = B::BX, C = B::CELLS, m = P / 2, G = GroupOf<P>::G;
     extern __shared__ __align__(16) unsigned char smraw[];
     R* s = reinterpret_cast<R*>(smraw);
     if ((int)blockIdx.x >= *nwork) return;
     const int4 w = work[blockIdx.x];
     const int tile = w.x;
     const int tx = tile % nbx, ty = (tile / nbx) % nby, tz = tile / (nbx * nby);
-    const int ox = tx * T - (m - 1), oy = ty * T - (m - 1), oz = tz * T - (m - 1);
+    const int ox = tx * T - B::XA, oy = ty * T - (m - 1), oz = tz * T - (m - 1);
     const int mask = M - 1;
     const size_t M3 = (size_t)M * M * M;
-    for (int i = threadIdx.x; i < PT3; i += blockDim.x) {
-        const int lx = i % PT, ly = (i / PT) % PT, lz = i / (PT * PT);
-        const size_t gi = ((size_t)((oz + lz) & mask) * M + ((oy + ly) & mask)) * M + ((ox + lx) & mask);
+    // stage the box of every field with 16-byte loads
+    constexpr int EV = 16 / sizeof(R);  // elements per 16-byte vector
+    constexpr int NV = BX / EV;
+    for (int i = threadIdx.x; i < NV * PT * PT; i += blockDim.x) {
+        const int vx = i % NV, ly = (i / NV) % PT, lz = i / (NV * PT);
+        const size_t gi = ((size_t)((oz + lz) & mask) * M + ((oy + ly) & mask)) * M + ((ox + EV * vx) & mask);
+        const int si = (lz * PT + ly) * BX + EV * vx;
 #pragma unroll
-        for (int f = 0; f < NF; f++) s[f * PT3 + i] = fld[f * M3 + gi];
+        for (int f = 0; f < NF; f++)
+            *reinterpret_cast<float4*>(s + f * C + si) = __ldg(reinterpret_cast<const float4*>(fld + f * M3 + gi));
     }
     __syncthreads();
 
@@ -149,16 +183,16 @@ __global__ void __launch_bounds__(256) k_gather(const int4* __restrict__ work, c
         if (lane < P) {
             R u = dx + (R)(m - 1 - lane);
             const R wx = dexp(-u * u * inv_b);
-            const R* base = s + (iz * PT + iy) * PT + ix + lane;
+            const R* base = s + (iz * PT + iy) * BX + ix + lane + B::XOFF;
 #pragma unroll
             for (int c = 0; c < P; c++) {
                 const R wxz = wx * wz[c];
 #pragma unroll
                 for (int b = 0; b < P; b++) {
                     const R ww = wxz * wy[b];
-                    const int o = (c * PT + b) * PT;
+                    const int o = (c * PT + b) * BX;
 #pragma unroll
-                    for (int f = 0; f < NF; f++) acc[f] += ww * base[f * PT3 + o];
+                    for (int f = 0; f < NF; f++) acc[f] += ww * base[f * C + o];
                 }
             }
         }
