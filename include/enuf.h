@@ -158,6 +158,35 @@ int enuf_last_timings(enuf_plan* plan, const char** names, float* times_ms, int 
  * (memset nodes not counted). */
 int enuf_launch_count(enuf_plan* plan, int flags, int with_forces);
 
+/* Real-space part only (the pair sum of Eq. 17 / Eq. 29), for callers that
+ * cannot allocate device memory: code running inside a framework whose
+ * device memory is reserved by its own pool allocator, plugins handed only
+ * their input and output buffers, or code that must not allocate (and so
+ * possibly synchronise or fail) after set-up.  The paper has no counterpart
+ * of this entry point; it is a variant of the library's all-pairs real-space
+ * kernel that allocates nothing: it reads the raw positions (no sorting) and
+ * keeps its only scratch, per-block partial sums and a completion counter, in
+ * a fixed array in device memory that every GPU loading the library holds
+ * until the process exits.
+ *   pos, q: N x 3 and N inputs (device; float for ENUF_MIXED, double for
+ *   ENUF_FP64).  L: 3 box edges (host).  r_c <= min(L)/2 (minimum image).
+ *   F, phi: N x 3 and N outputs (device, may be NULL): the pair force
+ *   coulomb_k q_i sum_j ... and the pair potential coulomb_k sum_j q_j
+ *   erfc(alpha r)/r, written, not accumulated.  out: 10 doubles (device):
+ *   E_real followed by the 9 entries of its virial, row-major.
+ *   cuda_stream: cudaStream_t the work is ordered on (NULL = legacy stream).
+ * Limits and behaviour: N <= 262,144 (the fixed scratch holds 1024 blocks of
+ * 256 particles); larger N returns ENUF_EUNSUPPORTED with a message.  The
+ * cost grows as N^2.  The first call on each device looks up the scratch
+ * array's device address (cudaGetSymbolAddress with that device current);
+ * make that first call before any stream capture.  All calls on a device
+ * share the scratch, so calls whose kernels overlap on the GPU (different
+ * streams, or different host threads) race and give wrong results; order
+ * them.  Each call clears the counter it needs before its kernel runs.
+ * Asynchronous; errors are reported by the return code and enuf_last_error. */
+int enuf_real_space_noalloc(const void* pos, const void* q, int64_t N, const double* L, double alpha, double r_c,
+                            double coulomb_k, int precision, void* F, void* phi, double* out, void* cuda_stream);
+
 /* Thread-local description of the last failure ("" if none). */
 const char* enuf_last_error(void);
 

@@ -78,6 +78,9 @@ def lib():
         L.enuf_backward.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
         L.enuf_last_timings.argtypes = [_vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float), ctypes.c_int]
         L.enuf_launch_count.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
+        L.enuf_real_space_noalloc.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                              _vp, _vp, _vp, _vp]
         _lib = L
     return _lib
 
@@ -262,6 +265,31 @@ class Plan:
         if n < 0:
             _check(n)
         return [(names[i].decode(), float(times[i])) for i in range(n)]
+
+
+def real_space_noalloc(pos, q, L, alpha, r_c, coulomb_k=1.0, F=None, phi=None, out=None):
+    """Real-space pair sum through the entry point that allocates no device
+    memory inside the library (for callers that cannot allocate; see
+    include/enuf.h).  pos, q: float32 or float64 CUDA tensors.  Returns
+    (out[10] = E_real and its virial, F, phi) on the device; asynchronous on
+    the current stream.  Buffers not given are allocated here by torch, in
+    the caller's process, before the call."""
+    import torch
+    dt = pos.dtype
+    prec = FP64 if dt == torch.float64 else MIXED
+    N = q.shape[0]
+    if F is None:
+        F = torch.empty((N, 3), dtype=dt, device=pos.device)
+    if phi is None:
+        phi = torch.empty((N,), dtype=dt, device=pos.device)
+    if out is None:
+        out = torch.empty((10,), dtype=torch.float64, device=pos.device)
+    Lv = (ctypes.c_double * 3)(*[float(x) for x in np.broadcast_to(np.asarray(L, dtype=np.float64).reshape(-1), (3,))])
+    _check(lib().enuf_real_space_noalloc(_vp(pos.data_ptr()), _vp(q.data_ptr()), int(N), Lv, float(alpha),
+                                         float(r_c), float(coulomb_k), prec, _vp(F.data_ptr()),
+                                         _vp(phi.data_ptr()), _vp(out.data_ptr()),
+                                         _vp(torch.cuda.current_stream(pos.device).cuda_stream)))
+    return out, F, phi
 
 
 def _autograd():

@@ -664,6 +664,12 @@ int check_status(const double* parts)
 
 }  // namespace
 
+namespace enuf {
+// Lets the other translation unit of the library report through
+// enuf_last_error().
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace enuf
+
 // ====================================================================== C ABI
 extern "C" {
 
