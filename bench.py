@@ -116,6 +116,8 @@ def algorithmic_bytes(kernel, N, M, nc, nf, rs=4):
         "scatter": (4 + 4 + rec) * N + (rec + 4) * N,
         "spread": rec * N + rs * M3,
         "fft_x": rs * M3 + vs * M * M * Kx,
+        "fft_xy": rs * M3 + vs * M * P,
+        "ifft_yx": nf * vs * M * P + nf * rs * M3,
         "fft_y": vs * M * M * Kx + vs * M * P,
         "fft_z_kspace": vs * M * P * (1 + nf),
         "ifft_y": nf * vs * M * P + nf * vs * M * M * Kx,

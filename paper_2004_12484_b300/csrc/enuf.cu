@@ -66,9 +66,14 @@ struct Resolved {
     int ncell[3], nrbins;
     double h[3];
     FftGeom gfx, gy, gz;
+    int fxy_threads;  // > 0: fused x-y kernels with this block size
+    size_t fxy_smem;
+    bool gather_direct;  // interpolate straight from L2-resident field planes
 };
 
 int ffthreads(int n) { return n >= 8 ? n / 8 : 1; }
+// slots of one transform of length n in shared memory (PadLen in fft.cuh)
+int padlen(int n) { return n + n / 16; }
 
 int resolve(const enuf_params* in, Resolved& r)
 {
@@ -130,17 +135,35 @@ int resolve(const enuf_params* in, Resolved& r)
         int nch = (r.Kx + 15) / 16;
         int W = round_up((r.Kx + nch - 1) / nch, gran);
         while (W * NT > 1024) W -= gran;
-        while ((size_t)(W * (M + 1) + M) * vsz > (size_t)kMaxSmem) W -= gran;
+        while ((size_t)(W * (padlen(M) + 1) + M) * vsz > (size_t)kMaxSmem) W -= gran;
         r.gy = FftGeom{r.nc, r.Kx, r.Kb, r.P, W, 0};
     }
     // k_fz: pencils per block
     {
         int W = round_up(16, gran);
         while (W * NT > 1024) W -= gran;
-        while ((size_t)(2 * W * (M + 1) + M) * vsz + 32 * 7 * 8 + (size_t)9 * r.Kb * r.rsz > (size_t)kMaxSmem) W -= gran;
+        while ((size_t)(4 * W * (padlen(M) + 1) + M) * vsz + 32 * 7 * 8 + (size_t)9 * r.Kb * r.rsz > (size_t)kMaxSmem) W -= gran;
         r.gz = FftGeom{r.nc, r.Kx, r.Kb, r.P, W, 0};
     }
     if (r.gy.W < 1 || r.gz.W < 1) return fail(ENUF_EUNSUPPORTED, "FFT block shape does not fit");
+    // the four field planes stay in L2 (126 MB) when they total <= 64 MB
+    r.gather_direct = (size_t)4 * M * M * M * r.rsz <= (size_t)64 << 20 && !std::getenv("ENUF_STAGED_GATHER");
+    // fused x-y passes (one CTA per z-plane) where the pruned plane fits
+    r.fxy_threads = 0;
+    r.fxy_smem = 0;
+    if (M >= 32 && M <= 256) {
+        const int NTX = ffthreads(M / 2), NTY = ffthreads(M);
+        for (int t : {1024, 512, 256}) {
+            if (t > M * NTX || t % 32 || t < NTY) continue;
+            const int RB = t / NTX, CB = t / NTY, KxR = (r.Kx + CB - 1) / CB * CB;
+            const size_t sm = ((size_t)RB * padlen(M / 2) + (size_t)KxR * (padlen(M) + 1) + M) * vsz;
+            if (sm <= (size_t)kMaxSmem) {
+                r.fxy_threads = t;
+                r.fxy_smem = sm;
+                break;
+            }
+        }
+    }
     return ENUF_OK;
 }
 
@@ -148,7 +171,7 @@ int resolve(const enuf_params* in, Resolved& r)
 struct Layout {
     size_t status, out, mean;
     size_t counts, offsets, work, nwork;
-    size_t key, rank, rec_tmp, rec, perm;
+    size_t key, rank, rec_tmp, rec, perm, tile_of;
     size_t rcounts, roffsets, rrec, rperm, rcell;
     size_t qpart, kpart, rpart, fpart;
     size_t twid, tk, te, td;
@@ -182,6 +205,7 @@ Layout layout(const Resolved& r)
     L.rec_tmp = take(N * recsz);
     L.rec = take(N * recsz);
     L.perm = take(N * 4);
+    L.tile_of = take(N * 4);
     L.rcounts = take((r.nrbins + 1) * 4);
     L.roffsets = take((r.nrbins + 1) * 4);
     L.rrec = take(N * recsz);
@@ -234,16 +258,27 @@ struct enuf_plan {
     unsigned long long stamp = 0;
     // derived constants
     double b = 0, inv_b = 0, cnorm3 = 0;
+    int lnb = 0;  // log2 of tiles per dimension
     // profiling
     std::vector<std::string> tnames;
     std::vector<cudaEvent_t> tevents;
     std::vector<float> ttimes;
-    int nrec = 0;
+    cudaGraphExec_t prof_exec = nullptr;
 };
 
 namespace {
 
 template <typename T> T* at(enuf_plan* pl, size_t off) { return reinterpret_cast<T*>(pl->ws + off); }
+
+// Window constants for the kernels: 1/b and exp(-a^2/b), a < 16 (computed in
+// double on the host, rounded to the kernel's type).
+template <typename R> WinC<R> winc(const enuf_plan* pl)
+{
+    WinC<R> w{};
+    w.inv_b = (R)pl->inv_b;
+    for (int a = 0; a < 16; a++) w.c[a] = (R)std::exp(-(double)a * a * pl->inv_b);
+    return w;
+}
 
 // ------------------------------------------------------------------ launching
 struct Launcher {
@@ -260,11 +295,8 @@ struct Launcher {
             if (e != cudaSuccess) return fail(ENUF_ECUDA, std::string("cudaFuncSetAttribute(") + name + "): " + cudaGetErrorString(e));
         }
         if (attr_only) { count++; return ENUF_OK; }
-        if (pl->profile) {
-            cudaEvent_t e0;
-            cudaEventCreate(&e0);
-            cudaEventRecord(e0, st);
-            pl->tevents.push_back(e0);
+        if (pl->profile && pl->tnames.size() + 1 < pl->tevents.size()) {
+            CK(cudaEventRecordWithFlags(pl->tevents[pl->tnames.size()], st, cudaEventRecordExternal));
             pl->tnames.push_back(name);
         }
         k<<<grid, block, smem, st>>>(args...);
@@ -294,7 +326,7 @@ int launch_spread_t(Launcher& L, enuf_plan* pl)
     const Layout& y = pl->lay;
     return L.go("spread", k_spread<R, P, T>, dim3(r.max_work), dim3(256), (size_t)Box<P, T>::CELLS * sizeof(R),
                 at<const int4>(pl, y.work), at<const int>(pl, y.nwork), at<const typename Rec<R>::T>(pl, y.rec),
-                r.prm.M, r.nbt[0], r.nbt[1], (R)pl->inv_b, (R)pl->cnorm3, at<R>(pl, y.grid));
+                r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), (R)pl->cnorm3, at<R>(pl, y.grid));
 }
 
 template <typename R, int P, int T>
@@ -302,14 +334,28 @@ int launch_gather_t(Launcher& L, enuf_plan* pl, int nf, R* F, R* phi)
 {
     const Resolved& r = pl->r;
     const Layout& y = pl->lay;
+    if (r.gather_direct) {
+        constexpr int G = GroupOf<P>::G;
+        const int N = (int)r.prm.N;
+        const dim3 grid((unsigned)(((size_t)N * G + 255) / 256));
+        if (nf == 4)
+            return L.go("gather", k_gather_direct<R, P, T, 4>, grid, dim3(256), 0, N,
+                        at<const typename Rec<R>::T>(pl, y.rec), at<const uint32_t>(pl, y.tile_of),
+                        at<const uint32_t>(pl, y.perm), r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), (R)pl->cnorm3,
+                        at<const R>(pl, y.fld), F, phi);
+        return L.go("gather", k_gather_direct<R, P, T, 3>, grid, dim3(256), 0, N,
+                    at<const typename Rec<R>::T>(pl, y.rec), at<const uint32_t>(pl, y.tile_of),
+                    at<const uint32_t>(pl, y.perm), r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), (R)pl->cnorm3,
+                    at<const R>(pl, y.fld), F, phi);
+    }
     const size_t smem = (size_t)nf * Box<P, T>::CELLS * sizeof(R);
     if (nf == 4)
         return L.go("gather", k_gather<R, P, T, 4>, dim3(r.max_work), dim3(256), smem, at<const int4>(pl, y.work),
                     at<const int>(pl, y.nwork), at<const typename Rec<R>::T>(pl, y.rec), at<const uint32_t>(pl, y.perm),
-                    r.prm.M, r.nbt[0], r.nbt[1], (R)pl->inv_b, (R)pl->cnorm3, at<const R>(pl, y.fld), F, phi);
+                    r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), (R)pl->cnorm3, at<const R>(pl, y.fld), F, phi);
     return L.go("gather", k_gather<R, P, T, 3>, dim3(r.max_work), dim3(256), smem, at<const int4>(pl, y.work),
                 at<const int>(pl, y.nwork), at<const typename Rec<R>::T>(pl, y.rec), at<const uint32_t>(pl, y.perm),
-                r.prm.M, r.nbt[0], r.nbt[1], (R)pl->inv_b, (R)pl->cnorm3, at<const R>(pl, y.fld), F, phi);
+                r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), (R)pl->cnorm3, at<const R>(pl, y.fld), F, phi);
 }
 
 #define DISPATCH_P(T_, FN, ...)                                           \
@@ -345,24 +391,29 @@ int launch_fft_chain_m(Launcher& L, enuf_plan* pl, int nf)
     const Layout& y = pl->lay;
     const V* W = at<const V>(pl, y.twid);
     const size_t vs = sizeof(V);
+    const bool fused = r.fxy_threads > 0 && !std::getenv("ENUF_NO_FUSED_XY");
+    if (fused) {
+        LCHK(L.go("fft_xy", k_fxy<R, M>, dim3(M), dim3(r.fxy_threads), r.fxy_smem, at<const R>(pl, y.grid),
+                  at<V>(pl, y.C2), r.gy, W));
+    }
     // forward x
-    {
+    if (!fused) {
         const int NT = ffthreads(M / 2), rows = r.gfx.rows;
         const int nblk = (M * M + rows - 1) / rows;
-        LCHK(L.go("fft_x", k_fx<R, M>, dim3(nblk), dim3(rows * NT), (size_t)(rows * (M / 2) + M) * vs, at<const R>(pl, y.grid),
+        LCHK(L.go("fft_x", k_fx<R, M>, dim3(nblk), dim3(rows * NT), (size_t)(rows * padlen(M / 2) + M) * vs, at<const R>(pl, y.grid),
                   at<V>(pl, y.C1), r.gfx, W));
     }
     const int NT = ffthreads(M);
     // forward y
-    {
+    if (!fused) {
         const int Wc = r.gy.W;
-        LCHK(L.go("fft_y", k_fy<R, M>, dim3((r.Kx + Wc - 1) / Wc, M), dim3(Wc * NT), (size_t)(Wc * (M + 1) + M) * vs,
+        LCHK(L.go("fft_y", k_fy<R, M>, dim3((r.Kx + Wc - 1) / Wc, M), dim3(Wc * NT), (size_t)(Wc * (padlen(M) + 1) + M) * vs,
                   at<const V>(pl, y.C1), at<V>(pl, y.C2), r.gy, W));
     }
     // z + reciprocal-space step + inverse z
     {
         const int Wc = r.gz.W;
-        const size_t smem = (size_t)(2 * Wc * (M + 1) + M) * vs + 32 * 7 * 8 + (size_t)9 * r.Kb * sizeof(R);
+        const size_t smem = (size_t)(std::max(nf, 1) * Wc * (padlen(M) + 1) + M) * vs + 32 * 7 * 8 + (size_t)9 * r.Kb * sizeof(R);
         KTables<R> kt;
         kt.tk = at<const R>(pl, y.tk);
         kt.te = at<const R>(pl, y.te);
@@ -383,17 +434,21 @@ int launch_fft_chain_m(Launcher& L, enuf_plan* pl, int nf)
                       W, kt, at<double>(pl, y.kpart)));
     }
     if (nf == 0) return ENUF_OK;
+    if (fused) {
+        return L.go("ifft_yx", k_iyx<R, M>, dim3(M, nf), dim3(r.fxy_threads), r.fxy_smem, at<const V>(pl, y.C3),
+                    at<R>(pl, y.fld), r.gy, W);
+    }
     // inverse y
     {
         const int Wc = r.gy.W;
-        LCHK(L.go("ifft_y", k_iy<R, M>, dim3((r.Kx + Wc - 1) / Wc, M, nf), dim3(Wc * NT), (size_t)(Wc * (M + 1) + M) * vs,
+        LCHK(L.go("ifft_y", k_iy<R, M>, dim3((r.Kx + Wc - 1) / Wc, M, nf), dim3(Wc * NT), (size_t)(Wc * (padlen(M) + 1) + M) * vs,
                   at<const V>(pl, y.C3), at<V>(pl, y.C4), r.gy, W));
     }
     // inverse x (complex to real)
     {
         const int NTh = ffthreads(M / 2), rows = r.gfx.rows;
         const int nrows = nf * M * M;
-        LCHK(L.go("ifft_x", k_ix<R, M>, dim3((nrows + rows - 1) / rows), dim3(rows * NTh), (size_t)(rows * (M / 2) + M) * vs,
+        LCHK(L.go("ifft_x", k_ix<R, M>, dim3((nrows + rows - 1) / rows), dim3(rows * NTh), (size_t)(rows * padlen(M / 2) + M) * vs,
                   at<const V>(pl, y.C4), at<R>(pl, y.fld), r.gfx, nrows, W));
     }
     return ENUF_OK;
@@ -454,7 +509,7 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
               at<int>(pl, y.status)));
     LCHK(L.go("scatter", k_scatter<R>, dim3(nblkN), dim3(256), 0, N, at<const uint32_t>(pl, y.key),
               at<const uint32_t>(pl, y.rank), at<const uint32_t>(pl, y.offsets), at<const RecT>(pl, y.rec_tmp),
-              at<RecT>(pl, y.rec), at<uint32_t>(pl, y.perm), (uint32_t*)nullptr));
+              at<RecT>(pl, y.rec), at<uint32_t>(pl, y.perm), at<uint32_t>(pl, y.tile_of)));
     // (a3) spread
     const size_t M3 = (size_t)r.prm.M * r.prm.M * r.prm.M;
     LCHK(L.memset(at<void>(pl, y.grid), M3 * sizeof(R)));
@@ -610,19 +665,31 @@ int compute_impl(enuf_plan* pl, const void* pos, const void* q, void* F, void* p
     if (flags & ~(ENUF_WANT_VIRIAL | ENUF_WANT_PHI | ENUF_REMOVE_NET_FORCE | ENUF_KSPACE_ONLY))
         return fail(ENUF_EINVAL, "unknown flag bits");
     if (!(flags & ENUF_WANT_PHI)) phi = nullptr;
-    if (pl->profile || !pl->use_graph) {
-        for (auto e : pl->tevents) cudaEventDestroy(e);
-        pl->tevents.clear();
-        pl->tnames.clear();
-        int rc = run_sequence(pl, pl->stream, false, pos, q, F, phi, out, flags);
-        if (pl->profile) {
-            cudaEvent_t e1;
-            cudaEventCreate(&e1);
-            cudaEventRecord(e1, pl->stream);
-            pl->tevents.push_back(e1);
+    if (pl->profile) {
+        // a fresh graph per call with an event-record node before every
+        // kernel and one after the last, so kernel times carry no launch gaps
+        if (pl->prof_exec) {
+            cudaGraphExecDestroy(pl->prof_exec);
+            pl->prof_exec = nullptr;
         }
-        return rc;
+        pl->tnames.clear();
+        cudaGraph_t graph;
+        CK(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal));
+        int rc = run_sequence(pl, pl->cap_stream, false, pos, q, F, phi, out, flags);
+        if (rc == ENUF_OK) cudaEventRecordWithFlags(pl->tevents[pl->tnames.size()], pl->cap_stream, cudaEventRecordExternal);
+        cudaError_t e = cudaStreamEndCapture(pl->cap_stream, &graph);
+        if (rc != ENUF_OK) {
+            if (e == cudaSuccess) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(ENUF_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&pl->prof_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(ENUF_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+        CK(cudaGraphLaunch(pl->prof_exec, pl->stream));
+        return ENUF_OK;
     }
+    if (!pl->use_graph) return run_sequence(pl, pl->stream, false, pos, q, F, phi, out, flags);
     for (auto& g : pl->graphs) {
         if (g.pos == pos && g.q == q && g.F == F && g.phi == phi && g.out == out && g.flags == flags) {
             g.stamp = ++pl->stamp;
@@ -701,10 +768,15 @@ int enuf_plan_create(const enuf_params* params, void* cuda_stream, int allocate,
     pl->b = 2.0 * sigma * m / ((2.0 * sigma - 1.0) * kPi);
     pl->inv_b = 1.0 / pl->b;
     pl->cnorm3 = std::pow(kPi * pl->b, -1.5);
+    while ((1 << pl->lnb) < r.nbt[0]) pl->lnb++;
     const char* ev = std::getenv("ENUF_NO_GRAPH");
     pl->use_graph = !(ev && ev[0] == '1');
     ev = std::getenv("ENUF_PROFILE");
     pl->profile = ev && ev[0] == '1';
+    if (pl->profile) {
+        pl->tevents.resize(48);
+        for (auto& x : pl->tevents) cudaEventCreate(&x);
+    }
     cudaError_t e = cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete pl;
@@ -761,6 +833,7 @@ int enuf_plan_destroy(enuf_plan* pl)
 {
     if (!pl) return ENUF_OK;
     drop_graphs(pl);
+    if (pl->prof_exec) cudaGraphExecDestroy(pl->prof_exec);
     for (auto e : pl->tevents) cudaEventDestroy(e);
     if (pl->own_ws && pl->ws) cudaFree(pl->ws);
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
@@ -833,9 +906,9 @@ int enuf_backward(enuf_plan* pl, const void* pos, const void* q, const double* g
 int enuf_last_timings(enuf_plan* pl, const char** names, float* times_ms, int cap)
 {
     if (!pl) return fail(ENUF_EINVAL, "plan is NULL");
-    if (!pl->profile || pl->tevents.size() < 2) return 0;
-    CK(cudaEventSynchronize(pl->tevents.back()));
     const int n = (int)pl->tnames.size();
+    if (!pl->profile || n == 0) return 0;
+    CK(cudaEventSynchronize(pl->tevents[n]));
     pl->ttimes.assign(n, 0.f);
     for (int i = 0; i < n; i++) cudaEventElapsedTime(&pl->ttimes[i], pl->tevents[i], pl->tevents[i + 1]);
     const int m = std::min(n, cap);

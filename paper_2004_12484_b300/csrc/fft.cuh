@@ -85,32 +85,49 @@ template <int N> struct FftThreads {
     static constexpr int NT = N >= 8 ? N / 8 : 1;
 };
 
-// One Stockham pass of radix R on a contiguous transform of length N in
-// shared memory, served by NT = max(1, N/8) threads (t = 0..NT-1).  All
-// threads of the CTA must call it (it contains barriers).  W is the table
-// exp(-2 pi i k / Mtab), k < Mtab, and ws = Mtab / N.
-template <typename V, int N, int R, int Ns, bool INV>
-__device__ __forceinline__ void stockham_pass(V* x, int t, const V* __restrict__ W, int ws)
+// Shared-memory layout of one transform: element e lives at pidx(e) = e +
+// e/16, which spreads the stride-R writes of the first Stockham passes over
+// all banks.  A transform of length N occupies PadLen<N>::V slots.
+__device__ __forceinline__ int pidx(int e) { return e + (e >> 4); }
+template <int N> struct PadLen {
+    static constexpr int V = N + N / 16;
+};
+
+// One Stockham pass of radix R on NTR contiguous transforms of length N in
+// shared memory (transform r starts at x + r * trs), served by NT = max(1,
+// N/8) threads (t = 0..NT-1) that each handle the same butterflies of all NTR
+// transforms.  All threads of the CTA must call it (it contains barriers).
+// W is the table exp(-2 pi i k / Mtab), k < Mtab, and ws = Mtab / N.  Element e of a
+// transform is stored at pidx(e).
+template <typename V, int N, int R, int Ns, bool INV, int NTR>
+__device__ __forceinline__ void stockham_pass(V* x, int trs, int t, const V* __restrict__ W, int ws)
 {
     constexpr int NT = FftThreads<N>::NT;
     constexpr int NB = N / R;
     constexpr int PER = NB / NT;
-    V v[PER][R];
+    V v[NTR][PER][R];
 #pragma unroll
     for (int b = 0; b < PER; b++) {
         const int j = t + b * NT;
         const int k = j & (Ns - 1);
-#pragma unroll
-        for (int r = 0; r < R; r++) v[b][r] = x[j + r * NB];
+        V tw[R];
         if (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < R; r++) {
-                V tw = W[(r * k * (N / (Ns * R))) * ws];
-                if (INV) tw.y = -tw.y;
-                v[b][r] = cmul(v[b][r], tw);
+                tw[r] = W[(r * k * (N / (Ns * R))) * ws];
+                if (INV) tw[r].y = -tw[r].y;
             }
         }
-        dftR<V, R, INV>(v[b]);
+#pragma unroll
+        for (int q = 0; q < NTR; q++) {
+#pragma unroll
+            for (int r = 0; r < R; r++) v[q][b][r] = x[q * trs + pidx(j + r * NB)];
+            if (Ns > 1) {
+#pragma unroll
+                for (int r = 1; r < R; r++) v[q][b][r] = cmul(v[q][b][r], tw[r]);
+            }
+            dftR<V, R, INV>(v[q][b]);
+        }
     }
     __syncthreads();
 #pragma unroll
@@ -119,27 +136,37 @@ __device__ __forceinline__ void stockham_pass(V* x, int t, const V* __restrict__
         const int k = j & (Ns - 1);
         const int d = (j - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; r++) x[d + r * Ns] = v[b][r];
+        for (int q = 0; q < NTR; q++) {
+#pragma unroll
+            for (int r = 0; r < R; r++) x[q * trs + pidx(d + r * Ns)] = v[q][b][r];
+        }
     }
     __syncthreads();
 }
 
-template <typename V, int N, int Ns, bool INV> struct FftPasses {
-    static __device__ __forceinline__ void run(V* x, int t, const V* __restrict__ W, int ws)
+template <typename V, int N, int Ns, bool INV, int NTR> struct FftPasses {
+    static __device__ __forceinline__ void run(V* x, int trs, int t, const V* __restrict__ W, int ws)
     {
         constexpr int R = (Ns * 8 <= N) ? 8 : ((Ns * 4 <= N) ? 4 : 2);
-        stockham_pass<V, N, R, Ns, INV>(x, t, W, ws);
-        FftPasses<V, N, Ns * R, INV>::run(x, t, W, ws);
+        stockham_pass<V, N, R, Ns, INV, NTR>(x, trs, t, W, ws);
+        FftPasses<V, N, Ns * R, INV, NTR>::run(x, trs, t, W, ws);
     }
 };
-template <typename V, int N, bool INV> struct FftPasses<V, N, N, INV> {
-    static __device__ __forceinline__ void run(V*, int, const V* __restrict__, int) {}
+template <typename V, int N, bool INV, int NTR> struct FftPasses<V, N, N, INV, NTR> {
+    static __device__ __forceinline__ void run(V*, int, int, const V* __restrict__, int) {}
 };
 
 template <typename V, int N, bool INV>
 __device__ __forceinline__ void fft_smem(V* x, int t, const V* __restrict__ W, int ws)
 {
-    FftPasses<V, N, 1, INV>::run(x, t, W, ws);
+    FftPasses<V, N, 1, INV, 1>::run(x, 0, t, W, ws);
+}
+
+// NTR transforms at x, x + trs, ... handled together by the same threads.
+template <typename V, int N, bool INV, int NTR>
+__device__ __forceinline__ void fft_smem_multi(V* x, int trs, int t, const V* __restrict__ W, int ws)
+{
+    FftPasses<V, N, 1, INV, NTR>::run(x, trs, t, W, ws);
 }
 
 // Copies the twiddle table exp(-2 pi i k / M), k < M, into shared memory.
@@ -167,28 +194,80 @@ __global__ void k_fx(const R* __restrict__ grid, typename Cpx<R>::T* __restrict_
                      const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
-    constexpr int MH = M / 2, NT = FftThreads<MH>::NT;
+    constexpr int MH = M / 2, NT = FftThreads<MH>::NT, RS = PadLen<MH>::V;
     extern __shared__ __align__(16) unsigned char smraw[];
     V* s = reinterpret_cast<V*>(smraw);
     const int rows = g.rows, row0 = blockIdx.x * rows, nrows = M * M;
-    const V* sW = stage_twiddles(s + rows * MH, Wg, M);
+    const V* sW = stage_twiddles(s + rows * RS, Wg, M);
     const V* gin = reinterpret_cast<const V*>(grid);
     for (int i = threadIdx.x; i < rows * MH; i += blockDim.x) {
         const int r = i / MH, j = i % MH, row = row0 + r;
-        s[i] = row < nrows ? gin[(size_t)row * MH + j] : V{R(0), R(0)};
+        s[r * RS + pidx(j)] = row < nrows ? gin[(size_t)row * MH + j] : V{R(0), R(0)};
     }
     __syncthreads();
-    fft_smem<V, MH, false>(s + (threadIdx.x / NT) * MH, threadIdx.x % NT, sW, 2);
+    fft_smem<V, MH, false>(s + (threadIdx.x / NT) * RS, threadIdx.x % NT, sW, 2);
     const int Kx = g.Kx;
     for (int i = threadIdx.x; i < rows * Kx; i += blockDim.x) {
         const int r = i / Kx, k = i % Kx, row = row0 + r;
         if (row >= nrows) continue;
-        const V zk = s[r * MH + (k % MH)];
-        const V zc = cconj(s[r * MH + ((MH - k) % MH)]);
+        const V zk = s[r * RS + pidx(k % MH)];
+        const V zc = cconj(s[r * RS + pidx((MH - k) % MH)]);
         const V fe = V{R(0.5) * (zk.x + zc.x), R(0.5) * (zk.y + zc.y)};
         const V d = csub(zk, zc);
         const V fo = V{R(0.5) * d.y, R(-0.5) * d.x};  // -i/2 (zk - zc)
         C1[(size_t)row * Kx + k] = cadd(fe, cmul(sW[k], fo));
+    }
+}
+
+// ---------------------------------------------------------------- k_fxy
+// Fused forward x and y passes for grids whose pruned plane fits in shared
+// memory: one CTA per z-plane (grid: M blocks, 1024 threads).  The x-rows are
+// transformed in batches, the kept kx columns are stored transposed in a
+// plane buffer, transformed along y, and the band rows written to C2.
+template <typename R, int M>
+__global__ void __launch_bounds__(1024) k_fxy(const R* __restrict__ grid, typename Cpx<R>::T* __restrict__ C2,
+                                              FftGeom g, const typename Cpx<R>::T* __restrict__ Wg)
+{
+    using V = typename Cpx<R>::T;
+    constexpr int MH = M / 2, NTX = FftThreads<MH>::NT, NTY = FftThreads<M>::NT, LD = PadLen<M>::V + 1;
+    constexpr int RS = PadLen<MH>::V;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int Kx = g.Kx, Kb = g.Kb, nc = g.nc;
+    const int RB = blockDim.x / NTX;  // rows per batch
+    const int CB = blockDim.x / NTY;  // columns per batch
+    V* rowbuf = reinterpret_cast<V*>(smraw);
+    V* plane = rowbuf + RB * RS;  // [Kx (rounded to CB)][LD]
+    V* sW = plane + ((Kx + CB - 1) / CB) * CB * LD;
+    stage_twiddles(sW, Wg, M);
+    const int z = blockIdx.x;
+    const V* gin = reinterpret_cast<const V*>(grid + (size_t)z * M * M);
+    for (int y0 = 0; y0 < M; y0 += RB) {
+        for (int i = threadIdx.x; i < RB * MH; i += blockDim.x) {
+            const int r = i / MH, j = i % MH, y = y0 + r;
+            rowbuf[r * RS + pidx(j)] = y < M ? gin[(size_t)y * MH + j] : V{R(0), R(0)};
+        }
+        __syncthreads();
+        fft_smem<V, MH, false>(rowbuf + (threadIdx.x / NTX) * RS, threadIdx.x % NTX, sW, 2);
+        for (int i = threadIdx.x; i < RB * Kx; i += blockDim.x) {
+            const int r = i / Kx, k = i % Kx, y = y0 + r;
+            if (y >= M) continue;
+            const V zk = rowbuf[r * RS + pidx(k % MH)];
+            const V zc = cconj(rowbuf[r * RS + pidx((MH - k) % MH)]);
+            const V fe = V{R(0.5) * (zk.x + zc.x), R(0.5) * (zk.y + zc.y)};
+            const V d = csub(zk, zc);
+            const V fo = V{R(0.5) * d.y, R(-0.5) * d.x};
+            plane[k * LD + pidx(y)] = cadd(fe, cmul(sW[k], fo));
+        }
+        __syncthreads();
+    }
+    for (int k0 = 0; k0 < Kx; k0 += CB) {
+        fft_smem<V, M, false>(plane + (k0 + threadIdx.x / NTY) * LD, threadIdx.x % NTY, sW, 1);
+    }
+    V* dst = C2 + (size_t)z * Kb * Kx;
+    for (int i = threadIdx.x; i < Kb * Kx; i += blockDim.x) {
+        const int kb = i / Kx, kx = i % Kx;
+        const int ky = kb <= nc ? kb : M - Kb + kb;
+        dst[i] = plane[kx * LD + pidx(ky)];
     }
 }
 
@@ -199,7 +278,7 @@ __global__ void k_fy(const typename Cpx<R>::T* __restrict__ C1, typename Cpx<R>:
                      const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
-    constexpr int NT = FftThreads<M>::NT, LD = M + 1;
+    constexpr int NT = FftThreads<M>::NT, LD = PadLen<M>::V + 1;
     extern __shared__ __align__(16) unsigned char smraw[];
     V* s = reinterpret_cast<V*>(smraw);
     const int Wc = g.W, Kx = g.Kx, Kb = g.Kb, nc = g.nc;
@@ -207,7 +286,7 @@ __global__ void k_fy(const typename Cpx<R>::T* __restrict__ C1, typename Cpx<R>:
     const V* sW = stage_twiddles(s + Wc * LD, Wg, M);
     for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
         const int w = i % Wc, y = i / Wc, kx = kx0 + w;
-        s[w * LD + y] = kx < Kx ? C1[((size_t)z * M + y) * Kx + kx] : V{R(0), R(0)};
+        s[w * LD + pidx(y)] = kx < Kx ? C1[((size_t)z * M + y) * Kx + kx] : V{R(0), R(0)};
     }
     __syncthreads();
     fft_smem<V, M, false>(s + (threadIdx.x / NT) * LD, threadIdx.x % NT, sW, 1);
@@ -215,7 +294,7 @@ __global__ void k_fy(const typename Cpx<R>::T* __restrict__ C1, typename Cpx<R>:
         const int w = i % Wc, kb = i / Wc, kx = kx0 + w;
         if (kx >= Kx) continue;
         const int ky = kb <= nc ? kb : M - Kb + kb;
-        C2[((size_t)z * Kb + kb) * Kx + kx] = s[w * LD + ky];
+        C2[((size_t)z * Kb + kb) * Kx + kx] = s[w * LD + pidx(ky)];
     }
 }
 
@@ -236,17 +315,19 @@ template <typename R> struct KTables {
 // Writes NF inverse-z-transformed field spectra C3[f][z][kb][kx] and the
 // block's energy/virial partials part[blockIdx][0..6] =
 // (E, Wxx, Wyy, Wzz, Wxy, Wxz, Wyz).  NF = 0 gives the energy only.
+// Shared memory: max(NF, 1) buffers of W pencils (the first also holds the
+// forward transform), the twiddles, the reciprocal tables, the reduction.
 template <typename R, int M, int NF>
 __global__ void k_fz(const typename Cpx<R>::T* __restrict__ C2, typename Cpx<R>::T* __restrict__ C3, FftGeom g,
                      const typename Cpx<R>::T* __restrict__ Wg, KTables<R> ktg, double* __restrict__ part)
 {
     using V = typename Cpx<R>::T;
-    constexpr int NT = FftThreads<M>::NT, LD = M + 1;
+    constexpr int NT = FftThreads<M>::NT, LD = PadLen<M>::V + 1, NB = NF > 0 ? NF : 1;
     extern __shared__ __align__(16) unsigned char smraw[];
     V* X = reinterpret_cast<V*>(smraw);
     const int Wc = g.W, Kx = g.Kx, Kb = g.Kb, nc = g.nc, P = g.P;
-    V* Y = X + Wc * LD;
-    double* red = reinterpret_cast<double*>(Y + Wc * LD);
+    const int FS = Wc * LD;  // field buffer stride
+    double* red = reinterpret_cast<double*>(X + NB * FS);
     V* sW = reinterpret_cast<V*>(red + 32 * 7);
     stage_twiddles(sW, Wg, M);
     R* stab = reinterpret_cast<R*>(sW + M);
@@ -255,37 +336,38 @@ __global__ void k_fz(const typename Cpx<R>::T* __restrict__ C2, typename Cpx<R>:
         stab[3 * Kb + i] = ktg.te[i];
         stab[6 * Kb + i] = ktg.td[i];
     }
-    KTables<R> kt = ktg;
-    kt.tk = stab;
-    kt.te = stab + 3 * Kb;
-    kt.td = stab + 6 * Kb;
-    const V* W = sW;
+    const R* tk = stab;
+    const R* te = stab + 3 * Kb;
+    const R* td = stab + 6 * Kb;
     const int p0 = blockIdx.x * Wc;
     for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
         const int w = i % Wc, z = i / Wc, p = p0 + w;
-        X[w * LD + z] = p < P ? C2[(size_t)z * P + p] : V{R(0), R(0)};
+        X[w * LD + pidx(z)] = p < P ? C2[(size_t)z * P + p] : V{R(0), R(0)};
     }
     __syncthreads();
-    fft_smem<V, M, false>(X + (threadIdx.x / NT) * LD, threadIdx.x % NT, W, 1);
+    fft_smem<V, M, false>(X + (threadIdx.x / NT) * LD, threadIdx.x % NT, sW, 1);
 
-    // scaling, energy / virial, subdivided field spectrum (common factor)
+    // scaling, energy / virial, subdivided field spectra
     R acc[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
     for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
         const int w = i / M, z = i % M, p = p0 + w;
         V val = V{R(0), R(0)};
+        R kxv = R(0), kyv = R(0), kzv = R(0);
         const int nz = z <= nc ? z : (z >= M - nc ? z - M : (1 << 20));
         if (p < P && nz != (1 << 20)) {
             const int kx = p % Kx, kb = p / Kx;
             const int nx = kx, ny = kb <= nc ? kb : kb - Kb;
             if (nx != 0 || ny != 0 || nz != 0) {
-                const R kxv = kt.tk[nx + nc], kyv = kt.tk[Kb + ny + nc], kzv = kt.tk[2 * Kb + nz + nc];
+                kxv = tk[nx + nc];
+                kyv = tk[Kb + ny + nc];
+                kzv = tk[2 * Kb + nz + nc];
                 const R k2 = kxv * kxv + kyv * kyv + kzv * kzv;
-                const R G = kt.te[nx + nc] * kt.te[Kb + ny + nc] * kt.te[2 * Kb + nz + nc] / k2;
-                const R D2 = kt.td[nx + nc] * kt.td[Kb + ny + nc] * kt.td[2 * Kb + nz + nc];
-                const V gh = X[w * LD + z];
+                const R G = te[nx + nc] * te[Kb + ny + nc] * te[2 * Kb + nz + nc] / k2;
+                const R D2 = td[nx + nc] * td[Kb + ny + nc] * td[2 * Kb + nz + nc];
+                const V gh = X[w * LD + pidx(z)];
                 const R s2 = D2 * (gh.x * gh.x + gh.y * gh.y);  // |S(n)|^2
-                const R e = (nx == 0 ? R(1) : R(2)) * kt.cE * G * s2;
-                const R c = R(2) * (R(1) / k2 + kt.inv4a2);
+                const R e = (nx == 0 ? R(1) : R(2)) * ktg.cE * G * s2;
+                const R c = R(2) * (R(1) / k2 + ktg.inv4a2);
                 acc[0] += e;
                 acc[1] += e * (R(1) - c * kxv * kxv);
                 acc[2] += e * (R(1) - c * kyv * kyv);
@@ -293,39 +375,27 @@ __global__ void k_fz(const typename Cpx<R>::T* __restrict__ C2, typename Cpx<R>:
                 acc[4] -= e * c * kxv * kyv;
                 acc[5] -= e * c * kxv * kzv;
                 acc[6] -= e * c * kyv * kzv;
-                const R f = kt.cF * G * D2;
+                const R f = ktg.cF * G * D2;
                 val = V{f * gh.x, f * gh.y};
             }
         }
-        X[w * LD + z] = val;
+        if (NF > 0) {
+            // -i k_t val for the three field components, val for the potential
+            X[w * LD + pidx(z)] = V{kxv * val.y, -kxv * val.x};
+            if (NF > 1) X[FS + w * LD + pidx(z)] = V{kyv * val.y, -kyv * val.x};
+            if (NF > 2) X[2 * FS + w * LD + pidx(z)] = V{kzv * val.y, -kzv * val.x};
+            if (NF > 3) X[3 * FS + w * LD + pidx(z)] = val;
+        }
     }
     block_reduce_to_double<R, 7>(acc, part + 8 * (size_t)blockIdx.x, red);
-
+    if (NF == 0) return;
+    fft_smem_multi<V, M, true, NB>(X + (threadIdx.x / NT) * LD, FS, threadIdx.x % NT, sW, 1);
+    for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
+        const int w = i % Wc, z = i / Wc, p = p0 + w;
+        if (p < P) {
 #pragma unroll
-    for (int f = 0; f < NF; f++) {
-        for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
-            const int w = i / M, z = i % M, p = p0 + w;
-            const V v = X[w * LD + z];
-            V o;
-            if (f == 3) {
-                o = v;  // potential: cF G D^2 ghat
-            } else {
-                int n;
-                if (f == 0) n = (p < P) ? p % Kx : 0;
-                else if (f == 1) { const int kb = (p < P) ? p / Kx : 0; n = kb <= nc ? kb : kb - Kb; }
-                else n = z <= nc ? z : (z >= M - nc ? z - M : 0);
-                const R kf = kt.tk[f * Kb + n + nc];
-                o = V{kf * v.y, -kf * v.x};  // -i k_f v
-            }
-            Y[w * LD + z] = o;
+            for (int f = 0; f < NB; f++) C3[((size_t)f * M + z) * P + p] = X[f * FS + w * LD + pidx(z)];
         }
-        __syncthreads();
-        fft_smem<V, M, true>(Y + (threadIdx.x / NT) * LD, threadIdx.x % NT, W, 1);
-        for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
-            const int w = i % Wc, z = i / Wc, p = p0 + w;
-            if (p < P) C3[((size_t)f * M + z) * P + p] = Y[w * LD + z];
-        }
-        __syncthreads();
     }
 }
 
@@ -336,7 +406,7 @@ __global__ void k_iy(const typename Cpx<R>::T* __restrict__ C3, typename Cpx<R>:
                      const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
-    constexpr int NT = FftThreads<M>::NT, LD = M + 1;
+    constexpr int NT = FftThreads<M>::NT, LD = PadLen<M>::V + 1;
     extern __shared__ __align__(16) unsigned char smraw[];
     V* s = reinterpret_cast<V*>(smraw);
     const int Wc = g.W, Kx = g.Kx, Kb = g.Kb, nc = g.nc, P = g.P;
@@ -352,14 +422,75 @@ __global__ void k_iy(const typename Cpx<R>::T* __restrict__ C3, typename Cpx<R>:
             else if (y >= M - nc) kb = y - (M - Kb);
             if (kb >= 0) v = src[(size_t)kb * Kx + kx];
         }
-        s[w * LD + y] = v;
+        s[w * LD + pidx(y)] = v;
     }
     __syncthreads();
     fft_smem<V, M, true>(s + (threadIdx.x / NT) * LD, threadIdx.x % NT, W, 1);
     V* dst = C4 + ((size_t)f * M + z) * M * Kx;
     for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
         const int w = i % Wc, y = i / Wc, kx = kx0 + w;
-        if (kx < Kx) dst[(size_t)y * Kx + kx] = s[w * LD + y];
+        if (kx < Kx) dst[(size_t)y * Kx + kx] = s[w * LD + pidx(y)];
+    }
+}
+
+// ---------------------------------------------------------------- k_iyx
+// Fused inverse y and x (complex-to-real) passes: one CTA per (z-plane,
+// field) (grid: (M, NF) blocks, 1024 threads).
+template <typename R, int M>
+__global__ void __launch_bounds__(1024) k_iyx(const typename Cpx<R>::T* __restrict__ C3, R* __restrict__ fld,
+                                              FftGeom g, const typename Cpx<R>::T* __restrict__ Wg)
+{
+    using V = typename Cpx<R>::T;
+    constexpr int MH = M / 2, NTX = FftThreads<MH>::NT, NTY = FftThreads<M>::NT, LD = PadLen<M>::V + 1;
+    constexpr int RS = PadLen<MH>::V;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int Kx = g.Kx, Kb = g.Kb, nc = g.nc, P = g.P;
+    const int RB = blockDim.x / NTX;
+    const int CB = blockDim.x / NTY;
+    V* rowbuf = reinterpret_cast<V*>(smraw);
+    V* plane = rowbuf + RB * RS;
+    const int KxR = ((Kx + CB - 1) / CB) * CB;
+    V* sW = plane + KxR * LD;
+    stage_twiddles(sW, Wg, M);
+    const int z = blockIdx.x, f = blockIdx.y;
+    const V* src = C3 + ((size_t)f * M + z) * P;
+    for (int i = threadIdx.x; i < KxR * M; i += blockDim.x) {
+        const int kx = i / M, y = i % M;
+        V v = V{R(0), R(0)};
+        if (kx < Kx) {
+            int kb = -1;
+            if (y <= nc) kb = y;
+            else if (y >= M - nc) kb = y - (M - Kb);
+            if (kb >= 0) v = src[(size_t)kb * Kx + kx];
+        }
+        plane[kx * LD + pidx(y)] = v;
+    }
+    __syncthreads();
+    for (int k0 = 0; k0 < Kx; k0 += CB) {
+        fft_smem<V, M, true>(plane + (k0 + threadIdx.x / NTY) * LD, threadIdx.x % NTY, sW, 1);
+    }
+    V* out = reinterpret_cast<V*>(fld + ((size_t)f * M + z) * M * M);
+    for (int y0 = 0; y0 < M; y0 += RB) {
+        for (int i = threadIdx.x; i < RB * MH; i += blockDim.x) {
+            const int r = i / MH, k = i % MH, y = y0 + r;
+            V zz = V{R(0), R(0)};
+            if (y < M) {
+                const V a = k <= nc ? plane[k * LD + pidx(y)] : V{R(0), R(0)};
+                const int kb = MH - k;
+                const V b = kb <= nc ? cconj(plane[kb * LD + pidx(y)]) : V{R(0), R(0)};
+                const V fe = cadd(a, b);
+                const V fo = cmul(csub(a, b), cconj(sW[k]));
+                zz = V{fe.x - fo.y, fe.y + fo.x};
+            }
+            rowbuf[r * RS + pidx(k)] = zz;
+        }
+        __syncthreads();
+        fft_smem<V, MH, true>(rowbuf + (threadIdx.x / NTX) * RS, threadIdx.x % NTX, sW, 2);
+        for (int i = threadIdx.x; i < RB * MH; i += blockDim.x) {
+            const int r = i / MH, j = i % MH, y = y0 + r;
+            if (y < M) out[(size_t)y * MH + j] = rowbuf[r * RS + pidx(j)];
+        }
+        __syncthreads();
     }
 }
 
@@ -372,11 +503,11 @@ __global__ void k_ix(const typename Cpx<R>::T* __restrict__ C4, R* __restrict__ 
                      const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
-    constexpr int MH = M / 2, NT = FftThreads<MH>::NT;
+    constexpr int MH = M / 2, NT = FftThreads<MH>::NT, RS = PadLen<MH>::V;
     extern __shared__ __align__(16) unsigned char smraw[];
     V* s = reinterpret_cast<V*>(smraw);
     const int rows = g.rows, row0 = blockIdx.x * rows, Kx = g.Kx, nc = g.nc;
-    const V* W = stage_twiddles(s + rows * MH, Wg, M);
+    const V* W = stage_twiddles(s + rows * RS, Wg, M);
     __syncthreads();
     for (int i = threadIdx.x; i < rows * MH; i += blockDim.x) {
         const int r = i / MH, k = i % MH, row = row0 + r;
@@ -390,14 +521,14 @@ __global__ void k_ix(const typename Cpx<R>::T* __restrict__ C4, R* __restrict__ 
             const V fo = cmul(csub(a, b), cconj(W[k]));  // (a - b) e^{+2 pi i k / M}
             z = V{fe.x - fo.y, fe.y + fo.x};             // fe + i fo
         }
-        s[i] = z;
+        s[r * RS + pidx(k)] = z;
     }
     __syncthreads();
-    fft_smem<V, MH, true>(s + (threadIdx.x / NT) * MH, threadIdx.x % NT, W, 2);
+    fft_smem<V, MH, true>(s + (threadIdx.x / NT) * RS, threadIdx.x % NT, W, 2);
     V* out = reinterpret_cast<V*>(fld);
     for (int i = threadIdx.x; i < rows * MH; i += blockDim.x) {
         const int r = i / MH, j = i % MH, row = row0 + r;
-        if (row < nrows) out[(size_t)row * MH + j] = s[i];
+        if (row < nrows) out[(size_t)row * MH + j] = s[r * RS + pidx(j)];
     }
 }
 

@@ -28,17 +28,37 @@ template <int P> struct GroupOf {
     static constexpr int G = P <= 2 ? 2 : (P <= 4 ? 4 : (P <= 8 ? 8 : 16));
 };
 
+// Per-plan window constants: 1/b and c[a] = exp(-a^2 / b), a < P.
+template <typename R> struct WinC {
+    R inv_b;
+    R c[16];
+};
+
 // Window weights of one dimension for the in-cell fraction d in [0, 1]:
-// w[a] = exp(-(d + m - 1 - a)^2 / b), a = 0..P-1 (normalisation applied by
-// the caller).
+// w[a] = exp(-(d + j)^2 / b) with j = m - 1 - a, a = 0..P-1 (normalisation
+// applied by the caller).  Fast Gaussian gridding (Greengard and Lee, the
+// gridding of Sec. 3.1), centred on the particle's cell so that no factor
+// is raised beyond the power m: (d + j)^2 = d^2 + 2 d j + j^2 gives
+// w = exp(-d^2/b) g^j c[j] for j >= 0 and exp(-d^2/b) (1/g)^(-j) c[-j] for
+// j < 0, with g = exp(-2d/b) and c[j] = exp(-j^2/b): three exponentials per
+// dimension instead of P.
 template <typename R, int P>
-__device__ __forceinline__ void window_weights(R d, R inv_b, R (&w)[P])
+__device__ __forceinline__ void window_weights(R d, const WinC<R>& wc, R (&w)[P])
 {
     constexpr int m = P / 2;
+    const R e0 = dexp(-d * d * wc.inv_b);
+    const R g = dexp(R(-2) * d * wc.inv_b);
+    const R gi = dexp(R(2) * d * wc.inv_b);
+    R up = e0, dn = e0;
 #pragma unroll
-    for (int a = 0; a < P; a++) {
-        R u = d + (R)(m - 1 - a);
-        w[a] = dexp(-u * u * inv_b);
+    for (int j = 0; j < m; j++) {       // a = m - 1 - j
+        w[m - 1 - j] = up * wc.c[j];
+        up *= g;
+    }
+#pragma unroll
+    for (int j = 1; j <= m; j++) {      // a = m - 1 + j
+        dn *= gi;
+        w[m - 1 + j] = dn * wc.c[j];
     }
 }
 
@@ -66,10 +86,11 @@ template <int P, int T> struct Box {
 
 template <typename R, int P, int T>
 __global__ void __launch_bounds__(256) k_spread(const int4* __restrict__ work, const int* __restrict__ nwork,
-                                                const typename Rec<R>::T* __restrict__ rec, int M, int nbx,
-                                                int nby, R inv_b, R cnorm3, R* __restrict__ grid)
+                                                const typename Rec<R>::T* __restrict__ rec, int M, int lnbx,
+                                                int lnby, WinC<R> wc, R cnorm3, R* __restrict__ grid)
 {
     using B = Box<P, T>;
+    const R inv_b = wc.inv_b;
     constexpr int PT = B::PT, BX = B::BX, m = P / 2, G = GroupOf<P>::G;
     extern __shared__ __align__(16) unsigned char smraw[];
     R* acc = reinterpret_cast<R*>(smraw);
@@ -87,8 +108,8 @@ __global__ void __launch_bounds__(256) k_spread(const int4* __restrict__ work, c
         split_offset<R, T>(r.y, iy, dy);
         split_offset<R, T>(r.z, iz, dz);
         R wy[P], wz[P];
-        window_weights<R, P>(dy, inv_b, wy);
-        window_weights<R, P>(dz, inv_b, wz);
+        window_weights<R, P>(dy, wc, wy);
+        window_weights<R, P>(dz, wc, wz);
         if (lane < P) {
             R u = dx + (R)(m - 1 - lane);
             const R wx = r.w * cnorm3 * dexp(-u * u * inv_b);
@@ -104,7 +125,7 @@ __global__ void __launch_bounds__(256) k_spread(const int4* __restrict__ work, c
     __syncthreads();
 
     const int tile = w.x;
-    const int tx = tile % nbx, ty = (tile / nbx) % nby, tz = tile / (nbx * nby);
+    const int tx = tile & ((1 << lnbx) - 1), ty = (tile >> lnbx) & ((1 << lnby) - 1), tz = tile >> (lnbx + lnby);
     const int ox = tx * T - B::XA, oy = ty * T - (m - 1), oz = tz * T - (m - 1);
     const int mask = M - 1;  // M is a power of two (and a multiple of 4)
     if constexpr (sizeof(R) == 4) {
@@ -137,18 +158,19 @@ __global__ void __launch_bounds__(256) k_spread(const int4* __restrict__ work, c
 template <typename R, int P, int T, int NF>
 __global__ void __launch_bounds__(256) k_gather(const int4* __restrict__ work, const int* __restrict__ nwork,
                                                 const typename Rec<R>::T* __restrict__ rec,
-                                                const uint32_t* __restrict__ perm, int M, int nbx, int nby,
-                                                R inv_b, R cnorm3, const R* __restrict__ fld, R* __restrict__ F,
+                                                const uint32_t* __restrict__ perm, int M, int lnbx, int lnby,
+                                                WinC<R> wc, R cnorm3, const R* __restrict__ fld, R* __restrict__ F,
                                                 R* __restrict__ phi)
 {
     using B = Box<P, T>;
+    const R inv_b = wc.inv_b;
     constexpr int PT = B::PT, BX = B::BX, C = B::CELLS, m = P / 2, G = GroupOf<P>::G;
     extern __shared__ __align__(16) unsigned char smraw[];
     R* s = reinterpret_cast<R*>(smraw);
     if ((int)blockIdx.x >= *nwork) return;
     const int4 w = work[blockIdx.x];
     const int tile = w.x;
-    const int tx = tile % nbx, ty = (tile / nbx) % nby, tz = tile / (nbx * nby);
+    const int tx = tile & ((1 << lnbx) - 1), ty = (tile >> lnbx) & ((1 << lnby) - 1), tz = tile >> (lnbx + lnby);
     const int ox = tx * T - B::XA, oy = ty * T - (m - 1), oz = tz * T - (m - 1);
     const int mask = M - 1;
     const size_t M3 = (size_t)M * M * M;
@@ -175,8 +197,8 @@ __global__ void __launch_bounds__(256) k_gather(const int4* __restrict__ work, c
         split_offset<R, T>(r.y, iy, dy);
         split_offset<R, T>(r.z, iz, dz);
         R wy[P], wz[P];
-        window_weights<R, P>(dy, inv_b, wy);
-        window_weights<R, P>(dz, inv_b, wz);
+        window_weights<R, P>(dy, wc, wy);
+        window_weights<R, P>(dz, wc, wz);
         R acc[NF];
 #pragma unroll
         for (int f = 0; f < NF; f++) acc[f] = R(0);
@@ -211,6 +233,77 @@ __global__ void __launch_bounds__(256) k_gather(const int4* __restrict__ work, c
             }
             if (NF == 4 && phi) phi[oi] = cnorm3 * acc[NF - 1];
         }
+    }
+}
+
+// Interpolation without staging, for grids whose field planes stay resident
+// in L2 (the whole set is at most a few tens of MB): one group of G lanes per
+// particle in sorted order, reading each window row of p consecutive cells
+// straight from global memory (tile-sorted particles keep the reads of a CTA
+// close together, so most hit in L1).
+template <typename R, int P, int T, int NF>
+__global__ void __launch_bounds__(256) k_gather_direct(int N, const typename Rec<R>::T* __restrict__ rec,
+                                                       const uint32_t* __restrict__ tile_of,
+                                                       const uint32_t* __restrict__ perm, int M, int lnbx, int lnby,
+                                                       WinC<R> wc, R cnorm3, const R* __restrict__ fld,
+                                                       R* __restrict__ F, R* __restrict__ phi)
+{
+    constexpr int m = P / 2, G = GroupOf<P>::G;
+    const R inv_b = wc.inv_b;
+    const int lane = threadIdx.x % G;
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+    if (j >= N) return;  // whole groups leave together
+    const unsigned gmask = (G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G)));
+    const int M3 = M * M * M;  // < 2^31 for M <= 512
+    const int mask = M - 1;
+    const typename Rec<R>::T r = rec[j];
+    const int tile = (int)tile_of[j];
+    const int tx = tile & ((1 << lnbx) - 1), ty = (tile >> lnbx) & ((1 << lnby) - 1), tz = tile >> (lnbx + lnby);
+    int ix, iy, iz;
+    R dx, dy, dz;
+    split_offset<R, T>(r.x, ix, dx);
+    split_offset<R, T>(r.y, iy, dy);
+    split_offset<R, T>(r.z, iz, dz);
+    R wy[P], wz[P];
+    window_weights<R, P>(dy, wc, wy);
+    window_weights<R, P>(dz, wc, wz);
+    R acc[NF];
+#pragma unroll
+    for (int f = 0; f < NF; f++) acc[f] = R(0);
+    if (lane < P) {
+        R u = dx + (R)(m - 1 - lane);
+        const R wx = dexp(-u * u * inv_b);
+        const int gx = (tx * T + ix - (m - 1) + lane) & mask;
+        const int y0 = ty * T + iy - (m - 1), z0 = tz * T + iz - (m - 1);
+        int yo[P];
+#pragma unroll
+        for (int b = 0; b < P; b++) yo[b] = ((y0 + b) & mask) * M;
+#pragma unroll
+        for (int c = 0; c < P; c++) {
+            const R wxz = wx * wz[c];
+            const R* zb = fld + (((z0 + c) & mask) * M * M + gx);
+#pragma unroll
+            for (int b = 0; b < P; b++) {
+                const R ww = wxz * wy[b];
+#pragma unroll
+                for (int f = 0; f < NF; f++) acc[f] += ww * __ldg(zb + f * M3 + yo[b]);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+#pragma unroll
+        for (int f = 0; f < NF; f++) acc[f] += __shfl_xor_sync(gmask, acc[f], o, G);
+    }
+    if (lane == 0) {
+        const uint32_t oi = perm[j];
+        if (F) {
+            const R qc = r.w * cnorm3;
+            F[3 * (size_t)oi] = qc * acc[0];
+            F[3 * (size_t)oi + 1] = qc * acc[1];
+            F[3 * (size_t)oi + 2] = qc * acc[2];
+        }
+        if (NF == 4 && phi) phi[oi] = cnorm3 * acc[NF - 1];
     }
 }
 

@@ -226,3 +226,30 @@ def test_host_buffer_entry_point_matches_device_call():
     assert abs(E / parts["E"] - 1) < 1e-6
     assert float((Fh - F.cpu()).abs().max()) < 1e-5 * float(F.abs().max())
     assert np.abs(Wv - W2).max() < 1e-5 * np.abs(W2).max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_unfused_fft_passes_match_fused(precision, monkeypatch):
+    """Grids up to 256 use the fused x-y FFT kernels; the separate-pass
+    kernels (used for 512 and below 32) are checked at the same size."""
+    monkeypatch.setenv("ENUF_NO_FUSED_XY", "1")
+    g = np.random.default_rng(16)
+    L = np.array([30.0, 30.0, 30.0])
+    pos = g.uniform(0, 30, size=(1500, 3))
+    q = g.normal(size=1500)
+    q -= q.mean()
+    check_full(pos, q, L, 0.35, 8.0, 64, 6, 16, precision, escale=True)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_staged_gather_matches(precision, monkeypatch):
+    """Small grids interpolate straight from L2-resident fields; the
+    shared-memory staged kernel (used for large grids) is checked here on a
+    small one."""
+    monkeypatch.setenv("ENUF_STAGED_GATHER", "1")
+    g = np.random.default_rng(17)
+    L = np.array([26.0, 29.0, 31.0])
+    pos = g.uniform(0, 30, size=(1800, 3))
+    q = g.normal(size=1800)
+    q -= q.mean()
+    check_full(pos, q, L, 0.35, 8.0, 32, 8, 8, precision, escale=True)
