@@ -187,6 +187,32 @@ int enuf_launch_count(enuf_plan* plan, int flags, int with_forces);
 int enuf_real_space_noalloc(const void* pos, const void* q, int64_t N, const double* L, double alpha, double r_c,
                             double coulomb_k, int precision, void* F, void* phi, double* out, void* cuda_stream);
 
+/* ---------------------------------------------------------------------
+ * Learned parameter selector (the paper chooses alpha, r_c, n_c by the
+ * procedure of Sec. 2.3.2 / Eq. 31-32; the build adds a small network that
+ * predicts the time-optimal choice from a system descriptor).  Network:
+ * 6 -> 64 -> 64 -> 4 with SiLU activations; parameters packed row-major as
+ * W1[64][6], b1[64], W2[64][64], b2[64], W3[4][64], b3[4].  Weights used by
+ * the forward pass are bfloat16; accumulation is float.
+ * --------------------------------------------------------------------- */
+#define ENUF_MLP_NPARAM 4868
+
+/* Inference: y[n][4] = net(x[n][6]).  w_bf16: ENUF_MLP_NPARAM bfloat16
+ * values; x, y: float, device.  Asynchronous on `stream`. */
+int enuf_mlp_forward(const void* w_bf16, const float* x, int64_t n, float* y, void* stream);
+
+/* One fused training step on a mini-batch (x: batch x 6, y_target: batch x 4,
+ * out_weight: 4 loss weights; all device float): forward, backward of
+ * L = 1/(4 batch) sum out_weight_c (y - y_target)^2, gradients summed over the
+ * batch, then (if apply_update) Adam on the float master weights w_master
+ * (moments adam_m, adam_v; 1-based step) and the bfloat16 copy w_bf16 that
+ * the forward pass reads.  loss_out (1 float) and grad_out (ENUF_MLP_NPARAM
+ * floats) may be NULL.  Runs as one CTA; asynchronous on `stream`. */
+int enuf_mlp_train_step(float* w_master, void* w_bf16, float* adam_m, float* adam_v, const float* x,
+                        const float* y_target, const float* out_weight, int batch, float lr, float beta1,
+                        float beta2, float eps, int step, float* loss_out, float* grad_out, int apply_update,
+                        void* stream);
+
 /* Thread-local description of the last failure ("" if none). */
 const char* enuf_last_error(void);
 

@@ -48,7 +48,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not needs_build():
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *NVCC_FLAGS, "-o", tmp, os.path.join(SRC_DIR, "enuf.cu"), os.path.join(SRC_DIR, "noalloc.cu")]
+    cmd = [nvcc(), *NVCC_FLAGS, "-o", tmp, os.path.join(SRC_DIR, "enuf.cu"), os.path.join(SRC_DIR, "noalloc.cu"),
+           os.path.join(SRC_DIR, "mlp.cu")]
     if verbose:
         print(" ".join(cmd), flush=True)
     subprocess.check_call(cmd)
