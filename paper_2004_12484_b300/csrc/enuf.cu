@@ -41,11 +41,15 @@ int fail(int code, const std::string& msg)
     return code;
 }
 
+// On a CUDA error: clear the runtime's pending (non-sticky) error so that
+// later, unrelated launch checks do not see it, and report it.
 #define CK(call)                                                                              \
     do {                                                                                      \
         cudaError_t e_ = (call);                                                              \
-        if (e_ != cudaSuccess)                                                                \
+        if (e_ != cudaSuccess) {                                                              \
+            cudaGetLastError();                                                               \
             return fail(ENUF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));      \
+        }                                                                                     \
     } while (0)
 
 constexpr int kWorkCap = 512;  // particles per work item of spread / gather
@@ -138,10 +142,11 @@ int resolve(const enuf_params* in, Resolved& r)
         while ((size_t)(W * (padlen(M) + 1) + M) * vsz > (size_t)kMaxSmem) W -= gran;
         r.gy = FftGeom{r.nc, r.Kx, r.Kb, r.P, W, 0};
     }
-    // k_fz: pencils per block
+    // k_fz: pencils per block (at most 512 threads: the batched inverse
+    // transforms of four fields need up to 128 registers per thread)
     {
         int W = round_up(16, gran);
-        while (W * NT > 1024) W -= gran;
+        while (W * NT > 512) W -= gran;
         while ((size_t)(4 * W * (padlen(M) + 1) + M) * vsz + 32 * 7 * 8 + (size_t)9 * r.Kb * r.rsz > (size_t)kMaxSmem) W -= gran;
         r.gz = FftGeom{r.nc, r.Kx, r.Kb, r.P, W, 0};
     }
@@ -682,10 +687,16 @@ int compute_impl(enuf_plan* pl, const void* pos, const void* q, void* F, void* p
             if (e == cudaSuccess) cudaGraphDestroy(graph);
             return rc;
         }
-        if (e != cudaSuccess) return fail(ENUF_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+        if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ENUF_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+    }
         e = cudaGraphInstantiate(&pl->prof_exec, graph, 0);
         cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return fail(ENUF_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+        if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ENUF_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
         CK(cudaGraphLaunch(pl->prof_exec, pl->stream));
         return ENUF_OK;
     }
@@ -705,11 +716,17 @@ int compute_impl(enuf_plan* pl, const void* pos, const void* q, void* F, void* p
         if (e == cudaSuccess) cudaGraphDestroy(graph);
         return rc;
     }
-    if (e != cudaSuccess) return fail(ENUF_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ENUF_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+    }
     GraphEntry ge{pos, q, F, phi, out, flags, nullptr, ++pl->stamp};
     e = cudaGraphInstantiate(&ge.exec, graph, 0);
     cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return fail(ENUF_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ENUF_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
     if (pl->graphs.size() >= 8) {
         auto old = std::min_element(pl->graphs.begin(), pl->graphs.end(),
                                     [](const GraphEntry& a, const GraphEntry& b) { return a.stamp < b.stamp; });

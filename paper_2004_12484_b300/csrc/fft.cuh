@@ -190,7 +190,7 @@ struct FftGeom {
 // ---------------------------------------------------------------- k_fx
 // grid: ceil(M*M / rows) blocks, rows * NT(M/2) threads.
 template <typename R, int M>
-__global__ void k_fx(const R* __restrict__ grid, typename Cpx<R>::T* __restrict__ C1, FftGeom g,
+__global__ void __launch_bounds__(256) k_fx(const R* __restrict__ grid, typename Cpx<R>::T* __restrict__ C1, FftGeom g,
                      const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(1024) k_fxy(const R* __restrict__ grid, typena
 // ---------------------------------------------------------------- k_fy
 // grid: (ceil(Kx / W), M) blocks, W * NT(M) threads.
 template <typename R, int M>
-__global__ void k_fy(const typename Cpx<R>::T* __restrict__ C1, typename Cpx<R>::T* __restrict__ C2, FftGeom g,
+__global__ void __launch_bounds__(1024) k_fy(const typename Cpx<R>::T* __restrict__ C1, typename Cpx<R>::T* __restrict__ C2, FftGeom g,
                      const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
@@ -318,7 +318,7 @@ template <typename R> struct KTables {
 // Shared memory: max(NF, 1) buffers of W pencils (the first also holds the
 // forward transform), the twiddles, the reciprocal tables, the reduction.
 template <typename R, int M, int NF>
-__global__ void k_fz(const typename Cpx<R>::T* __restrict__ C2, typename Cpx<R>::T* __restrict__ C3, FftGeom g,
+__global__ void __launch_bounds__(512) k_fz(const typename Cpx<R>::T* __restrict__ C2, typename Cpx<R>::T* __restrict__ C3, FftGeom g,
                      const typename Cpx<R>::T* __restrict__ Wg, KTables<R> ktg, double* __restrict__ part)
 {
     using V = typename Cpx<R>::T;
@@ -402,7 +402,7 @@ __global__ void k_fz(const typename Cpx<R>::T* __restrict__ C2, typename Cpx<R>:
 // ---------------------------------------------------------------- k_iy
 // grid: (ceil(Kx / W), M, NF) blocks, W * NT(M) threads.
 template <typename R, int M>
-__global__ void k_iy(const typename Cpx<R>::T* __restrict__ C3, typename Cpx<R>::T* __restrict__ C4, FftGeom g,
+__global__ void __launch_bounds__(1024) k_iy(const typename Cpx<R>::T* __restrict__ C3, typename Cpx<R>::T* __restrict__ C4, FftGeom g,
                      const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
@@ -499,7 +499,7 @@ __global__ void __launch_bounds__(1024) k_iyx(const typename Cpx<R>::T* __restri
 // rows: X_k (k = 0..n_c, zero above) -> x_j = sum_k X_k e^{2 pi i k j/M} over
 // the Hermitian-completed spectrum.
 template <typename R, int M>
-__global__ void k_ix(const typename Cpx<R>::T* __restrict__ C4, R* __restrict__ fld, FftGeom g, int nrows,
+__global__ void __launch_bounds__(256) k_ix(const typename Cpx<R>::T* __restrict__ C4, R* __restrict__ fld, FftGeom g, int nrows,
                      const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
