@@ -109,7 +109,7 @@ int resolve(const enuf_params* in, Resolved& r)
     // memory (the same box geometry as Box<P, T> in spread_gather.cuh)
     auto box_bytes = [&](int T) {
         const int m = p.p / 2, XA = (m - 1 + 3) / 4 * 4, BX = (XA + T + m + 3) / 4 * 4, PT = T + p.p - 1;
-        return (size_t)BX * PT * PT * 4 * r.rsz;
+        return ((size_t)BX * PT * PT * 4 + (size_t)32 * p.p * p.p) * r.rsz;
     };
     r.T = (!r.fp64 && p.M >= 128) ? 16 : 8;
     while (r.T > 4 && box_bytes(r.T) > (size_t)kMaxSmem) r.T /= 2;
@@ -152,7 +152,7 @@ int resolve(const enuf_params* in, Resolved& r)
     }
     if (r.gy.W < 1 || r.gz.W < 1) return fail(ENUF_EUNSUPPORTED, "FFT block shape does not fit");
     // the four field planes stay in L2 (126 MB) when they total <= 64 MB
-    r.gather_direct = (size_t)4 * M * M * M * r.rsz <= (size_t)64 << 20 && !std::getenv("ENUF_STAGED_GATHER");
+    r.gather_direct = r.T < 16 && (size_t)4 * M * M * M * r.rsz <= (size_t)64 << 20 && !std::getenv("ENUF_STAGED_GATHER");
     // fused x-y passes (one CTA per z-plane) where the pruned plane fits
     r.fxy_threads = 0;
     r.fxy_smem = 0;
@@ -329,7 +329,8 @@ int launch_spread_t(Launcher& L, enuf_plan* pl)
 {
     const Resolved& r = pl->r;
     const Layout& y = pl->lay;
-    return L.go("spread", k_spread<R, P, T>, dim3(r.max_work), dim3(256), (size_t)Box<P, T>::CELLS * sizeof(R),
+    return L.go("spread", k_spread<R, P, T>, dim3(r.max_work), dim3(256),
+                (size_t)(Box<P, T>::CELLS + 8 * P * P) * sizeof(R),
                 at<const int4>(pl, y.work), at<const int>(pl, y.nwork), at<const typename Rec<R>::T>(pl, y.rec),
                 r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), (R)pl->cnorm3, at<R>(pl, y.grid));
 }
@@ -353,12 +354,15 @@ int launch_gather_t(Launcher& L, enuf_plan* pl, int nf, R* F, R* phi)
                     at<const uint32_t>(pl, y.perm), r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), (R)pl->cnorm3,
                     at<const R>(pl, y.fld), F, phi);
     }
-    const size_t smem = (size_t)nf * Box<P, T>::CELLS * sizeof(R);
+    // 1024 threads for the large 16-cell tiles (one CTA per SM holds the
+    // box), 256 for the smaller tiles; each warp keeps P*P weight products
+    constexpr int NTH = T == 16 ? 1024 : 256;
+    const size_t smem = ((size_t)nf * Box<P, T>::CELLS + (NTH / 32) * P * P) * sizeof(R);
     if (nf == 4)
-        return L.go("gather", k_gather<R, P, T, 4>, dim3(r.max_work), dim3(256), smem, at<const int4>(pl, y.work),
+        return L.go("gather", k_gather<R, P, T, 4, NTH>, dim3(r.max_work), dim3(NTH), smem, at<const int4>(pl, y.work),
                     at<const int>(pl, y.nwork), at<const typename Rec<R>::T>(pl, y.rec), at<const uint32_t>(pl, y.perm),
                     r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), (R)pl->cnorm3, at<const R>(pl, y.fld), F, phi);
-    return L.go("gather", k_gather<R, P, T, 3>, dim3(r.max_work), dim3(256), smem, at<const int4>(pl, y.work),
+    return L.go("gather", k_gather<R, P, T, 3, NTH>, dim3(r.max_work), dim3(NTH), smem, at<const int4>(pl, y.work),
                 at<const int>(pl, y.nwork), at<const typename Rec<R>::T>(pl, y.rec), at<const uint32_t>(pl, y.perm),
                 r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), (R)pl->cnorm3, at<const R>(pl, y.fld), F, phi);
 }

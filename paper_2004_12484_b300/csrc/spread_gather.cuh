@@ -62,6 +62,16 @@ __device__ __forceinline__ void window_weights(R d, const WinC<R>& wc, R (&w)[P]
     }
 }
 
+// Shared-memory reduction without a returned value (red.shared.add).
+__device__ __forceinline__ void shared_add(float* a, float v)
+{
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(a)), "f"(v) : "memory");
+}
+__device__ __forceinline__ void shared_add(double* a, double v)
+{
+    asm volatile("red.shared.add.f64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(a)), "d"(v) : "memory");
+}
+
 template <typename R, int T>
 __device__ __forceinline__ void split_offset(R o, int& i, R& d)
 {
@@ -69,6 +79,42 @@ __device__ __forceinline__ void split_offset(R o, int& i, R& d)
     if (c > T - 1) c = T - 1; // float rounding can give o == T
     i = c;
     d = o - (R)c;
+}
+
+// Products wy[b] * wz[c] of one particle's y and z window weights, written
+// by the warp into `wyz` (row rr = b + P c): lane k < P evaluates the two
+// exponentials of offset k and the products are formed with shuffles.
+template <typename R, int P>
+__device__ __forceinline__ void pair_weights(R dy, R dz, R inv_b, R* wyz, int lane)
+{
+    constexpr int m = P / 2;
+    const int k = lane < P ? lane : 0;
+    const R uy = dy + (R)(m - 1 - k), uz = dz + (R)(m - 1 - k);
+    const R wy = dexp(-uy * uy * inv_b), wz = dexp(-uz * uz * inv_b);
+#pragma unroll
+    for (int r0 = 0; r0 < P * P; r0 += 32) {
+        const int rr = r0 + lane;
+        const int b = rr % P, c = (rr / P) % P;
+        const R vy = __shfl_sync(0xffffffffu, wy, b);
+        const R vz = __shfl_sync(0xffffffffu, wz, c);
+        if (rr < P * P) wyz[rr] = vy * vz;
+    }
+}
+
+// Visits the P*P window rows of one particle with a whole warp, 32/G rows
+// per step: lane G g + a handles x-offset a (if a < P) of row rr = (32/G) it
+// + g, so the rows of one instruction start on different banks; f(rr, b, c)
+// with b = rr % P, c = rr / P.
+template <int P, typename Fn>
+__device__ __forceinline__ void window_rows(int a, int g, Fn&& f)
+{
+    constexpr int RPI = 32 / GroupOf<P>::G;
+    if (a >= P) return;
+#pragma unroll
+    for (int it = 0; it < (P * P + RPI - 1) / RPI; it++) {
+        const int rr = RPI * it + g;
+        if (rr < P * P) f(rr, rr % P, rr / P);
+    }
 }
 
 // Shared-memory box of a tile: x from tile_x0 - XA to tile_x0 - XA + BX
@@ -94,33 +140,33 @@ __global__ void __launch_bounds__(256) k_spread(const int4* __restrict__ work, c
     constexpr int PT = B::PT, BX = B::BX, m = P / 2, G = GroupOf<P>::G;
     extern __shared__ __align__(16) unsigned char smraw[];
     R* acc = reinterpret_cast<R*>(smraw);
+    R* wyz_all = acc + B::CELLS;  // P*P products per warp
     if ((int)blockIdx.x >= *nwork) return;  // uniform for the whole CTA
     const int4 w = work[blockIdx.x];
     for (int i = threadIdx.x; i < B::CELLS; i += blockDim.x) acc[i] = R(0);
     __syncthreads();
 
-    const int lane = threadIdx.x % G, grp = threadIdx.x / G, ngrp = blockDim.x / G;
-    for (int j = w.y + grp; j < w.z; j += ngrp) {
+    // one warp per particle: lane = 8 * g + a serves x-offset a of rows
+    // 4 it + g, so the four rows of one instruction start on different banks
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int g = lane / G, a = lane % G;
+    R* wyz = wyz_all + warp * (P * P);
+    for (int j = w.y + warp; j < w.z; j += nwarp) {
         const typename Rec<R>::T r = rec[j];
         int ix, iy, iz;
         R dx, dy, dz;
         split_offset<R, T>(r.x, ix, dx);
         split_offset<R, T>(r.y, iy, dy);
         split_offset<R, T>(r.z, iz, dz);
-        R wy[P], wz[P];
-        window_weights<R, P>(dy, wc, wy);
-        window_weights<R, P>(dz, wc, wz);
-        if (lane < P) {
-            R u = dx + (R)(m - 1 - lane);
-            const R wx = r.w * cnorm3 * dexp(-u * u * inv_b);
-            R* base = acc + (iz * PT + iy) * BX + ix + lane + B::XOFF;
-#pragma unroll
-            for (int c = 0; c < P; c++) {
-                const R wxz = wx * wz[c];
-#pragma unroll
-                for (int b = 0; b < P; b++) atomicAdd(base + (c * PT + b) * BX, wxz * wy[b]);
-            }
-        }
+        pair_weights<R, P>(dy, dz, inv_b, wyz, lane);
+        const R ua = dx + (R)(m - 1 - (a % P));
+        const R wx = r.w * cnorm3 * dexp(-ua * ua * inv_b);
+        R* base = acc + (iz * PT + iy) * BX + ix + B::XOFF;
+        __syncwarp();
+        window_rows<P>(a, g, [&](int rr, int b, int c) {
+            shared_add(base + (c * PT + b) * BX + a, wx * wyz[rr]);
+        });
+        __syncwarp();
     }
     __syncthreads();
 
@@ -155,8 +201,8 @@ __global__ void __launch_bounds__(256) k_spread(const int4* __restrict__ work, c
 // 0..2 give the force per unit charge (F_i = q_i * value), field 3 (when
 // NF = 4) the potential phi_i.  F is written (not accumulated) in the
 // caller's particle order through perm.
-template <typename R, int P, int T, int NF>
-__global__ void __launch_bounds__(256) k_gather(const int4* __restrict__ work, const int* __restrict__ nwork,
+template <typename R, int P, int T, int NF, int NTH>
+__global__ void __launch_bounds__(NTH) k_gather(const int4* __restrict__ work, const int* __restrict__ nwork,
                                                 const typename Rec<R>::T* __restrict__ rec,
                                                 const uint32_t* __restrict__ perm, int M, int lnbx, int lnby,
                                                 WinC<R> wc, R cnorm3, const R* __restrict__ fld, R* __restrict__ F,
@@ -187,41 +233,35 @@ __global__ void __launch_bounds__(256) k_gather(const int4* __restrict__ work, c
     }
     __syncthreads();
 
-    const int lane = threadIdx.x % G, grp = threadIdx.x / G, ngrp = blockDim.x / G;
-    const unsigned gmask = (G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G)));
-    for (int j = w.y + grp; j < w.z; j += ngrp) {
+    // one warp per particle, rows spread over the lanes as in k_spread
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int g = lane / G, a = lane % G;
+    R* wyz = s + NF * C + warp * (P * P);
+    for (int j = w.y + warp; j < w.z; j += nwarp) {
         const typename Rec<R>::T r = rec[j];
         int ix, iy, iz;
         R dx, dy, dz;
         split_offset<R, T>(r.x, ix, dx);
         split_offset<R, T>(r.y, iy, dy);
         split_offset<R, T>(r.z, iz, dz);
-        R wy[P], wz[P];
-        window_weights<R, P>(dy, wc, wy);
-        window_weights<R, P>(dz, wc, wz);
+        pair_weights<R, P>(dy, dz, inv_b, wyz, lane);
+        const R ua = dx + (R)(m - 1 - (a % P));
+        const R wx = dexp(-ua * ua * inv_b);
+        const R* base = s + (iz * PT + iy) * BX + ix + B::XOFF + a;
         R acc[NF];
 #pragma unroll
         for (int f = 0; f < NF; f++) acc[f] = R(0);
-        if (lane < P) {
-            R u = dx + (R)(m - 1 - lane);
-            const R wx = dexp(-u * u * inv_b);
-            const R* base = s + (iz * PT + iy) * BX + ix + lane + B::XOFF;
+        __syncwarp();
+        window_rows<P>(a, g, [&](int rr, int b, int c) {
+            const R ww = wx * wyz[rr];
+            const int o = (c * PT + b) * BX;
 #pragma unroll
-            for (int c = 0; c < P; c++) {
-                const R wxz = wx * wz[c];
+            for (int f = 0; f < NF; f++) acc[f] += ww * base[f * C + o];
+        });
 #pragma unroll
-                for (int b = 0; b < P; b++) {
-                    const R ww = wxz * wy[b];
-                    const int o = (c * PT + b) * BX;
+        for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-                    for (int f = 0; f < NF; f++) acc[f] += ww * base[f * C + o];
-                }
-            }
-        }
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) {
-#pragma unroll
-            for (int f = 0; f < NF; f++) acc[f] += __shfl_xor_sync(gmask, acc[f], o, G);
+            for (int f = 0; f < NF; f++) acc[f] += __shfl_xor_sync(0xffffffffu, acc[f], o);
         }
         if (lane == 0) {
             const uint32_t oi = perm[j];
@@ -233,6 +273,7 @@ __global__ void __launch_bounds__(256) k_gather(const int4* __restrict__ work, c
             }
             if (NF == 4 && phi) phi[oi] = cnorm3 * acc[NF - 1];
         }
+        __syncwarp();
     }
 }
 
