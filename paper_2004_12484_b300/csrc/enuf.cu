@@ -109,7 +109,7 @@ int resolve(const enuf_params* in, Resolved& r)
     // memory (the same box geometry as Box<P, T> in spread_gather.cuh)
     auto box_bytes = [&](int T) {
         const int m = p.p / 2, XA = (m - 1 + 3) / 4 * 4, BX = (XA + T + m + 3) / 4 * 4, PT = T + p.p - 1;
-        return ((size_t)BX * PT * PT * 4 + (size_t)32 * p.p * p.p) * r.rsz;
+        return ((size_t)BX * PT * PT * 4 + (size_t)32 * p.p * p.p) * r.rsz + (size_t)kWorkCap * (4 * r.rsz + 4);
     };
     r.T = (!r.fp64 && p.M >= 128) ? 16 : 8;
     while (r.T > 4 && box_bytes(r.T) > (size_t)kMaxSmem) r.T /= 2;
@@ -357,7 +357,8 @@ int launch_gather_t(Launcher& L, enuf_plan* pl, int nf, R* F, R* phi)
     // 1024 threads for the large 16-cell tiles (one CTA per SM holds the
     // box), 256 for the smaller tiles; each warp keeps P*P weight products
     constexpr int NTH = T == 16 ? 1024 : 256;
-    const size_t smem = ((size_t)nf * Box<P, T>::CELLS + (NTH / 32) * P * P) * sizeof(R);
+    const size_t smem = ((size_t)nf * Box<P, T>::CELLS + (NTH / 32) * P * P) * sizeof(R) +
+                        (size_t)kWorkCap * (sizeof(typename Rec<R>::T) + 4);
     if (nf == 4)
         return L.go("gather", k_gather<R, P, T, 4, NTH>, dim3(r.max_work), dim3(NTH), smem, at<const int4>(pl, y.work),
                     at<const int>(pl, y.nwork), at<const typename Rec<R>::T>(pl, y.rec), at<const uint32_t>(pl, y.perm),

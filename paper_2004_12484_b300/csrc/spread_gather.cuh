@@ -138,9 +138,10 @@ __global__ void __launch_bounds__(256) k_spread(const int4* __restrict__ work, c
     using B = Box<P, T>;
     const R inv_b = wc.inv_b;
     constexpr int PT = B::PT, BX = B::BX, m = P / 2, G = GroupOf<P>::G;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    R* acc = reinterpret_cast<R*>(smraw);
+    extern __shared__ __align__(32) unsigned char smraw_sg[];
+    R* acc = reinterpret_cast<R*>(smraw_sg);
     R* wyz_all = acc + B::CELLS;  // P*P products per warp
+    using RecT = typename Rec<R>::T;
     if ((int)blockIdx.x >= *nwork) return;  // uniform for the whole CTA
     const int4 w = work[blockIdx.x];
     for (int i = threadIdx.x; i < B::CELLS; i += blockDim.x) acc[i] = R(0);
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(256) k_spread(const int4* __restrict__ work, c
     const int g = lane / G, a = lane % G;
     R* wyz = wyz_all + warp * (P * P);
     for (int j = w.y + warp; j < w.z; j += nwarp) {
-        const typename Rec<R>::T r = rec[j];
+        const RecT r = rec[j];
         int ix, iy, iz;
         R dx, dy, dz;
         split_offset<R, T>(r.x, ix, dx);
@@ -211,8 +212,8 @@ __global__ void __launch_bounds__(NTH) k_gather(const int4* __restrict__ work, c
     using B = Box<P, T>;
     const R inv_b = wc.inv_b;
     constexpr int PT = B::PT, BX = B::BX, C = B::CELLS, m = P / 2, G = GroupOf<P>::G;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    R* s = reinterpret_cast<R*>(smraw);
+    extern __shared__ __align__(32) unsigned char smraw_sg[];
+    R* s = reinterpret_cast<R*>(smraw_sg);
     if ((int)blockIdx.x >= *nwork) return;
     const int4 w = work[blockIdx.x];
     const int tile = w.x;
@@ -231,6 +232,13 @@ __global__ void __launch_bounds__(NTH) k_gather(const int4* __restrict__ work, c
         for (int f = 0; f < NF; f++)
             *reinterpret_cast<float4*>(s + f * C + si) = __ldg(reinterpret_cast<const float4*>(fld + f * M3 + gi));
     }
+    using RecT = typename Rec<R>::T;
+    RecT* srec = reinterpret_cast<RecT*>(s + NF * C + (blockDim.x >> 5) * (P * P));
+    uint32_t* sperm = reinterpret_cast<uint32_t*>(srec + (w.z - w.y));
+    for (int i = threadIdx.x; i < w.z - w.y; i += blockDim.x) {
+        srec[i] = rec[w.y + i];
+        sperm[i] = perm[w.y + i];
+    }
     __syncthreads();
 
     // one warp per particle, rows spread over the lanes as in k_spread
@@ -238,7 +246,7 @@ __global__ void __launch_bounds__(NTH) k_gather(const int4* __restrict__ work, c
     const int g = lane / G, a = lane % G;
     R* wyz = s + NF * C + warp * (P * P);
     for (int j = w.y + warp; j < w.z; j += nwarp) {
-        const typename Rec<R>::T r = rec[j];
+        const typename Rec<R>::T r = srec[j - w.y];
         int ix, iy, iz;
         R dx, dy, dz;
         split_offset<R, T>(r.x, ix, dx);
@@ -264,7 +272,7 @@ __global__ void __launch_bounds__(NTH) k_gather(const int4* __restrict__ work, c
             for (int f = 0; f < NF; f++) acc[f] += __shfl_xor_sync(0xffffffffu, acc[f], o);
         }
         if (lane == 0) {
-            const uint32_t oi = perm[j];
+            const uint32_t oi = sperm[j - w.y];
             if (F) {
                 const R qc = r.w * cnorm3;
                 F[3 * (size_t)oi] = qc * acc[0];
