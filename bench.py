@@ -72,6 +72,20 @@ def dist_env():
     return rank, world
 
 
+def aggregate(ms_local, n_local, dist=None, device="cpu"):
+    """Whole-job value over ranks: the slowest rank's time (max over ranks)
+    and the particles of all ranks.  Returns (Mparticles/s, ms_max, n_total)."""
+    import torch
+    ms_max, n_tot = float(ms_local), float(n_local)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        n = torch.tensor([float(n_local)], dtype=torch.float64, device=device)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+        ms_max, n_tot = float(t.item()), float(n.item())
+    return n_tot / (ms_max * 1e-3) / 1e6, ms_max, n_tot
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -274,12 +288,7 @@ def main():
     clk = clocks.stop() if clocks else None
     if clk is not None:
         clk["window"] = "samples every 200 ms from 1.5 s of the same untimed steps before the timed region to 0.5 s after"
-    ms_max = ms
-    if pg is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = N * world / (ms_max * 1e-3) / 1e6
+    value, ms_max, _ = aggregate(ms, N, pg, device=dev)
     launches = plan.launch_count(kflags, True)
 
     extra = {}
