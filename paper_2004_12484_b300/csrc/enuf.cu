@@ -403,14 +403,14 @@ int launch_fft_chain_m(Launcher& L, enuf_plan* pl, int nf)
     const size_t vs = sizeof(V);
     const bool fused = r.fxy_threads > 0 && !std::getenv("ENUF_NO_FUSED_XY");
     if (fused) {
-        LCHK(L.go("fft_xy", k_fxy<R, M>, dim3(M), dim3(r.fxy_threads), r.fxy_smem, at<const R>(pl, y.grid),
+        LCHK(L.go("fft_xy", k_fxy<R, M>, dim3(M), dim3(r.fxy_threads), r.fxy_smem, at<R>(pl, y.grid),
                   at<V>(pl, y.C2), r.gy, W));
     }
     // forward x
     if (!fused) {
         const int NT = ffthreads(M / 2), rows = r.gfx.rows;
         const int nblk = (M * M + rows - 1) / rows;
-        LCHK(L.go("fft_x", k_fx<R, M>, dim3(nblk), dim3(rows * NT), (size_t)(rows * padlen(M / 2) + M) * vs, at<const R>(pl, y.grid),
+        LCHK(L.go("fft_x", k_fx<R, M>, dim3(nblk), dim3(rows * NT), (size_t)(rows * padlen(M / 2) + M) * vs, at<R>(pl, y.grid),
                   at<V>(pl, y.C1), r.gfx, W));
     }
     const int NT = ffthreads(M);
@@ -506,15 +506,15 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
     const int nf = want_phi ? 4 : (F ? 3 : 0);
     using RecT = typename Rec<R>::T;
 
-    LCHK(L.memset(at<void>(pl, y.status), 16));
+    // the status word and the bin counts are kept zeroed between calls by
+    // the kernels that consume them (k_finalize, k_scan_bins)
     // (a1, a2) counting sort into grid tiles
-    LCHK(L.memset(at<void>(pl, y.counts), (size_t)(r.nbins + 1) * 4));
     const int Sg[3] = {r.prm.M, r.prm.M, r.prm.M};
     const BinGeom gg = make_geom(Sg, r.T, r.prm.L, true);
     LCHK(L.go("bin_keys", k_bin_keys<R>, dim3(nblkN), dim3(256), 0, N, pos, q, gg, at<uint32_t>(pl, y.key),
               at<uint32_t>(pl, y.rank), at<RecT>(pl, y.rec_tmp), at<uint32_t>(pl, y.counts), at<int>(pl, y.status),
               at<double>(pl, y.qpart)));
-    LCHK(L.go("scan_bins", k_scan_bins, dim3(1), dim3(1024), 0, r.nbins, at<const uint32_t>(pl, y.counts),
+    LCHK(L.go("scan_bins", k_scan_bins, dim3(1), dim3(1024), 0, r.nbins, at<uint32_t>(pl, y.counts),
               at<uint32_t>(pl, y.offsets), kWorkCap, at<int4>(pl, y.work), at<int>(pl, y.nwork), r.max_work,
               at<int>(pl, y.status)));
     LCHK(L.go("scatter", k_scatter<R>, dim3(nblkN), dim3(256), 0, N, at<const uint32_t>(pl, y.key),
@@ -531,12 +531,11 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
     // (a8) real space
     int nr = 0;
     if (!konly) {
-        LCHK(L.memset(at<void>(pl, y.rcounts), (size_t)(r.nrbins + 1) * 4));
         const BinGeom gr = make_geom(r.ncell, 1, r.prm.L, false);
         LCHK(L.go("real_bin_keys", k_bin_keys<R>, dim3(nblkN), dim3(256), 0, N, pos, q, gr, at<uint32_t>(pl, y.key),
                   at<uint32_t>(pl, y.rank), at<RecT>(pl, y.rec_tmp), at<uint32_t>(pl, y.rcounts), at<int>(pl, y.status),
                   (double*)nullptr));
-        LCHK(L.go("real_scan", k_scan_bins, dim3(1), dim3(1024), 0, r.nrbins, at<const uint32_t>(pl, y.rcounts),
+        LCHK(L.go("real_scan", k_scan_bins, dim3(1), dim3(1024), 0, r.nrbins, at<uint32_t>(pl, y.rcounts),
                   at<uint32_t>(pl, y.roffsets), kWorkCap, (int4*)nullptr, (int*)nullptr, 0, at<int>(pl, y.status)));
         LCHK(L.go("real_scatter", k_scatter<R>, dim3(nblkN), dim3(256), 0, N, at<const uint32_t>(pl, y.key),
                   at<const uint32_t>(pl, y.rank), at<const uint32_t>(pl, y.roffsets), at<const RecT>(pl, y.rec_tmp),
@@ -575,7 +574,7 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
     fp.kspace_only = konly ? 1 : 0;
     double* o = out ? out : at<double>(pl, y.out);
     LCHK(L.go("finalize", k_finalize, dim3(1), dim3(512), 0, at<const double>(pl, y.qpart), at<const double>(pl, y.kpart),
-              at<const double>(pl, y.rpart), fp, at<const int>(pl, y.status), o));
+              at<const double>(pl, y.rpart), fp, at<int>(pl, y.status), o));
     if (want_phi && !konly)
         LCHK(L.go("phi_background", k_phi_background<R>, dim3(nblkN), dim3(256), 0, N, (const double*)o,
                   -r.prm.coulomb_k * kPi / (fp.V * r.prm.alpha * r.prm.alpha), phi));
@@ -661,9 +660,25 @@ int bind_workspace(enuf_plan* pl, void* ptr)
 {
     drop_graphs(pl);
     pl->ws = (char*)ptr;
+    // the status word and the bin counts start (and are kept) zeroed
+    CK(cudaMemset(pl->ws, 0, pl->lay.total));
     LCHK(upload_tables(pl));
     pl->attrs_done = false;
     return prepare_attrs(pl);
+}
+
+// Restores the buffers that evaluations expect zeroed (after an evaluation
+// was cut short).
+void reset_zeroed(enuf_plan* pl)
+{
+    const Layout& y = pl->lay;
+    const Resolved& r = pl->r;
+    const size_t M3 = (size_t)r.prm.M * r.prm.M * r.prm.M;
+    cudaMemsetAsync(pl->ws + y.status, 0, 16, pl->stream);
+    cudaMemsetAsync(pl->ws + y.counts, 0, (size_t)(r.nbins + 1) * 4, pl->stream);
+    cudaMemsetAsync(pl->ws + y.rcounts, 0, (size_t)(r.nrbins + 1) * 4, pl->stream);
+    cudaMemsetAsync(pl->ws + y.grid, 0, M3 * r.rsz, pl->stream);
+    cudaGetLastError();
 }
 
 int compute_impl(enuf_plan* pl, const void* pos, const void* q, void* F, void* phi, double* out, int flags)
@@ -705,7 +720,11 @@ int compute_impl(enuf_plan* pl, const void* pos, const void* q, void* F, void* p
         CK(cudaGraphLaunch(pl->prof_exec, pl->stream));
         return ENUF_OK;
     }
-    if (!pl->use_graph) return run_sequence(pl, pl->stream, false, pos, q, F, phi, out, flags);
+    if (!pl->use_graph) {
+        int rc = run_sequence(pl, pl->stream, false, pos, q, F, phi, out, flags);
+        if (rc != ENUF_OK) reset_zeroed(pl);
+        return rc;
+    }
     for (auto& g : pl->graphs) {
         if (g.pos == pos && g.q == q && g.F == F && g.phi == phi && g.out == out && g.flags == flags) {
             g.stamp = ++pl->stamp;

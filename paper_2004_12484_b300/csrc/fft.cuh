@@ -190,7 +190,7 @@ struct FftGeom {
 // ---------------------------------------------------------------- k_fx
 // grid: ceil(M*M / rows) blocks, rows * NT(M/2) threads.
 template <typename R, int M>
-__global__ void __launch_bounds__(256) k_fx(const R* __restrict__ grid, typename Cpx<R>::T* __restrict__ C1, FftGeom g,
+__global__ void __launch_bounds__(256) k_fx(R* __restrict__ grid, typename Cpx<R>::T* __restrict__ C1, FftGeom g,
                      const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(256) k_fx(const R* __restrict__ grid, typename
     V* s = reinterpret_cast<V*>(smraw);
     const int rows = g.rows, row0 = blockIdx.x * rows, nrows = M * M;
     const V* sW = stage_twiddles(s + rows * RS, Wg, M);
-    const V* gin = reinterpret_cast<const V*>(grid);
+    V* gin = reinterpret_cast<V*>(grid);
     for (int i = threadIdx.x; i < rows * MH; i += blockDim.x) {
         const int r = i / MH, j = i % MH, row = row0 + r;
         s[r * RS + pidx(j)] = row < nrows ? gin[(size_t)row * MH + j] : V{R(0), R(0)};
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(256) k_fx(const R* __restrict__ grid, typename
 // transformed in batches, the kept kx columns are stored transposed in a
 // plane buffer, transformed along y, and the band rows written to C2.
 template <typename R, int M>
-__global__ void __launch_bounds__(1024) k_fxy(const R* __restrict__ grid, typename Cpx<R>::T* __restrict__ C2,
+__global__ void __launch_bounds__(1024) k_fxy(R* __restrict__ grid, typename Cpx<R>::T* __restrict__ C2,
                                               FftGeom g, const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(1024) k_fxy(const R* __restrict__ grid, typena
     V* sW = plane + ((Kx + CB - 1) / CB) * CB * LD;
     stage_twiddles(sW, Wg, M);
     const int z = blockIdx.x;
-    const V* gin = reinterpret_cast<const V*>(grid + (size_t)z * M * M);
+    V* gin = reinterpret_cast<V*>(grid + (size_t)z * M * M);
     for (int y0 = 0; y0 < M; y0 += RB) {
         for (int i = threadIdx.x; i < RB * MH; i += blockDim.x) {
             const int r = i / MH, j = i % MH, y = y0 + r;

@@ -141,7 +141,7 @@ struct FinalParams {
 // the background term and writes the ENUF_NOUT results.
 __global__ void __launch_bounds__(512) k_finalize(const double* __restrict__ qpart, const double* __restrict__ kpart,
                                                   const double* __restrict__ rpart, FinalParams fp,
-                                                  const int* __restrict__ status, double* __restrict__ out)
+                                                  int* __restrict__ status, double* __restrict__ out)
 {
     __shared__ double s[16];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -179,6 +179,7 @@ __global__ void __launch_bounds__(512) k_finalize(const double* __restrict__ qpa
         out[9] = w6[3]; out[10] = w6[1] + Eb; out[11] = w6[5];
         out[12] = w6[4]; out[13] = w6[5]; out[14] = w6[2] + Eb;
         out[15] = (double)(*status);
+        *status = 0;  // cleared for the next evaluation
     }
 }
 

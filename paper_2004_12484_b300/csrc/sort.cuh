@@ -96,7 +96,8 @@ __global__ void __launch_bounds__(256) k_bin_keys(int N, const R* __restrict__ p
 // Pass 2 (one block of 1024 threads): exclusive scan of the bin counts into
 // offsets, and a work list of (bin, begin, end) items of at most `cap`
 // particles each for the kernels that process bins (heavy bins are split).
-__global__ void __launch_bounds__(1024) k_scan_bins(int nbins, const uint32_t* __restrict__ count,
+// The counts are cleared after use, ready for the next evaluation.
+__global__ void __launch_bounds__(1024) k_scan_bins(int nbins, uint32_t* __restrict__ count,
                                                     uint32_t* __restrict__ offset, int cap,
                                                     int4* __restrict__ work, int* __restrict__ nwork, int max_work,
                                                     int* __restrict__ status)
@@ -125,6 +126,7 @@ __global__ void __launch_bounds__(1024) k_scan_bins(int nbins, const uint32_t* _
     uint32_t base = s_cnt[tid] - c, wbase = s_wrk[tid] - w;
     for (int b = b0; b < b1; b++) {
         uint32_t n = count[b];
+        count[b] = 0u;
         offset[b] = base;
         if (work) {
             for (uint32_t s = 0; s < n; s += cap) {
