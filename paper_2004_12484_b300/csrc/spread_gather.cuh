@@ -117,6 +117,44 @@ __device__ __forceinline__ void window_rows(int a, int g, Fn&& f)
     }
 }
 
+// Calls f(b, c, w) for the window rows this lane serves (see window_rows),
+// with w = wy[b] * wz[c].  For p = 8 and p = 4 the lane's rows fall on fixed
+// y offsets, so the weights stay in registers (two shuffles per particle);
+// other widths go through the per-warp product table `wyz` in shared memory.
+template <typename R, int P, typename Fn>
+__device__ __forceinline__ void visit_window(R dy, R dz, const WinC<R>& wc, R* wyz, int lane, Fn&& f)
+{
+    constexpr int G = GroupOf<P>::G;
+    const int g = lane / G, a = lane % G;
+    if constexpr (P == 8) {
+        R wz[8];
+        window_weights<R, 8>(dz, wc, wz);
+        const R u = dy + (R)(3 - a);
+        const R wyo = dexp(-u * u * wc.inv_b);
+        const R wy0 = __shfl_sync(0xffffffffu, wyo, g), wy1 = __shfl_sync(0xffffffffu, wyo, g + 4);
+#pragma unroll
+        for (int it = 0; it < 16; it++) {
+            const int c = it >> 1;
+            if (it & 1) f(g + 4, c, wy1 * wz[c]);
+            else f(g, c, wy0 * wz[c]);
+        }
+    } else if constexpr (P == 4) {
+        R wz[4];
+        window_weights<R, 4>(dz, wc, wz);
+        const R u = dy + (R)(1 - a);
+        const R wyo = dexp(-u * u * wc.inv_b);
+        const int b = g & 3, hi = g >> 2;
+        const R wyb = __shfl_sync(0xffffffffu, wyo, b);
+#pragma unroll
+        for (int it = 0; it < 2; it++) f(b, 2 * it + hi, wyb * (hi ? wz[2 * it + 1] : wz[2 * it]));
+    } else {
+        pair_weights<R, P>(dy, dz, wc.inv_b, wyz, lane);
+        __syncwarp();
+        window_rows<P>(a, g, [&](int rr, int b, int c) { f(b, c, wyz[rr]); });
+        __syncwarp();
+    }
+}
+
 // Shared-memory box of a tile: x from tile_x0 - XA to tile_x0 - XA + BX
 // (XA >= m - 1 and BX multiples of 4 so that rows start on 16-byte
 // boundaries in global memory), y and z from tile origin - (m - 1) over
@@ -159,15 +197,12 @@ __global__ void __launch_bounds__(256) k_spread(const int4* __restrict__ work, c
         split_offset<R, T>(r.x, ix, dx);
         split_offset<R, T>(r.y, iy, dy);
         split_offset<R, T>(r.z, iz, dz);
-        pair_weights<R, P>(dy, dz, inv_b, wyz, lane);
         const R ua = dx + (R)(m - 1 - (a % P));
         const R wx = r.w * cnorm3 * dexp(-ua * ua * inv_b);
-        R* base = acc + (iz * PT + iy) * BX + ix + B::XOFF;
-        __syncwarp();
-        window_rows<P>(a, g, [&](int rr, int b, int c) {
-            shared_add(base + (c * PT + b) * BX + a, wx * wyz[rr]);
+        R* base = acc + (iz * PT + iy) * BX + ix + B::XOFF + a;
+        visit_window<R, P>(dy, dz, wc, wyz, lane, [&](int b, int c, R wyzv) {
+            if (a < P) shared_add(base + (c * PT + b) * BX, wx * wyzv);
         });
-        __syncwarp();
     }
     __syncthreads();
 
@@ -252,19 +287,19 @@ __global__ void __launch_bounds__(NTH) k_gather(const int4* __restrict__ work, c
         split_offset<R, T>(r.x, ix, dx);
         split_offset<R, T>(r.y, iy, dy);
         split_offset<R, T>(r.z, iz, dz);
-        pair_weights<R, P>(dy, dz, inv_b, wyz, lane);
         const R ua = dx + (R)(m - 1 - (a % P));
         const R wx = dexp(-ua * ua * inv_b);
         const R* base = s + (iz * PT + iy) * BX + ix + B::XOFF + a;
         R acc[NF];
 #pragma unroll
         for (int f = 0; f < NF; f++) acc[f] = R(0);
-        __syncwarp();
-        window_rows<P>(a, g, [&](int rr, int b, int c) {
-            const R ww = wx * wyz[rr];
-            const int o = (c * PT + b) * BX;
+        visit_window<R, P>(dy, dz, wc, wyz, lane, [&](int b, int c, R wyzv) {
+            if (a < P) {
+                const R ww = wx * wyzv;
+                const int o = (c * PT + b) * BX;
 #pragma unroll
-            for (int f = 0; f < NF; f++) acc[f] += ww * base[f * C + o];
+                for (int f = 0; f < NF; f++) acc[f] += ww * base[f * C + o];
+            }
         });
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
