@@ -112,6 +112,10 @@ int resolve(const enuf_params* in, Resolved& r)
         return ((size_t)BX * PT * PT * 4 + (size_t)32 * p.p * p.p) * r.rsz + (size_t)kWorkCap * (4 * r.rsz + 4);
     };
     r.T = (!r.fp64 && p.M >= 128) ? 16 : 8;
+    if (const char* tv = std::getenv("ENUF_TILE")) {  // tuning knob: tile edge 4, 8 or 16
+        const int t = std::atoi(tv);
+        if ((t == 4 || t == 8 || t == 16) && t <= p.M) r.T = t;
+    }
     while (r.T > 4 && box_bytes(r.T) > (size_t)kMaxSmem) r.T /= 2;
     if (box_bytes(r.T) > (size_t)kMaxSmem) return fail(ENUF_EUNSUPPORTED, "window too wide for the tile box");
     for (int t = 0; t < 3; t++) r.nbt[t] = p.M / r.T;
