@@ -157,14 +157,18 @@ int resolve(const enuf_params* in, Resolved& r)
     if (r.gy.W < 1 || r.gz.W < 1) return fail(ENUF_EUNSUPPORTED, "FFT block shape does not fit");
     // the four field planes stay in L2 (126 MB) when they total <= 64 MB
     r.gather_direct = r.T < 16 && (size_t)4 * M * M * M * r.rsz <= (size_t)64 << 20 && !std::getenv("ENUF_STAGED_GATHER");
-    // fused x-y passes (one CTA per z-plane) where the pruned plane fits
+    // fused x-y passes (one CTA per z-plane) where the pruned plane fits:
+    // the kept kx columns are transformed in as few batches as the 1024-thread
+    // limit allows, each batch CB columns wide with no idle column slots;
+    // the rows then go through in batches of blockDim / NTX
     r.fxy_threads = 0;
     r.fxy_smem = 0;
     if (M >= 32 && M <= 256) {
         const int NTX = ffthreads(M / 2), NTY = ffthreads(M);
-        for (int t : {1024, 512, 256}) {
-            if (t > M * NTX || t % 32 || t < NTY) continue;
-            const int RB = t / NTX, CB = t / NTY, KxR = (r.Kx + CB - 1) / CB * CB;
+        for (int nbatch = (r.Kx * NTY + 1023) / 1024; nbatch <= r.Kx; nbatch++) {
+            const int CB = (r.Kx + nbatch - 1) / nbatch, t = CB * NTY;
+            if (t > 1024 || t % NTX) continue;
+            const int RB = t / NTX, KxR = (r.Kx + CB - 1) / CB * CB;
             const size_t sm = ((size_t)RB * padlen(M / 2) + (size_t)KxR * (padlen(M) + 1) + M) * vsz;
             if (sm <= (size_t)kMaxSmem) {
                 r.fxy_threads = t;

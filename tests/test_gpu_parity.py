@@ -253,3 +253,28 @@ def test_staged_gather_matches(precision, monkeypatch):
     q = g.normal(size=1800)
     q -= q.mean()
     check_full(pos, q, L, 0.35, 8.0, 32, 8, 8, precision, escale=True)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_positions_on_cell_and_box_boundaries(precision):
+    """Positions exactly on grid-cell faces, on the box faces (0 and L),
+    just below L (float rounding can carry them to L), and several boxes
+    away in both directions are wrapped and binned consistently."""
+    g = np.random.default_rng(18)
+    L = np.array([24.0, 24.0, 24.0])
+    M = 32
+    h = L[0] / M
+    n = 600
+    cells = g.integers(0, M, size=(n, 3)).astype(np.float64) * h
+    pos = cells.copy()
+    pos[: n // 4] += g.uniform(0, h, size=(n // 4, 3))
+    pos[n // 4: n // 4 + 20, 0] = L[0] - 1e-7
+    pos[n // 4 + 20: n // 4 + 40, 1] = 0.0
+    pos[n // 4 + 40: n // 4 + 60] += 3 * L
+    pos[n // 4 + 60: n // 4 + 80] -= 5 * L
+    # drop exact duplicates (coincident charges have no finite energy)
+    _, keep = np.unique(np.round(np.mod(pos, L), 9), axis=0, return_index=True)
+    pos = pos[np.sort(keep)]
+    q = g.normal(size=len(pos))
+    q -= q.mean()
+    check_full(pos, q, L, 0.4, 8.0, M, 6, 8, precision, escale=True)
