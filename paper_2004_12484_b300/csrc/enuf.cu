@@ -147,11 +147,14 @@ int resolve(const enuf_params* in, Resolved& r)
         r.gy = FftGeom{r.nc, r.Kx, r.Kb, r.P, W, 0};
     }
     // k_fz: pencils per block (at most 512 threads: the batched inverse
-    // transforms of four fields need up to 128 registers per thread)
+    // transforms of four fields need up to 128 registers per thread); its
+    // passes use radix 4, so M/4 threads serve one pencil
     {
-        int W = round_up(16, gran);
-        while (W * NT > 512) W -= gran;
-        while ((size_t)(4 * W * (padlen(M) + 1) + M) * vsz + 32 * 7 * 8 + (size_t)9 * r.Kb * r.rsz > (size_t)kMaxSmem) W -= gran;
+        const int NTZ = M >= 4 ? M / 4 : 1, granz = std::max(1, 32 / NTZ);
+        int W = round_up(16, granz);
+        while (W * NTZ > 512) W -= granz;
+        while ((size_t)(4 * W * (padlen(M) + 1) + M) * vsz + 32 * 7 * 8 + (size_t)9 * r.Kb * r.rsz > (size_t)kMaxSmem)
+            W -= granz;
         r.gz = FftGeom{r.nc, r.Kx, r.Kb, r.P, W, 0};
     }
     if (r.gy.W < 1 || r.gz.W < 1) return fail(ENUF_EUNSUPPORTED, "FFT block shape does not fit");
@@ -441,6 +444,7 @@ int launch_fft_chain_m(Launcher& L, enuf_plan* pl, int nf)
         kt.cF = (R)(r.prm.coulomb_k * 4.0 * kPi / V3);
         kt.inv4a2 = (R)(1.0 / (4.0 * r.prm.alpha * r.prm.alpha));
         const dim3 g((r.P + Wc - 1) / Wc);
+        const int NT = M >= 4 ? M / 4 : 1;  // threads per pencil in k_fz (radix-4 passes)
         if (nf == 0)
             LCHK(L.go("fft_z_kspace", k_fz<R, M, 0>, g, dim3(Wc * NT), smem, at<const V>(pl, y.C2), at<V>(pl, y.C3), r.gz,
                       W, kt, at<double>(pl, y.kpart)));

@@ -81,8 +81,10 @@ template <typename V, int R, bool INV> __device__ __forceinline__ void dftR(V* v
     else dft2<V, INV>(v);
 }
 
-template <int N> struct FftThreads {
-    static constexpr int NT = N >= 8 ? N / 8 : 1;
+// Threads serving one transform of length N when passes use radix MR (8 or
+// 4) and below: each thread holds MR elements per pass.
+template <int N, int MR = 8> struct FftThreads {
+    static constexpr int NT = N >= MR ? N / MR : 1;
 };
 
 // Shared-memory layout of one transform: element e lives at pidx(e) = e +
@@ -99,10 +101,10 @@ template <int N> struct PadLen {
 // transforms.  All threads of the CTA must call it (it contains barriers).
 // W is the table exp(-2 pi i k / Mtab), k < Mtab, and ws = Mtab / N.  Element e of a
 // transform is stored at pidx(e).
-template <typename V, int N, int R, int Ns, bool INV, int NTR>
+template <typename V, int N, int R, int Ns, bool INV, int NTR, int MR>
 __device__ __forceinline__ void stockham_pass(V* x, int trs, int t, const V* __restrict__ W, int ws)
 {
-    constexpr int NT = FftThreads<N>::NT;
+    constexpr int NT = FftThreads<N, MR>::NT;
     constexpr int NB = N / R;
     constexpr int PER = NB / NT;
     V v[NTR][PER][R];
@@ -144,29 +146,29 @@ __device__ __forceinline__ void stockham_pass(V* x, int trs, int t, const V* __r
     __syncthreads();
 }
 
-template <typename V, int N, int Ns, bool INV, int NTR> struct FftPasses {
+template <typename V, int N, int Ns, bool INV, int NTR, int MR> struct FftPasses {
     static __device__ __forceinline__ void run(V* x, int trs, int t, const V* __restrict__ W, int ws)
     {
-        constexpr int R = (Ns * 8 <= N) ? 8 : ((Ns * 4 <= N) ? 4 : 2);
-        stockham_pass<V, N, R, Ns, INV, NTR>(x, trs, t, W, ws);
-        FftPasses<V, N, Ns * R, INV, NTR>::run(x, trs, t, W, ws);
+        constexpr int R = (MR >= 8 && Ns * 8 <= N) ? 8 : ((Ns * 4 <= N) ? 4 : 2);
+        stockham_pass<V, N, R, Ns, INV, NTR, MR>(x, trs, t, W, ws);
+        FftPasses<V, N, Ns * R, INV, NTR, MR>::run(x, trs, t, W, ws);
     }
 };
-template <typename V, int N, bool INV, int NTR> struct FftPasses<V, N, N, INV, NTR> {
+template <typename V, int N, bool INV, int NTR, int MR> struct FftPasses<V, N, N, INV, NTR, MR> {
     static __device__ __forceinline__ void run(V*, int, int, const V* __restrict__, int) {}
 };
 
-template <typename V, int N, bool INV>
+template <typename V, int N, bool INV, int MR = 8>
 __device__ __forceinline__ void fft_smem(V* x, int t, const V* __restrict__ W, int ws)
 {
-    FftPasses<V, N, 1, INV, 1>::run(x, 0, t, W, ws);
+    FftPasses<V, N, 1, INV, 1, MR>::run(x, 0, t, W, ws);
 }
 
 // NTR transforms at x, x + trs, ... handled together by the same threads.
-template <typename V, int N, bool INV, int NTR>
+template <typename V, int N, bool INV, int NTR, int MR = 8>
 __device__ __forceinline__ void fft_smem_multi(V* x, int trs, int t, const V* __restrict__ W, int ws)
 {
-    FftPasses<V, N, 1, INV, NTR>::run(x, trs, t, W, ws);
+    FftPasses<V, N, 1, INV, NTR, MR>::run(x, trs, t, W, ws);
 }
 
 // Copies the twiddle table exp(-2 pi i k / M), k < M, into shared memory.
@@ -322,7 +324,9 @@ __global__ void __launch_bounds__(512) k_fz(const typename Cpx<R>::T* __restrict
                      const typename Cpx<R>::T* __restrict__ Wg, KTables<R> ktg, double* __restrict__ part)
 {
     using V = typename Cpx<R>::T;
-    constexpr int NT = FftThreads<M>::NT, LD = PadLen<M>::V + 1, NB = NF > 0 ? NF : 1;
+    // radix-4 passes: twice the threads of the radix-8 kernels, for more
+    // parallelism in this small kernel
+    constexpr int MR = 4, NT = FftThreads<M, MR>::NT, LD = PadLen<M>::V + 1, NB = NF > 0 ? NF : 1;
     extern __shared__ __align__(16) unsigned char smraw[];
     V* X = reinterpret_cast<V*>(smraw);
     const int Wc = g.W, Kx = g.Kx, Kb = g.Kb, nc = g.nc, P = g.P;
@@ -345,7 +349,7 @@ __global__ void __launch_bounds__(512) k_fz(const typename Cpx<R>::T* __restrict
         X[w * LD + pidx(z)] = p < P ? C2[(size_t)z * P + p] : V{R(0), R(0)};
     }
     __syncthreads();
-    fft_smem<V, M, false>(X + (threadIdx.x / NT) * LD, threadIdx.x % NT, sW, 1);
+    fft_smem<V, M, false, MR>(X + (threadIdx.x / NT) * LD, threadIdx.x % NT, sW, 1);
 
     // scaling, energy / virial, subdivided field spectra
     R acc[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
@@ -389,7 +393,7 @@ __global__ void __launch_bounds__(512) k_fz(const typename Cpx<R>::T* __restrict
     }
     block_reduce_to_double<R, 7>(acc, part + 8 * (size_t)blockIdx.x, red);
     if (NF == 0) return;
-    fft_smem_multi<V, M, true, NB>(X + (threadIdx.x / NT) * LD, FS, threadIdx.x % NT, sW, 1);
+    fft_smem_multi<V, M, true, NB, MR>(X + (threadIdx.x / NT) * LD, FS, threadIdx.x % NT, sW, 1);
     for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
         const int w = i % Wc, z = i / Wc, p = p0 + w;
         if (p < P) {
