@@ -196,6 +196,10 @@ struct Layout {
     size_t total;
 };
 
+// Word stride of the bin counters: one 128-byte line each while the padded
+// array stays small, packed otherwise.
+int count_stride(int nbins) { return nbins <= 8192 ? 32 : 1; }
+
 Layout layout(const Resolved& r)
 {
     Layout L{};
@@ -212,7 +216,7 @@ Layout layout(const Resolved& r)
     L.status = take(16);
     L.out = take(ENUF_NOUT * 8);
     L.mean = take(4 * 8);
-    L.counts = take((r.nbins + 1) * 4);
+    L.counts = take((size_t)(r.nbins + 1) * 4 * count_stride(r.nbins));
     L.offsets = take((r.nbins + 1) * 4);
     L.work = take((size_t)r.max_work * 16);
     L.nwork = take(4);
@@ -222,7 +226,7 @@ Layout layout(const Resolved& r)
     L.rec = take(N * recsz);
     L.perm = take(N * 4);
     L.tile_of = take(N * 4);
-    L.rcounts = take((r.nrbins + 1) * 4);
+    L.rcounts = take((size_t)(r.nrbins + 1) * 4 * count_stride(r.nrbins));
     L.roffsets = take((r.nrbins + 1) * 4);
     L.rrec = take(N * recsz);
     L.rperm = take(N * 4);
@@ -524,10 +528,10 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
     const int Sg[3] = {r.prm.M, r.prm.M, r.prm.M};
     const BinGeom gg = make_geom(Sg, r.T, r.prm.L, true);
     LCHK(L.go("bin_keys", k_bin_keys<R>, dim3(nblkN), dim3(256), 0, N, pos, q, gg, at<uint32_t>(pl, y.key),
-              at<uint32_t>(pl, y.rank), at<RecT>(pl, y.rec_tmp), at<uint32_t>(pl, y.counts), at<int>(pl, y.status),
-              at<double>(pl, y.qpart)));
+              at<uint32_t>(pl, y.rank), at<RecT>(pl, y.rec_tmp), at<uint32_t>(pl, y.counts), count_stride(r.nbins),
+              at<int>(pl, y.status), at<double>(pl, y.qpart)));
     LCHK(L.go("scan_bins", k_scan_bins, dim3(1), dim3(1024), 0, r.nbins, at<uint32_t>(pl, y.counts),
-              at<uint32_t>(pl, y.offsets), kWorkCap, at<int4>(pl, y.work), at<int>(pl, y.nwork), r.max_work,
+              count_stride(r.nbins), at<uint32_t>(pl, y.offsets), kWorkCap, at<int4>(pl, y.work), at<int>(pl, y.nwork), r.max_work,
               at<int>(pl, y.status)));
     LCHK(L.go("scatter", k_scatter<R>, dim3(nblkN), dim3(256), 0, N, at<const uint32_t>(pl, y.key),
               at<const uint32_t>(pl, y.rank), at<const uint32_t>(pl, y.offsets), at<const RecT>(pl, y.rec_tmp),
@@ -545,10 +549,10 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
     if (!konly) {
         const BinGeom gr = make_geom(r.ncell, 1, r.prm.L, false);
         LCHK(L.go("real_bin_keys", k_bin_keys<R>, dim3(nblkN), dim3(256), 0, N, pos, q, gr, at<uint32_t>(pl, y.key),
-                  at<uint32_t>(pl, y.rank), at<RecT>(pl, y.rec_tmp), at<uint32_t>(pl, y.rcounts), at<int>(pl, y.status),
-                  (double*)nullptr));
+                  at<uint32_t>(pl, y.rank), at<RecT>(pl, y.rec_tmp), at<uint32_t>(pl, y.rcounts),
+                  count_stride(r.nrbins), at<int>(pl, y.status), (double*)nullptr));
         LCHK(L.go("real_scan", k_scan_bins, dim3(1), dim3(1024), 0, r.nrbins, at<uint32_t>(pl, y.rcounts),
-                  at<uint32_t>(pl, y.roffsets), kWorkCap, (int4*)nullptr, (int*)nullptr, 0, at<int>(pl, y.status)));
+                  count_stride(r.nrbins), at<uint32_t>(pl, y.roffsets), kWorkCap, (int4*)nullptr, (int*)nullptr, 0, at<int>(pl, y.status)));
         LCHK(L.go("real_scatter", k_scatter<R>, dim3(nblkN), dim3(256), 0, N, at<const uint32_t>(pl, y.key),
                   at<const uint32_t>(pl, y.rank), at<const uint32_t>(pl, y.roffsets), at<const RecT>(pl, y.rec_tmp),
                   at<RecT>(pl, y.rrec), at<uint32_t>(pl, y.rperm), at<uint32_t>(pl, y.rcell)));
@@ -687,8 +691,8 @@ void reset_zeroed(enuf_plan* pl)
     const Resolved& r = pl->r;
     const size_t M3 = (size_t)r.prm.M * r.prm.M * r.prm.M;
     cudaMemsetAsync(pl->ws + y.status, 0, 16, pl->stream);
-    cudaMemsetAsync(pl->ws + y.counts, 0, (size_t)(r.nbins + 1) * 4, pl->stream);
-    cudaMemsetAsync(pl->ws + y.rcounts, 0, (size_t)(r.nrbins + 1) * 4, pl->stream);
+    cudaMemsetAsync(pl->ws + y.counts, 0, (size_t)(r.nbins + 1) * 4 * count_stride(r.nbins), pl->stream);
+    cudaMemsetAsync(pl->ws + y.rcounts, 0, (size_t)(r.nrbins + 1) * 4 * count_stride(r.nrbins), pl->stream);
     cudaMemsetAsync(pl->ws + y.grid, 0, M3 * r.rsz, pl->stream);
     cudaGetLastError();
 }

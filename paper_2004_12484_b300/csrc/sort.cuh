@@ -50,13 +50,16 @@ __device__ __forceinline__ void locate(float r, const BinGeom& g, int t, int& c,
 }
 
 // Pass 1: bin key, rank inside the bin (atomic counter), unsorted record,
-// per-block sums of q^2 and q (for the self and background terms).
+// per-block sums of q^2 and q (for the self and background terms).  The
+// counter of bin b is count[b * cs]: with few bins, a stride of one 128-byte
+// line per counter spreads the atomics over many L2 lines instead of a few
+// hot ones.
 template <typename R>
 __global__ void __launch_bounds__(256) k_bin_keys(int N, const R* __restrict__ pos, const R* __restrict__ q,
                                                   BinGeom g, uint32_t* __restrict__ key,
                                                   uint32_t* __restrict__ rank,
                                                   typename Rec<R>::T* __restrict__ rec,
-                                                  uint32_t* __restrict__ count, int* __restrict__ status,
+                                                  uint32_t* __restrict__ count, int cs, int* __restrict__ status,
                                                   double* __restrict__ qpart)
 {
     __shared__ double red[32 * 2];
@@ -82,7 +85,7 @@ __global__ void __launch_bounds__(256) k_bin_keys(int N, const R* __restrict__ p
         uint32_t b = (uint32_t)(c[0] / g.T) +
                      (uint32_t)g.nb[0] * ((uint32_t)(c[1] / g.T) + (uint32_t)g.nb[1] * (uint32_t)(c[2] / g.T));
         key[i] = b;
-        rank[i] = atomicAdd(&count[b], 1u);
+        rank[i] = atomicAdd(&count[(size_t)b * cs], 1u);
         typename Rec<R>::T rr;
         rr.x = off[0]; rr.y = off[1]; rr.z = off[2]; rr.w = qq;
         rec[i] = rr;
@@ -96,37 +99,48 @@ __global__ void __launch_bounds__(256) k_bin_keys(int N, const R* __restrict__ p
 // Pass 2 (one block of 1024 threads): exclusive scan of the bin counts into
 // offsets, and a work list of (bin, begin, end) items of at most `cap`
 // particles each for the kernels that process bins (heavy bins are split).
-// The counts are cleared after use, ready for the next evaluation.
-__global__ void __launch_bounds__(1024) k_scan_bins(int nbins, uint32_t* __restrict__ count,
+// Each thread sums a contiguous chunk of bins; the per-thread totals are
+// scanned with warp shuffles and one pass over the 32 warp totals.  The
+// counts are cleared after use, ready for the next evaluation.
+__global__ void __launch_bounds__(1024) k_scan_bins(int nbins, uint32_t* __restrict__ count, int cs,
                                                     uint32_t* __restrict__ offset, int cap,
                                                     int4* __restrict__ work, int* __restrict__ nwork, int max_work,
                                                     int* __restrict__ status)
 {
-    __shared__ uint32_t s_cnt[1024], s_wrk[1024];
-    const int tid = threadIdx.x, nt = blockDim.x;
+    __shared__ uint32_t s_cnt[32], s_wrk[32];
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
     const int chunk = (nbins + nt - 1) / nt;
     const int b0 = min(nbins, tid * chunk), b1 = min(nbins, b0 + chunk);
     uint32_t c = 0, w = 0;
     for (int b = b0; b < b1; b++) {
-        uint32_t n = count[b];
+        uint32_t n = count[(size_t)b * cs];
         c += n;
         if (work) w += (n + cap - 1) / cap;
     }
-    s_cnt[tid] = c;
-    s_wrk[tid] = w;
-    __syncthreads();
-    // Hillis-Steele inclusive scan of the per-thread totals
-    for (int o = 1; o < nt; o <<= 1) {
-        uint32_t a = tid >= o ? s_cnt[tid - o] : 0u, bw = tid >= o ? s_wrk[tid - o] : 0u;
-        __syncthreads();
-        s_cnt[tid] += a;
-        s_wrk[tid] += bw;
-        __syncthreads();
+    // inclusive scans inside each warp, then over the warp totals
+    uint32_t ic = c, iw = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t a = __shfl_up_sync(0xffffffffu, ic, o), bw = __shfl_up_sync(0xffffffffu, iw, o);
+        if (lane >= o) { ic += a; iw += bw; }
     }
-    uint32_t base = s_cnt[tid] - c, wbase = s_wrk[tid] - w;
+    if (lane == 31) { s_cnt[warp] = ic; s_wrk[warp] = iw; }
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t x = lane < nwarp ? s_cnt[lane] : 0u, y = lane < nwarp ? s_wrk[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t a = __shfl_up_sync(0xffffffffu, x, o), bw = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) { x += a; y += bw; }
+        }
+        s_cnt[lane] = x;
+        s_wrk[lane] = y;
+    }
+    __syncthreads();
+    uint32_t base = (warp ? s_cnt[warp - 1] : 0u) + ic - c, wbase = (warp ? s_wrk[warp - 1] : 0u) + iw - w;
     for (int b = b0; b < b1; b++) {
-        uint32_t n = count[b];
-        count[b] = 0u;
+        uint32_t n = count[(size_t)b * cs];
+        count[(size_t)b * cs] = 0u;
         offset[b] = base;
         if (work) {
             for (uint32_t s = 0; s < n; s += cap) {
@@ -137,9 +151,9 @@ __global__ void __launch_bounds__(1024) k_scan_bins(int nbins, uint32_t* __restr
         base += n;
     }
     if (tid == nt - 1) {
-        offset[nbins] = s_cnt[tid];
+        offset[nbins] = s_cnt[nwarp - 1];
         if (work) {
-            int nw = (int)s_wrk[tid];
+            int nw = (int)s_wrk[nwarp - 1];
             if (nw > max_work) { atomicOr(status, ST_WORKLIST); nw = max_work; }
             *nwork = nw;
         }
