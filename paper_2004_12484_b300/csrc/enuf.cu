@@ -290,12 +290,13 @@ namespace {
 
 template <typename T> T* at(enuf_plan* pl, size_t off) { return reinterpret_cast<T*>(pl->ws + off); }
 
-// Window constants for the kernels: 1/b and exp(-a^2/b), a < 16 (computed in
-// double on the host, rounded to the kernel's type).
+// Window constants for the kernels: 1/b, log2(e)/b and exp(-a^2/b), a < 16
+// (computed in double on the host, rounded to the kernel's type).
 template <typename R> WinC<R> winc(const enuf_plan* pl)
 {
     WinC<R> w{};
     w.inv_b = (R)pl->inv_b;
+    w.l2b = (R)(pl->inv_b / std::log(2.0));
     for (int a = 0; a < 16; a++) w.c[a] = (R)std::exp(-(double)a * a * pl->inv_b);
     return w;
 }

@@ -28,11 +28,17 @@ template <int P> struct GroupOf {
     static constexpr int G = P <= 2 ? 2 : (P <= 4 ? 4 : (P <= 8 ? 8 : 16));
 };
 
-// Per-plan window constants: 1/b and c[a] = exp(-a^2 / b), a < P.
+// Per-plan window constants: 1/b, log2(e)/b and c[a] = exp(-a^2 / b), a < P.
 template <typename R> struct WinC {
     R inv_b;
+    R l2b;
     R c[16];
 };
+
+// exp(-s / b).  Single precision evaluates 2^(-s log2(e) / b) with the
+// factor folded into one constant; double calls exp.
+__device__ __forceinline__ float win_exp(float s, const WinC<float>& wc) { return exp2f(-s * wc.l2b); }
+__device__ __forceinline__ double win_exp(double s, const WinC<double>& wc) { return exp(-s * wc.inv_b); }
 
 // Window weights of one dimension for the in-cell fraction d in [0, 1]:
 // w[a] = exp(-(d + j)^2 / b) with j = m - 1 - a, a = 0..P-1 (normalisation
@@ -46,9 +52,9 @@ template <typename R, int P>
 __device__ __forceinline__ void window_weights(R d, const WinC<R>& wc, R (&w)[P])
 {
     constexpr int m = P / 2;
-    const R e0 = dexp(-d * d * wc.inv_b);
-    const R g = dexp(R(-2) * d * wc.inv_b);
-    const R gi = dexp(R(2) * d * wc.inv_b);
+    const R e0 = win_exp(d * d, wc);
+    const R g = win_exp(R(2) * d, wc);
+    const R gi = win_exp(R(-2) * d, wc);
     R up = e0, dn = e0;
 #pragma unroll
     for (int j = 0; j < m; j++) {       // a = m - 1 - j
@@ -85,12 +91,12 @@ __device__ __forceinline__ void split_offset(R o, int& i, R& d)
 // by the warp into `wyz` (row rr = b + P c): lane k < P evaluates the two
 // exponentials of offset k and the products are formed with shuffles.
 template <typename R, int P>
-__device__ __forceinline__ void pair_weights(R dy, R dz, R inv_b, R* wyz, int lane)
+__device__ __forceinline__ void pair_weights(R dy, R dz, const WinC<R>& wc, R* wyz, int lane)
 {
     constexpr int m = P / 2;
     const int k = lane < P ? lane : 0;
     const R uy = dy + (R)(m - 1 - k), uz = dz + (R)(m - 1 - k);
-    const R wy = dexp(-uy * uy * inv_b), wz = dexp(-uz * uz * inv_b);
+    const R wy = win_exp(uy * uy, wc), wz = win_exp(uz * uz, wc);
 #pragma unroll
     for (int r0 = 0; r0 < P * P; r0 += 32) {
         const int rr = r0 + lane;
@@ -103,8 +109,8 @@ __device__ __forceinline__ void pair_weights(R dy, R dz, R inv_b, R* wyz, int la
 
 // Visits the P*P window rows of one particle with a whole warp, 32/G rows
 // per step: lane G g + a handles x-offset a (if a < P) of row rr = (32/G) it
-// + g, so the rows of one instruction start on different banks; f(rr, b, c)
-// with b = rr % P, c = rr / P.
+// + g, so the rows of one instruction start on different banks; f(it, rr, b,
+// c) with b = rr % P, c = rr / P.
 template <int P, typename Fn>
 __device__ __forceinline__ void window_rows(int a, int g, Fn&& f)
 {
@@ -113,12 +119,12 @@ __device__ __forceinline__ void window_rows(int a, int g, Fn&& f)
 #pragma unroll
     for (int it = 0; it < (P * P + RPI - 1) / RPI; it++) {
         const int rr = RPI * it + g;
-        if (rr < P * P) f(rr, rr % P, rr / P);
+        if (rr < P * P) f(it, rr, rr % P, rr / P);
     }
 }
 
-// Calls f(b, c, w) for the window rows this lane serves (see window_rows),
-// with w = wy[b] * wz[c].  For p = 8 and p = 4 the lane's rows fall on fixed
+// Calls f(s, b, c, w) for the window rows this lane serves (see
+// window_rows), with w = wy[b] * wz[c] and s = 0, 1, ... the lane's step.  For p = 8 and p = 4 the lane's rows fall on fixed
 // y offsets, so the weights stay in registers (two shuffles per particle);
 // other widths go through the per-warp product table `wyz` in shared memory.
 template <typename R, int P, typename Fn>
@@ -130,29 +136,47 @@ __device__ __forceinline__ void visit_window(R dy, R dz, const WinC<R>& wc, R* w
         R wz[8];
         window_weights<R, 8>(dz, wc, wz);
         const R u = dy + (R)(3 - a);
-        const R wyo = dexp(-u * u * wc.inv_b);
+        const R wyo = win_exp(u * u, wc);
         const R wy0 = __shfl_sync(0xffffffffu, wyo, g), wy1 = __shfl_sync(0xffffffffu, wyo, g + 4);
 #pragma unroll
         for (int it = 0; it < 16; it++) {
             const int c = it >> 1;
-            if (it & 1) f(g + 4, c, wy1 * wz[c]);
-            else f(g, c, wy0 * wz[c]);
+            if (it & 1) f(it, g + 4, c, wy1 * wz[c]);
+            else f(it, g, c, wy0 * wz[c]);
         }
     } else if constexpr (P == 4) {
         R wz[4];
         window_weights<R, 4>(dz, wc, wz);
         const R u = dy + (R)(1 - a);
-        const R wyo = dexp(-u * u * wc.inv_b);
+        const R wyo = win_exp(u * u, wc);
         const int b = g & 3, hi = g >> 2;
         const R wyb = __shfl_sync(0xffffffffu, wyo, b);
 #pragma unroll
-        for (int it = 0; it < 2; it++) f(b, 2 * it + hi, wyb * (hi ? wz[2 * it + 1] : wz[2 * it]));
+        for (int it = 0; it < 2; it++) f(it, b, 2 * it + hi, wyb * (hi ? wz[2 * it + 1] : wz[2 * it]));
     } else {
-        pair_weights<R, P>(dy, dz, wc.inv_b, wyz, lane);
+        pair_weights<R, P>(dy, dz, wc, wyz, lane);
         __syncwarp();
-        window_rows<P>(a, g, [&](int rr, int b, int c) { f(b, c, wyz[rr]); });
+        window_rows<P>(a, g, [&](int it, int rr, int b, int c) { f(it, b, c, wyz[rr]); });
         __syncwarp();
     }
+}
+
+// Sum over the warp of four values per lane, transposed: the lanes exchange
+// half of their values at each of the first two steps, so that 6 shuffles
+// replace 20.  Returns, in lane l, the total of value (l >> 3) & 3 (lanes 0,
+// 8, 16, 24 hold totals 0, 1, 2, 3).
+template <typename R>
+__device__ __forceinline__ R warp_sum4(const R (&v)[4], int lane)
+{
+    const bool h16 = lane & 16, h8 = lane & 8;
+    R k0 = h16 ? v[2] : v[0], k1 = h16 ? v[3] : v[1];
+    k0 += __shfl_xor_sync(0xffffffffu, h16 ? v[0] : v[2], 16);
+    k1 += __shfl_xor_sync(0xffffffffu, h16 ? v[1] : v[3], 16);
+    R k = h8 ? k1 : k0;
+    k += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+    return k;
 }
 
 // Shared-memory box of a tile: x from tile_x0 - XA to tile_x0 - XA + BX
@@ -174,7 +198,6 @@ __global__ void __launch_bounds__(256) k_spread(const int4* __restrict__ work, c
                                                 int lnby, WinC<R> wc, R cnorm3, R* __restrict__ grid)
 {
     using B = Box<P, T>;
-    const R inv_b = wc.inv_b;
     constexpr int PT = B::PT, BX = B::BX, m = P / 2, G = GroupOf<P>::G;
     extern __shared__ __align__(32) unsigned char smraw_sg[];
     R* acc = reinterpret_cast<R*>(smraw_sg);
@@ -188,7 +211,7 @@ __global__ void __launch_bounds__(256) k_spread(const int4* __restrict__ work, c
     // one warp per particle: lane = 8 * g + a serves x-offset a of rows
     // 4 it + g, so the four rows of one instruction start on different banks
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    const int g = lane / G, a = lane % G;
+    const int a = lane % G;
     R* wyz = wyz_all + warp * (P * P);
     for (int j = w.y + warp; j < w.z; j += nwarp) {
         const RecT r = rec[j];
@@ -198,9 +221,9 @@ __global__ void __launch_bounds__(256) k_spread(const int4* __restrict__ work, c
         split_offset<R, T>(r.y, iy, dy);
         split_offset<R, T>(r.z, iz, dz);
         const R ua = dx + (R)(m - 1 - (a % P));
-        const R wx = r.w * cnorm3 * dexp(-ua * ua * inv_b);
+        const R wx = r.w * cnorm3 * win_exp(ua * ua, wc);
         R* base = acc + (iz * PT + iy) * BX + ix + B::XOFF + a;
-        visit_window<R, P>(dy, dz, wc, wyz, lane, [&](int b, int c, R wyzv) {
+        visit_window<R, P>(dy, dz, wc, wyz, lane, [&](int, int b, int c, R wyzv) {
             if (a < P) shared_add(base + (c * PT + b) * BX, wx * wyzv);
         });
     }
@@ -245,7 +268,6 @@ __global__ void __launch_bounds__(NTH) k_gather(const int4* __restrict__ work, c
                                                 R* __restrict__ phi)
 {
     using B = Box<P, T>;
-    const R inv_b = wc.inv_b;
     constexpr int PT = B::PT, BX = B::BX, C = B::CELLS, m = P / 2, G = GroupOf<P>::G;
     extern __shared__ __align__(32) unsigned char smraw_sg[];
     R* s = reinterpret_cast<R*>(smraw_sg);
@@ -278,7 +300,7 @@ __global__ void __launch_bounds__(NTH) k_gather(const int4* __restrict__ work, c
 
     // one warp per particle, rows spread over the lanes as in k_spread
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    const int g = lane / G, a = lane % G;
+    const int a = lane % G;
     R* wyz = s + NF * C + warp * (P * P);
     for (int j = w.y + warp; j < w.z; j += nwarp) {
         const typename Rec<R>::T r = srec[j - w.y];
@@ -288,12 +310,10 @@ __global__ void __launch_bounds__(NTH) k_gather(const int4* __restrict__ work, c
         split_offset<R, T>(r.y, iy, dy);
         split_offset<R, T>(r.z, iz, dz);
         const R ua = dx + (R)(m - 1 - (a % P));
-        const R wx = dexp(-ua * ua * inv_b);
+        const R wx = win_exp(ua * ua, wc);
         const R* base = s + (iz * PT + iy) * BX + ix + B::XOFF + a;
-        R acc[NF];
-#pragma unroll
-        for (int f = 0; f < NF; f++) acc[f] = R(0);
-        visit_window<R, P>(dy, dz, wc, wyz, lane, [&](int b, int c, R wyzv) {
+        R acc[4] = {R(0), R(0), R(0), R(0)};
+        visit_window<R, P>(dy, dz, wc, wyz, lane, [&](int, int b, int c, R wyzv) {
             if (a < P) {
                 const R ww = wx * wyzv;
                 const int o = (c * PT + b) * BX;
@@ -301,20 +321,17 @@ __global__ void __launch_bounds__(NTH) k_gather(const int4* __restrict__ work, c
                 for (int f = 0; f < NF; f++) acc[f] += ww * base[f * C + o];
             }
         });
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-            for (int f = 0; f < NF; f++) acc[f] += __shfl_xor_sync(0xffffffffu, acc[f], o);
-        }
-        if (lane == 0) {
+        // warp sum of the four partials, transposed: after it lane 8 f
+        // holds the total of field f
+        const R tot = warp_sum4(acc, lane);
+        if ((lane & 7) == 0) {
+            const int f = lane >> 3;
             const uint32_t oi = sperm[j - w.y];
-            if (F) {
-                const R qc = r.w * cnorm3;
-                F[3 * (size_t)oi] = qc * acc[0];
-                F[3 * (size_t)oi + 1] = qc * acc[1];
-                F[3 * (size_t)oi + 2] = qc * acc[2];
+            if (f < 3) {
+                if (F) F[3 * (size_t)oi + f] = r.w * cnorm3 * tot;
+            } else if (NF == 4 && phi) {
+                phi[oi] = cnorm3 * tot;
             }
-            if (NF == 4 && phi) phi[oi] = cnorm3 * acc[NF - 1];
         }
         __syncwarp();
     }
@@ -333,7 +350,6 @@ __global__ void __launch_bounds__(256) k_gather_direct(int N, const typename Rec
                                                        R* __restrict__ F, R* __restrict__ phi)
 {
     constexpr int m = P / 2, G = GroupOf<P>::G;
-    const R inv_b = wc.inv_b;
     const int lane = threadIdx.x % G;
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) / G;
     if (j >= N) return;  // whole groups leave together
@@ -356,7 +372,7 @@ __global__ void __launch_bounds__(256) k_gather_direct(int N, const typename Rec
     for (int f = 0; f < NF; f++) acc[f] = R(0);
     if (lane < P) {
         R u = dx + (R)(m - 1 - lane);
-        const R wx = dexp(-u * u * inv_b);
+        const R wx = win_exp(u * u, wc);
         const int gx = (tx * T + ix - (m - 1) + lane) & mask;
         const int y0 = ty * T + iy - (m - 1), z0 = tz * T + iz - (m - 1);
         int yo[P];
