@@ -52,7 +52,8 @@ int fail(int code, const std::string& msg)
         }                                                                                     \
     } while (0)
 
-constexpr int kWorkCap = 512;  // particles per work item of spread / gather
+constexpr int kWorkCap = 512;    // particles per work item of the interpolation (a tile)
+constexpr int kSpreadCap = 128;  // particles per work item of the spreading (a sub-tile)
 constexpr int kMaxSmem = 227 * 1024;
 constexpr double kPi = 3.14159265358979323846;
 
@@ -65,7 +66,8 @@ struct Resolved {
     bool fp64;
     size_t rsz;    // sizeof(real)
     int nc, Kx, Kb, P;
-    int T, nbt[3], nbins, max_work;
+    int T, nbt[3], ntiles, max_work;  // tiles of T^3 cells, interpolation work items
+    int S, lr, nbins, max_work2;      // sub-tiles of S^3 (the sort's bins), lr = log2(T/S), spreading items
     bool cells;    // linked cells (else all pairs)
     int ncell[3], nrbins;
     double h[3];
@@ -119,8 +121,12 @@ int resolve(const enuf_params* in, Resolved& r)
     while (r.T > 4 && box_bytes(r.T) > (size_t)kMaxSmem) r.T /= 2;
     if (box_bytes(r.T) > (size_t)kMaxSmem) return fail(ENUF_EUNSUPPORTED, "window too wide for the tile box");
     for (int t = 0; t < 3; t++) r.nbt[t] = p.M / r.T;
-    r.nbins = r.nbt[0] * r.nbt[1] * r.nbt[2];
-    r.max_work = r.nbins + (int)(p.N / kWorkCap) + 1;
+    r.ntiles = r.nbt[0] * r.nbt[1] * r.nbt[2];
+    r.max_work = r.ntiles + (int)(p.N / kWorkCap) + 1;
+    r.S = std::min(r.T, 8);
+    r.lr = r.T / r.S == 2 ? 1 : 0;
+    r.nbins = r.ntiles << (3 * r.lr);
+    r.max_work2 = (int)std::min<int64_t>(r.nbins, p.N) + (int)(p.N / kSpreadCap) + 1;
     // linked cells of edge >= r_c, at least 3 per dimension
     r.cells = true;
     for (int t = 0; t < 3; t++) {
@@ -159,7 +165,7 @@ int resolve(const enuf_params* in, Resolved& r)
     }
     if (r.gy.W < 1 || r.gz.W < 1) return fail(ENUF_EUNSUPPORTED, "FFT block shape does not fit");
     // the four field planes stay in L2 (126 MB) when they total <= 64 MB
-    r.gather_direct = r.T < 16 && (size_t)4 * M * M * M * r.rsz <= (size_t)64 << 20 && !std::getenv("ENUF_STAGED_GATHER");
+    r.gather_direct = r.T < 16 && r.lr == 0 && (size_t)4 * M * M * M * r.rsz <= (size_t)64 << 20 && !std::getenv("ENUF_STAGED_GATHER");
     // fused x-y passes (one CTA per z-plane) where the pruned plane fits:
     // the kept kx columns are transformed in as few batches as the 1024-thread
     // limit allows, each batch CB columns wide with no idle column slots;
@@ -186,7 +192,7 @@ int resolve(const enuf_params* in, Resolved& r)
 // ------------------------------------------------------------------ workspace
 struct Layout {
     size_t status, out, mean;
-    size_t counts, offsets, work, nwork;
+    size_t counts, offsets, work, nwork, work2, nwork2, item2;
     size_t key, rank, rec_tmp, rec, perm, tile_of;
     size_t rcounts, roffsets, rrec, rperm, rcell;
     size_t qpart, kpart, rpart, fpart;
@@ -196,9 +202,10 @@ struct Layout {
     size_t total;
 };
 
-// Word stride of the bin counters: one 128-byte line each while the padded
-// array stays small, packed otherwise.
-int count_stride(int nbins) { return nbins <= 8192 ? 32 : 1; }
+// Word stride of the bin counters: with few bins, one 128-byte line each
+// (the particles' atomics spread over many L2 lines), one 32-byte sector
+// each up to 8192 bins, packed beyond.
+int count_stride(int nbins) { return nbins <= 1024 ? 32 : (nbins <= 8192 ? 8 : 1); }
 
 Layout layout(const Resolved& r)
 {
@@ -220,6 +227,9 @@ Layout layout(const Resolved& r)
     L.offsets = take((r.nbins + 1) * 4);
     L.work = take((size_t)r.max_work * 16);
     L.nwork = take(4);
+    L.work2 = take((size_t)r.max_work2 * 16);
+    L.nwork2 = take(4);
+    L.item2 = take((size_t)r.nbins * 4);
     L.key = take(N * 4);
     L.rank = take(N * 4);
     L.rec_tmp = take(N * recsz);
@@ -345,10 +355,11 @@ int launch_spread_t(Launcher& L, enuf_plan* pl)
 {
     const Resolved& r = pl->r;
     const Layout& y = pl->lay;
-    return L.go("spread", k_spread<R, P, T>, dim3(r.max_work), dim3(256),
-                (size_t)(Box<P, T>::CELLS + 8 * P * P) * sizeof(R),
-                at<const int4>(pl, y.work), at<const int>(pl, y.nwork), at<const typename Rec<R>::T>(pl, y.rec),
-                r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), (R)pl->cnorm3, at<R>(pl, y.grid));
+    constexpr int S = T < 8 ? T : 8;
+    return L.go("spread", k_spread<R, P, T>, dim3(r.max_work2), dim3(32),
+                (size_t)(SBox<P, S>::CELLS + P * P) * sizeof(R), at<const int4>(pl, y.work2),
+                at<const int>(pl, y.nwork2), at<const typename Rec<R>::T>(pl, y.rec), r.prm.M, pl->lnb, r.lr,
+                winc<R>(pl), (R)pl->cnorm3, at<R>(pl, y.grid));
 }
 
 template <typename R, int P, int T>
@@ -495,9 +506,11 @@ template <typename R> int launch_fft_chain(Launcher& L, enuf_plan* pl, int nf)
     }
 }
 
-BinGeom make_geom(const int S[3], int T, const double L3[3], bool grid_units)
+BinGeom make_geom(const int S[3], int T, const double L3[3], bool grid_units, int sub = 1, int lr = 0)
 {
     BinGeom g{};
+    g.sub = sub;
+    g.lr = lr;
     for (int t = 0; t < 3; t++) {
         g.S[t] = S[t];
         g.nb[t] = S[t] / T;
@@ -527,16 +540,19 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
     // the kernels that consume them (k_finalize, k_scan_bins)
     // (a1, a2) counting sort into grid tiles
     const int Sg[3] = {r.prm.M, r.prm.M, r.prm.M};
-    const BinGeom gg = make_geom(Sg, r.T, r.prm.L, true);
+    const BinGeom gg = make_geom(Sg, r.T, r.prm.L, true, r.S, r.lr);
     LCHK(L.go("bin_keys", k_bin_keys<R>, dim3(nblkN), dim3(256), 0, N, pos, q, gg, at<uint32_t>(pl, y.key),
               at<uint32_t>(pl, y.rank), at<RecT>(pl, y.rec_tmp), at<uint32_t>(pl, y.counts), count_stride(r.nbins),
               at<int>(pl, y.status), at<double>(pl, y.qpart)));
-    LCHK(L.go("scan_bins", k_scan_bins, dim3(1), dim3(1024), 0, r.nbins, at<uint32_t>(pl, y.counts),
-              count_stride(r.nbins), at<uint32_t>(pl, y.offsets), kWorkCap, at<int4>(pl, y.work), at<int>(pl, y.nwork), r.max_work,
+    LCHK(L.go("scan_bins", r.lr ? k_scan_bins<8> : k_scan_bins<1>, dim3(1), dim3(1024), kScanSmem, r.nbins,
+              at<uint32_t>(pl, y.counts), count_stride(r.nbins), at<uint32_t>(pl, y.offsets), kWorkCap,
+              at<int4>(pl, y.work), at<int>(pl, y.nwork), r.max_work, kSpreadCap, at<uint32_t>(pl, y.item2),
+              at<int>(pl, y.nwork2), r.max_work2,
               at<int>(pl, y.status)));
     LCHK(L.go("scatter", k_scatter<R>, dim3(nblkN), dim3(256), 0, N, at<const uint32_t>(pl, y.key),
               at<const uint32_t>(pl, y.rank), at<const uint32_t>(pl, y.offsets), at<const RecT>(pl, y.rec_tmp),
-              at<RecT>(pl, y.rec), at<uint32_t>(pl, y.perm), at<uint32_t>(pl, y.tile_of)));
+              at<RecT>(pl, y.rec), at<uint32_t>(pl, y.perm), at<uint32_t>(pl, y.tile_of),
+              at<const uint32_t>(pl, y.item2), kSpreadCap, at<int4>(pl, y.work2), r.max_work2));
     // (a3) spread
     const size_t M3 = (size_t)r.prm.M * r.prm.M * r.prm.M;
     LCHK(L.memset(at<void>(pl, y.grid), M3 * sizeof(R)));
@@ -552,11 +568,13 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
         LCHK(L.go("real_bin_keys", k_bin_keys<R>, dim3(nblkN), dim3(256), 0, N, pos, q, gr, at<uint32_t>(pl, y.key),
                   at<uint32_t>(pl, y.rank), at<RecT>(pl, y.rec_tmp), at<uint32_t>(pl, y.rcounts),
                   count_stride(r.nrbins), at<int>(pl, y.status), (double*)nullptr));
-        LCHK(L.go("real_scan", k_scan_bins, dim3(1), dim3(1024), 0, r.nrbins, at<uint32_t>(pl, y.rcounts),
-                  count_stride(r.nrbins), at<uint32_t>(pl, y.roffsets), kWorkCap, (int4*)nullptr, (int*)nullptr, 0, at<int>(pl, y.status)));
+        LCHK(L.go("real_scan", k_scan_bins<1>, dim3(1), dim3(1024), kScanSmem, r.nrbins, at<uint32_t>(pl, y.rcounts),
+                  count_stride(r.nrbins), at<uint32_t>(pl, y.roffsets), kWorkCap, (int4*)nullptr, (int*)nullptr, 0,
+                  kSpreadCap, (uint32_t*)nullptr, (int*)nullptr, 0, at<int>(pl, y.status)));
         LCHK(L.go("real_scatter", k_scatter<R>, dim3(nblkN), dim3(256), 0, N, at<const uint32_t>(pl, y.key),
                   at<const uint32_t>(pl, y.rank), at<const uint32_t>(pl, y.roffsets), at<const RecT>(pl, y.rec_tmp),
-                  at<RecT>(pl, y.rrec), at<uint32_t>(pl, y.rperm), at<uint32_t>(pl, y.rcell)));
+                  at<RecT>(pl, y.rrec), at<uint32_t>(pl, y.rperm), at<uint32_t>(pl, y.rcell), (const uint32_t*)nullptr,
+                  kSpreadCap, (int4*)nullptr, 0));
         RealParams<R> rp;
         for (int t = 0; t < 3; t++) {
             rp.nc[t] = r.ncell[t];

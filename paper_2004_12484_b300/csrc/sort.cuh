@@ -13,8 +13,10 @@ namespace enuf {
 
 struct BinGeom {
     int S[3];          // cells per dimension (M for the NFFT grid, n_cell for real space)
-    int T;             // cells per bin edge (tile edge; 1 for real space)
-    int nb[3];         // bins per dimension = S / T
+    int T;             // cells per tile edge (1 for real space)
+    int nb[3];         // tiles per dimension = S / T
+    int sub, lr;       // sub-tile edge and log2(T / sub): a bin is one of the
+                       // (T / sub)^3 sub-tiles of a tile, numbered tile-major
     double scale[3];   // S_t / L_t
     float scale_hi[3]; // float split of scale: scale ~ hi + lo
     float scale_lo[3];
@@ -84,6 +86,18 @@ __global__ void __launch_bounds__(256) k_bin_keys(int N, const R* __restrict__ p
         }
         uint32_t b = (uint32_t)(c[0] / g.T) +
                      (uint32_t)g.nb[0] * ((uint32_t)(c[1] / g.T) + (uint32_t)g.nb[1] * (uint32_t)(c[2] / g.T));
+        if (g.lr > 0) {
+            // sub-tile of the cell index the kernels split from the stored
+            // offset (same truncation and clamp as split_offset)
+            uint32_t sb = 0;
+#pragma unroll
+            for (int t = 0; t < 3; t++) {
+                int ci = (int)off[t];
+                if (ci > g.T - 1) ci = g.T - 1;
+                sb |= (uint32_t)(ci / g.sub) << (g.lr * t);
+            }
+            b = (b << (3 * g.lr)) | sb;
+        }
         key[i] = b;
         rank[i] = atomicAdd(&count[(size_t)b * cs], 1u);
         typename Rec<R>::T rr;
@@ -97,85 +111,166 @@ __global__ void __launch_bounds__(256) k_bin_keys(int N, const R* __restrict__ p
 }
 
 // Pass 2 (one block of 1024 threads): exclusive scan of the bin counts into
-// offsets, and a work list of (bin, begin, end) items of at most `cap`
-// particles each for the kernels that process bins (heavy bins are split).
-// Each thread sums a contiguous chunk of bins; the per-thread totals are
-// scanned with warp shuffles and one pass over the 32 warp totals.  The
-// counts are cleared after use, ready for the next evaluation.
+// offsets, the work list `work` of (group, begin, end) items over groups of
+// GROUP consecutive bins (the tiles) with at most `cap` particles per item
+// (heavy groups are split, empty ones get no item), and, for the per-bin
+// work list that the scatter pass writes, the index item2[b] of bin b's
+// first item when bins are cut into items of at most `cap2` particles.
+// The bins go through shared memory in segments of kScanSeg: one coalesced
+// read of the counts (which are cleared, ready for the next evaluation), 8
+// bins per thread, a shuffle scan of the per-thread totals, and coalesced
+// writes of the offsets and item indices.
+constexpr int kScanSeg = 8192;
+constexpr size_t kScanSmem = 2 * kScanSeg * sizeof(uint32_t);
+
+template <int GROUP>
 __global__ void __launch_bounds__(1024) k_scan_bins(int nbins, uint32_t* __restrict__ count, int cs,
-                                                    uint32_t* __restrict__ offset, int cap,
-                                                    int4* __restrict__ work, int* __restrict__ nwork, int max_work,
-                                                    int* __restrict__ status)
+                                                    uint32_t* __restrict__ offset, int cap, int4* __restrict__ work,
+                                                    int* __restrict__ nwork, int max_work, int cap2,
+                                                    uint32_t* __restrict__ item2, int* __restrict__ nwork2,
+                                                    int max_work2, int* __restrict__ status)
 {
-    __shared__ uint32_t s_cnt[32], s_wrk[32];
+    constexpr int PER = kScanSeg / 1024;
+    static_assert(PER % GROUP == 0, "a thread's bins hold whole groups");
+    extern __shared__ __align__(16) uint32_t s_scan[];
+    __shared__ uint32_t s_sum[3][32];
+    uint32_t* s_a = s_scan;             // counts, then offsets
+    uint32_t* s_b = s_scan + kScanSeg;  // item indices
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
-    const int chunk = (nbins + nt - 1) / nt;
-    const int b0 = min(nbins, tid * chunk), b1 = min(nbins, b0 + chunk);
-    uint32_t c = 0, w = 0;
-    for (int b = b0; b < b1; b++) {
-        uint32_t n = count[(size_t)b * cs];
-        c += n;
-        if (work) w += (n + cap - 1) / cap;
-    }
-    // inclusive scans inside each warp, then over the warp totals
-    uint32_t ic = c, iw = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t a = __shfl_up_sync(0xffffffffu, ic, o), bw = __shfl_up_sync(0xffffffffu, iw, o);
-        if (lane >= o) { ic += a; iw += bw; }
-    }
-    if (lane == 31) { s_cnt[warp] = ic; s_wrk[warp] = iw; }
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t x = lane < nwarp ? s_cnt[lane] : 0u, y = lane < nwarp ? s_wrk[lane] : 0u;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t a = __shfl_up_sync(0xffffffffu, x, o), bw = __shfl_up_sync(0xffffffffu, y, o);
-            if (lane >= o) { x += a; y += bw; }
+    uint32_t base[3] = {0u, 0u, 0u};  // particles, items of work, items of the per-bin list
+    for (int s0 = 0; s0 < nbins; s0 += kScanSeg) {
+        const int ns = min(kScanSeg, nbins - s0);
+        for (int i = tid; i < ns; i += nt) {
+            const size_t gi = (size_t)(s0 + i) * cs;
+            s_a[i] = count[gi];
+            count[gi] = 0u;
         }
-        s_cnt[lane] = x;
-        s_wrk[lane] = y;
-    }
-    __syncthreads();
-    uint32_t base = (warp ? s_cnt[warp - 1] : 0u) + ic - c, wbase = (warp ? s_wrk[warp - 1] : 0u) + iw - w;
-    for (int b = b0; b < b1; b++) {
-        uint32_t n = count[(size_t)b * cs];
-        count[(size_t)b * cs] = 0u;
-        offset[b] = base;
+        __syncthreads();
+        const int b0 = tid * PER;
+        uint32_t n[PER];
+        uint32_t v[3] = {0u, 0u, 0u};
+#pragma unroll
+        for (int k = 0; k < PER; k++) {
+            n[k] = b0 + k < ns ? s_a[b0 + k] : 0u;
+            v[0] += n[k];
+            if (item2) v[2] += (n[k] + cap2 - 1) / cap2;
+        }
         if (work) {
-            for (uint32_t s = 0; s < n; s += cap) {
-                if ((int)wbase < max_work) work[wbase] = make_int4(b, (int)(base + s), (int)(base + min(n, s + cap)), 0);
-                wbase++;
+#pragma unroll
+            for (int gg = 0; gg < PER / GROUP; gg++) {
+                uint32_t ng = 0;
+#pragma unroll
+                for (int k = 0; k < GROUP; k++) ng += n[gg * GROUP + k];
+                v[1] += (ng + cap - 1) / cap;
             }
         }
-        base += n;
+        // inclusive scans inside each warp, then over the warp totals
+        uint32_t inc[3] = {v[0], v[1], v[2]};
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+            for (int e = 0; e < 3; e++) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, inc[e], o);
+                if (lane >= o) inc[e] += t;
+            }
+        }
+        if (lane == 31) {
+#pragma unroll
+            for (int e = 0; e < 3; e++) s_sum[e][warp] = inc[e];
+        }
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t x[3];
+#pragma unroll
+            for (int e = 0; e < 3; e++) x[e] = lane < nwarp ? s_sum[e][lane] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+                for (int e = 0; e < 3; e++) {
+                    const uint32_t t = __shfl_up_sync(0xffffffffu, x[e], o);
+                    if (lane >= o) x[e] += t;
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < 3; e++) s_sum[e][lane] = x[e];
+        }
+        __syncthreads();
+        uint32_t ex[3];
+#pragma unroll
+        for (int e = 0; e < 3; e++) ex[e] = base[e] + (warp ? s_sum[e][warp - 1] : 0u) + inc[e] - v[e];
+        uint32_t o = ex[0], it2 = ex[2], wb = ex[1];
+#pragma unroll
+        for (int gg = 0; gg < PER / GROUP; gg++) {
+            const uint32_t gstart = o;
+#pragma unroll
+            for (int k = gg * GROUP; k < (gg + 1) * GROUP; k++) {
+                if (b0 + k < ns) {
+                    s_a[b0 + k] = o;
+                    s_b[b0 + k] = it2;
+                }
+                o += n[k];
+                if (item2) it2 += (n[k] + cap2 - 1) / cap2;
+            }
+            if (work) {
+                const uint32_t ng = o - gstart;
+                const int gidx = (s0 + b0) / GROUP + gg;
+                for (uint32_t s = 0; s < ng; s += cap) {
+                    if ((int)wb < max_work) work[wb] = make_int4(gidx, (int)(gstart + s), (int)(gstart + min(ng, s + cap)), 0);
+                    wb++;
+                }
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < ns; i += nt) {
+            offset[s0 + i] = s_a[i];
+            if (item2) item2[s0 + i] = s_b[i];
+        }
+#pragma unroll
+        for (int e = 0; e < 3; e++) base[e] += s_sum[e][nwarp - 1];
+        __syncthreads();
     }
-    if (tid == nt - 1) {
-        offset[nbins] = s_cnt[nwarp - 1];
+    if (tid == 0) {
+        offset[nbins] = base[0];
         if (work) {
-            int nw = (int)s_wrk[nwarp - 1];
+            int nw = (int)base[1];
             if (nw > max_work) { atomicOr(status, ST_WORKLIST); nw = max_work; }
             *nwork = nw;
+        }
+        if (item2) {
+            int nw = (int)base[2];
+            if (nw > max_work2) { atomicOr(status, ST_WORKLIST); nw = max_work2; }
+            *nwork2 = nw;
         }
     }
 }
 
 // Pass 3: scatter the records into bin order; perm[sorted] = original index.
+// With `work2`, the particle of rank r in bin b with r % cap2 == 0 also
+// writes the per-bin work item (b, begin, end) of the cap2 particles from
+// it, at index item2[b] + r / cap2.
 template <typename R>
 __global__ void __launch_bounds__(256) k_scatter(int N, const uint32_t* __restrict__ key,
                                                  const uint32_t* __restrict__ rank,
                                                  const uint32_t* __restrict__ offset,
                                                  const typename Rec<R>::T* __restrict__ rec_in,
                                                  typename Rec<R>::T* __restrict__ rec_out, uint32_t* __restrict__ perm,
-                                                 uint32_t* __restrict__ bin_of_sorted)
+                                                 uint32_t* __restrict__ bin_of_sorted,
+                                                 const uint32_t* __restrict__ item2, int cap2,
+                                                 int4* __restrict__ work2, int max_work2)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const uint32_t b = key[i];
-    const uint32_t d = offset[b] + rank[i];
+    const uint32_t r = rank[i];
+    const uint32_t d = offset[b] + r;
     rec_out[d] = rec_in[i];
     perm[d] = (uint32_t)i;
     if (bin_of_sorted) bin_of_sorted[d] = b;
+    if (work2 && r % (uint32_t)cap2 == 0u) {
+        const uint32_t it = item2[b] + r / (uint32_t)cap2;
+        const uint32_t nb = offset[b + 1] - offset[b];
+        if ((int)it < max_work2) work2[it] = make_int4((int)b, (int)d, (int)(offset[b] + min(nb, r + (uint32_t)cap2)), 0);
+    }
 }
 
 }  // namespace enuf

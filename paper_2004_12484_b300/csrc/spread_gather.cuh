@@ -8,14 +8,15 @@
 // window values are computed in registers (Sec. 3.2: "values of window
 // functions ... computed in local memory").
 //
-// Both kernels process one work item = (tile, particle range) per CTA.  A
-// tile is T^3 grid cells; its particles were counting-sorted into it.  The
-// CTA owns a padded shared-memory box covering every cell the tile's
-// particles touch (T+p-1 cells in y and z; in x widened to 16-byte aligned
-// rows).  Spreading accumulates into that box with shared-memory atomics and
-// flushes it with one global vector atomic per non-zero aligned group of four
-// cells (scalar atomics in double).  Interpolation stages the box of every
-// field with 16-byte loads and then reads only shared memory.  Inside a CTA, a group of G >= p lanes serves one
+// Particles were counting-sorted into sub-tiles (S^3 cells, S = min(T, 8))
+// numbered tile-major, so every tile of T^3 cells is one contiguous range.
+// Both kernels keep a padded shared-memory box covering every cell their
+// particles touch (edge + p - 1 cells in y and z; in x widened to 16-byte
+// aligned rows).  Spreading gives each warp one sub-tile and a private box,
+// updated without atomics and flushed with one global vector atomic per
+// non-zero aligned group of four cells (scalar atomics in double).
+// Interpolation gives each CTA one tile, stages the box of every field with
+// 16-byte loads and then reads only shared memory.  Inside a CTA, a group of G >= p lanes serves one
 // particle: lane a takes the x-offset a, so a group reads or writes p
 // consecutive cells of one grid row per step (no bank conflicts inside the
 // group); the group's partial sums are combined with shuffles.
@@ -66,16 +67,6 @@ __device__ __forceinline__ void window_weights(R d, const WinC<R>& wc, R (&w)[P]
         dn *= gi;
         w[m - 1 + j] = dn * wc.c[j];
     }
-}
-
-// Shared-memory reduction without a returned value (red.shared.add).
-__device__ __forceinline__ void shared_add(float* a, float v)
-{
-    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(a)), "f"(v) : "memory");
-}
-__device__ __forceinline__ void shared_add(double* a, double v)
-{
-    asm volatile("red.shared.add.f64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(a)), "d"(v) : "memory");
 }
 
 template <typename R, int T>
@@ -192,63 +183,146 @@ template <int P, int T> struct Box {
     static constexpr int XOFF = XA - (m - 1);  // box x of window point 0 minus floor(u)
 };
 
+// Spreading, one warp (the whole CTA) per work item = (sub-tile, particle
+// range).  A sub-tile is S^3 cells of a T^3 tile, S = min(T, 8); the warp
+// accumulates its particles into a private shared-memory box (S + p - 1
+// cells in y and z, 16-byte aligned rows in x) with plain read-add-write:
+// no other warp touches the box, so no shared-memory atomics are needed,
+// and the P*P/(32/G) rows a lane updates for one particle are distinct
+// cells, so their reads are all issued before their writes.  The box is then
+// added to the grid with one vector atomic per non-zero aligned group of four
+// cells (scalar atomics in double).  Work item index x = tile << (3 lr) |
+// sub-tile (lr = log2(T / S)).
+// The spreading box of a sub-tile (S^3 cells): the Box geometry with row
+// stride BX and plane stride PS padded so that the four rows one warp
+// instruction touches start on disjoint groups of 8 banks -- rows (b, c),
+// (b+1, c), (b, c+1), (b+1, c+1) for p = 8, four consecutive rows otherwise.
+template <int P, int S> struct SBox {
+    using B0 = Box<P, S>;
+    static constexpr int m = P / 2, XA = B0::XA, XOFF = B0::XOFF, PT = B0::PT;
+    static constexpr int BX = (P != 8 && B0::BX % 16 == 0) ? B0::BX + 8 : B0::BX;
+    static constexpr int PS = PT * BX + ((P == 8 && (PT * BX) % 16 == 0) ? 8 : 0);
+    static constexpr int CELLS = PT * PS;
+};
+
 template <typename R, int P, int T>
-__global__ void __launch_bounds__(256) k_spread(const int4* __restrict__ work, const int* __restrict__ nwork,
-                                                const typename Rec<R>::T* __restrict__ rec, int M, int lnbx,
-                                                int lnby, WinC<R> wc, R cnorm3, R* __restrict__ grid)
+__global__ void __launch_bounds__(32) k_spread(const int4* __restrict__ work, const int* __restrict__ nwork,
+                                               const typename Rec<R>::T* __restrict__ rec, int M, int lnb, int lr,
+                                               WinC<R> wc, R cnorm3, R* __restrict__ grid)
 {
-    using B = Box<P, T>;
-    constexpr int PT = B::PT, BX = B::BX, m = P / 2, G = GroupOf<P>::G;
+    constexpr int S = T < 8 ? T : 8;
+    using B = SBox<P, S>;
+    constexpr int PT = B::PT, BX = B::BX, PS = B::PS, m = P / 2, G = GroupOf<P>::G;
     extern __shared__ __align__(32) unsigned char smraw_sg[];
     R* acc = reinterpret_cast<R*>(smraw_sg);
-    R* wyz_all = acc + B::CELLS;  // P*P products per warp
+    R* wyz = acc + B::CELLS;  // P*P products (window widths without a register path)
     using RecT = typename Rec<R>::T;
     if ((int)blockIdx.x >= *nwork) return;  // uniform for the whole CTA
     const int4 w = work[blockIdx.x];
-    for (int i = threadIdx.x; i < B::CELLS; i += blockDim.x) acc[i] = R(0);
-    __syncthreads();
-
-    // one warp per particle: lane = 8 * g + a serves x-offset a of rows
-    // 4 it + g, so the four rows of one instruction start on different banks
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int lane = threadIdx.x;
+    for (int i = lane; i < B::CELLS * (int)sizeof(R) / 16; i += 32)
+        reinterpret_cast<float4*>(acc)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int sub = w.x & ((1 << (3 * lr)) - 1), tile = w.x >> (3 * lr), rm = (1 << lr) - 1;
+    const int sx = sub & rm, sy = (sub >> lr) & rm, sz = sub >> (2 * lr);
+    const int nbm = (1 << lnb) - 1;
+    const int tx = tile & nbm, ty = (tile >> lnb) & nbm, tz = tile >> (2 * lnb);
     const int a = lane % G;
-    R* wyz = wyz_all + warp * (P * P);
-    for (int j = w.y + warp; j < w.z; j += nwarp) {
-        const RecT r = rec[j];
-        int ix, iy, iz;
-        R dx, dy, dz;
-        split_offset<R, T>(r.x, ix, dx);
-        split_offset<R, T>(r.y, iy, dy);
-        split_offset<R, T>(r.z, iz, dz);
-        const R ua = dx + (R)(m - 1 - (a % P));
-        const R wx = r.w * cnorm3 * win_exp(ua * ua, wc);
-        R* base = acc + (iz * PT + iy) * BX + ix + B::XOFF + a;
-        visit_window<R, P>(dy, dz, wc, wyz, lane, [&](int, int b, int c, R wyzv) {
-            if (a < P) shared_add(base + (c * PT + b) * BX, wx * wyzv);
-        });
-    }
-    __syncthreads();
+    __syncwarp();
 
-    const int tile = w.x;
-    const int tx = tile & ((1 << lnbx) - 1), ty = (tile >> lnbx) & ((1 << lnby) - 1), tz = tile >> (lnbx + lnby);
-    const int ox = tx * T - B::XA, oy = ty * T - (m - 1), oz = tz * T - (m - 1);
+    for (int j0 = w.y; j0 < w.z; j0 += 32) {
+        // one record per lane, handed to the warp with shuffles
+        RecT mine;
+        if (j0 + lane < w.z) mine = rec[j0 + lane];
+        else mine.x = mine.y = mine.z = mine.w = R(0);
+        const int nj = min(32, w.z - j0);
+        for (int jj = 0; jj < nj; jj++) {
+            const R rx = __shfl_sync(0xffffffffu, mine.x, jj), ry = __shfl_sync(0xffffffffu, mine.y, jj);
+            const R rz = __shfl_sync(0xffffffffu, mine.z, jj), rq = __shfl_sync(0xffffffffu, mine.w, jj);
+            int ix, iy, iz;
+            R dx, dy, dz;
+            split_offset<R, T>(rx, ix, dx);
+            split_offset<R, T>(ry, iy, dy);
+            split_offset<R, T>(rz, iz, dz);
+            ix -= sx * S;  // cell inside the sub-tile, 0..S-1 (the bin was
+            iy -= sy * S;  // chosen from the same split)
+            iz -= sz * S;
+            const R ua = dx + (R)(m - 1 - (a % P));
+            const R wx = rq * cnorm3 * win_exp(ua * ua, wc);
+            constexpr int RPI = 32 / G;
+            constexpr int NV = P == 8 ? 16 : (P == 4 ? 2 : (P * P + RPI - 1) / RPI);
+            if constexpr (P == 8) {
+                // lane 8 g + a: x-offset a of rows b0 + 2i and planes c0 + 2k
+                // (b0 = g & 1, c0 = g >> 1); lane a also evaluates the y and z
+                // weights of offset a for the whole warp
+                const int g = lane >> 3, b0 = g & 1, c0 = g >> 1;
+                const R uy = dy + (R)(3 - a), uz = dz + (R)(3 - a);
+                const R wya = win_exp(uy * uy, wc), wza = win_exp(uz * uz, wc);
+                R t[4], wz[4];
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    t[i] = wx * __shfl_sync(0xffffffffu, wya, b0 + 2 * i);
+                    wz[i] = __shfl_sync(0xffffffffu, wza, c0 + 2 * i);
+                }
+                R* base = acc + (iz + c0) * PS + (iy + b0) * BX + ix + B::XOFF + a;
+                R old[16];
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+#pragma unroll
+                    for (int i = 0; i < 4; i++) old[4 * k + i] = base[2 * k * PS + 2 * i * BX];
+                }
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+#pragma unroll
+                    for (int i = 0; i < 4; i++) base[2 * k * PS + 2 * i * BX] = old[4 * k + i] + t[i] * wz[k];
+                }
+            } else if constexpr (NV <= 16) {
+                R* base = acc + (iz * PS) + iy * BX + ix + B::XOFF + a;
+                int off[NV];
+                R vv[NV];
+                unsigned valid = 0u;
+                visit_window<R, P>(dy, dz, wc, wyz, lane, [&](int st, int b, int c, R wyzv) {
+                    off[st] = c * PS + b * BX;
+                    vv[st] = wx * wyzv;
+                    valid |= 1u << st;
+                });
+                if (a < P) {
+                    R old[NV];
+#pragma unroll
+                    for (int k = 0; k < NV; k++)
+                        if (valid >> k & 1u) old[k] = base[off[k]];
+#pragma unroll
+                    for (int k = 0; k < NV; k++)
+                        if (valid >> k & 1u) base[off[k]] = old[k] + vv[k];
+                }
+            } else {
+                R* base = acc + (iz * PS) + iy * BX + ix + B::XOFF + a;
+                visit_window<R, P>(dy, dz, wc, wyz, lane, [&](int, int b, int c, R wyzv) {
+                    if (a < P) base[c * PS + b * BX] += wx * wyzv;
+                });
+            }
+            __syncwarp();
+        }
+    }
+
+    const int ox = tx * T + sx * S - B::XA, oy = ty * T + sy * S - (m - 1), oz = tz * T + sz * S - (m - 1);
     const int mask = M - 1;  // M is a power of two (and a multiple of 4)
     if constexpr (sizeof(R) == 4) {
         // one 16-byte vector atomic per aligned group of 4 cells
-        constexpr int NV = BX / 4;
-        for (int i = threadIdx.x; i < NV * PT * PT; i += blockDim.x) {
-            const int vx = i % NV, ly = (i / NV) % PT, lz = i / (NV * PT);
-            const float4 v = *reinterpret_cast<const float4*>(acc + (lz * PT + ly) * BX + 4 * vx);
+        constexpr int NV4 = B::B0::BX / 4;  // vectors per row that hold cells
+        for (int i = lane; i < NV4 * PT * PT; i += 32) {
+            const int vx = i % NV4, ly = (i / NV4) % PT, lz = i / (NV4 * PT);
+            const float4 v = *reinterpret_cast<const float4*>(acc + lz * PS + ly * BX + 4 * vx);
             if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) {
                 const int gx = (ox + 4 * vx) & mask, gy = (oy + ly) & mask, gz = (oz + lz) & mask;
                 atomicAdd(reinterpret_cast<float4*>(grid + ((size_t)gz * M + gy) * M + gx), v);
             }
         }
     } else {
-        for (int i = threadIdx.x; i < B::CELLS; i += blockDim.x) {
-            const R v = acc[i];
+        constexpr int NX = B::B0::BX;
+        for (int i = lane; i < NX * PT * PT; i += 32) {
+            const int lx = i % NX, ly = (i / NX) % PT, lz = i / (NX * PT);
+            const R v = acc[lz * PS + ly * BX + lx];
             if (v != R(0)) {
-                const int lx = i % BX, ly = (i / BX) % PT, lz = i / (BX * PT);
                 const int gx = (ox + lx) & mask, gy = (oy + ly) & mask, gz = (oz + lz) & mask;
                 atomicAdd(grid + ((size_t)gz * M + gy) * M + gx, v);
             }
