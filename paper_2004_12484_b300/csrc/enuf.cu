@@ -220,7 +220,7 @@ Layout layout(const Resolved& r)
     const size_t recsz = r.fp64 ? sizeof(d4) : sizeof(f4);
     const size_t nblkN = (N + 255) / 256;
     const size_t nblkZ = ((size_t)r.P + r.gz.W - 1) / r.gz.W;
-    L.status = take(16);
+    L.status = take(16);  // status word; at +8 and +12 the block counters of the two sorts
     L.out = take(ENUF_NOUT * 8);
     L.mean = take(4 * 8);
     L.counts = take((size_t)(r.nbins + 1) * 4 * count_stride(r.nbins));
@@ -536,19 +536,20 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
     const int nf = want_phi ? 4 : (F ? 3 : 0);
     using RecT = typename Rec<R>::T;
 
-    // the status word and the bin counts are kept zeroed between calls by
-    // the kernels that consume them (k_finalize, k_scan_bins)
+    // the status word, the bin counts and the block counters are kept
+    // zeroed between calls by the kernels that consume them (k_finalize, the
+    // scan in the last block of k_bin_keys)
     // (a1, a2) counting sort into grid tiles
     const int Sg[3] = {r.prm.M, r.prm.M, r.prm.M};
     const BinGeom gg = make_geom(Sg, r.T, r.prm.L, true, r.S, r.lr);
-    LCHK(L.go("bin_keys", k_bin_keys<R>, dim3(nblkN), dim3(256), 0, N, pos, q, gg, at<uint32_t>(pl, y.key),
-              at<uint32_t>(pl, y.rank), at<RecT>(pl, y.rec_tmp), at<uint32_t>(pl, y.counts), count_stride(r.nbins),
-              at<int>(pl, y.status), at<double>(pl, y.qpart)));
-    LCHK(L.go("scan_bins", r.lr ? k_scan_bins<8> : k_scan_bins<1>, dim3(1), dim3(1024), kScanSmem, r.nbins,
-              at<uint32_t>(pl, y.counts), count_stride(r.nbins), at<uint32_t>(pl, y.offsets), kWorkCap,
-              at<int4>(pl, y.work), at<int>(pl, y.nwork), r.max_work, kSpreadCap, at<uint32_t>(pl, y.item2),
-              at<int>(pl, y.nwork2), r.max_work2,
-              at<int>(pl, y.status)));
+    {
+        ScanArgs sa{r.nbins, at<uint32_t>(pl, y.counts), count_stride(r.nbins), at<uint32_t>(pl, y.offsets),
+                    kWorkCap, at<int4>(pl, y.work), at<int>(pl, y.nwork), r.max_work, kSpreadCap,
+                    at<uint32_t>(pl, y.item2), at<int>(pl, y.nwork2), r.max_work2, at<unsigned>(pl, y.status + 8)};
+        LCHK(L.go("bin_keys", r.lr ? k_bin_keys<R, 8> : k_bin_keys<R, 1>, dim3(nblkN), dim3(256), 0, N, pos, q, gg,
+                  at<uint32_t>(pl, y.key), at<uint32_t>(pl, y.rank), at<RecT>(pl, y.rec_tmp), sa, at<int>(pl, y.status),
+                  at<double>(pl, y.qpart)));
+    }
     LCHK(L.go("scatter", k_scatter<R>, dim3(nblkN), dim3(256), 0, N, at<const uint32_t>(pl, y.key),
               at<const uint32_t>(pl, y.rank), at<const uint32_t>(pl, y.offsets), at<const RecT>(pl, y.rec_tmp),
               at<RecT>(pl, y.rec), at<uint32_t>(pl, y.perm), at<uint32_t>(pl, y.tile_of),
@@ -565,12 +566,11 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
     int nr = 0;
     if (!konly) {
         const BinGeom gr = make_geom(r.ncell, 1, r.prm.L, false);
-        LCHK(L.go("real_bin_keys", k_bin_keys<R>, dim3(nblkN), dim3(256), 0, N, pos, q, gr, at<uint32_t>(pl, y.key),
-                  at<uint32_t>(pl, y.rank), at<RecT>(pl, y.rec_tmp), at<uint32_t>(pl, y.rcounts),
-                  count_stride(r.nrbins), at<int>(pl, y.status), (double*)nullptr));
-        LCHK(L.go("real_scan", k_scan_bins<1>, dim3(1), dim3(1024), kScanSmem, r.nrbins, at<uint32_t>(pl, y.rcounts),
-                  count_stride(r.nrbins), at<uint32_t>(pl, y.roffsets), kWorkCap, (int4*)nullptr, (int*)nullptr, 0,
-                  kSpreadCap, (uint32_t*)nullptr, (int*)nullptr, 0, at<int>(pl, y.status)));
+        ScanArgs sr{r.nrbins, at<uint32_t>(pl, y.rcounts), count_stride(r.nrbins), at<uint32_t>(pl, y.roffsets),
+                    kWorkCap, (int4*)nullptr, (int*)nullptr, 0, kSpreadCap, (uint32_t*)nullptr, (int*)nullptr, 0,
+                    at<unsigned>(pl, y.status + 12)};
+        LCHK(L.go("real_bin_keys", k_bin_keys<R, 1>, dim3(nblkN), dim3(256), 0, N, pos, q, gr, at<uint32_t>(pl, y.key),
+                  at<uint32_t>(pl, y.rank), at<RecT>(pl, y.rec_tmp), sr, at<int>(pl, y.status), (double*)nullptr));
         LCHK(L.go("real_scatter", k_scatter<R>, dim3(nblkN), dim3(256), 0, N, at<const uint32_t>(pl, y.key),
                   at<const uint32_t>(pl, y.rank), at<const uint32_t>(pl, y.roffsets), at<const RecT>(pl, y.rec_tmp),
                   at<RecT>(pl, y.rrec), at<uint32_t>(pl, y.rperm), at<uint32_t>(pl, y.rcell), (const uint32_t*)nullptr,

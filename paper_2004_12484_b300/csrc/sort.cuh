@@ -51,20 +51,181 @@ __device__ __forceinline__ void locate(float r, const BinGeom& g, int t, int& c,
     c = kk;
 }
 
+// The scan, run by the last block of k_bin_keys to finish (the bins are
+// complete once every other block has counted its particles): exclusive
+// scan of the bin counts into offsets, the work list `work` of (group,
+// begin, end) items over groups of GROUP consecutive bins (the tiles) with
+// at most `cap` particles per item (heavy groups are split, empty ones get
+// no item), and, for the per-bin work list that the scatter pass writes,
+// the index item2[b] of bin b's first item when bins are cut into items of
+// at most `cap2` particles.  The bins go through shared memory in segments
+// of NT * 8: one coalesced read of the counts (which are cleared, ready for
+// the next evaluation), 8 bins per thread, a shuffle scan of the per-thread
+// totals, and coalesced writes of the offsets and item indices.
+struct ScanArgs {
+    int nbins;
+    uint32_t* count;
+    int cs;             // word stride of the counters
+    uint32_t* offset;   // nbins + 1
+    int cap;
+    int4* work;         // NULL: no group work list
+    int* nwork;
+    int max_work;
+    int cap2;
+    uint32_t* item2;    // NULL: no per-bin item indices
+    int* nwork2;
+    int max_work2;
+    unsigned* done;     // blocks finished (kept zero between evaluations)
+};
+
+constexpr int kScanPer = 8;  // bins per thread and segment
+
+template <int GROUP, int NT>
+__device__ __forceinline__ void scan_bins_block(const ScanArgs& a, int* status, uint32_t* s_a, uint32_t* s_b,
+                                                uint32_t (*s_sum)[32])
+{
+    constexpr int PER = kScanPer, SEG = NT * PER, NWARP = NT / 32;
+    static_assert(PER % GROUP == 0, "a thread's bins hold whole groups");
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t base[3] = {0u, 0u, 0u};  // particles, items of work, items of the per-bin list
+    for (int s0 = 0; s0 < a.nbins; s0 += SEG) {
+        const int ns = min(SEG, a.nbins - s0);
+        {
+            // all of the thread's loads in flight at once
+            uint32_t t[PER];
+#pragma unroll
+            for (int k = 0; k < PER; k++) {
+                const int i = tid + k * NT;
+                t[k] = i < ns ? __ldcg(a.count + (size_t)(s0 + i) * a.cs) : 0u;
+            }
+#pragma unroll
+            for (int k = 0; k < PER; k++) {
+                const int i = tid + k * NT;
+                if (i < ns) {
+                    s_a[i] = t[k];
+                    a.count[(size_t)(s0 + i) * a.cs] = 0u;
+                }
+            }
+        }
+        __syncthreads();
+        const int b0 = tid * PER;
+        uint32_t n[PER];
+        uint32_t v[3] = {0u, 0u, 0u};
+#pragma unroll
+        for (int k = 0; k < PER; k++) {
+            n[k] = b0 + k < ns ? s_a[b0 + k] : 0u;
+            v[0] += n[k];
+            if (a.item2) v[2] += (n[k] + a.cap2 - 1) / a.cap2;
+        }
+        if (a.work) {
+#pragma unroll
+            for (int gg = 0; gg < PER / GROUP; gg++) {
+                uint32_t ng = 0;
+#pragma unroll
+                for (int k = 0; k < GROUP; k++) ng += n[gg * GROUP + k];
+                v[1] += (ng + a.cap - 1) / a.cap;
+            }
+        }
+        // inclusive scans inside each warp, then over the warp totals
+        uint32_t inc[3] = {v[0], v[1], v[2]};
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+            for (int e = 0; e < 3; e++) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, inc[e], o);
+                if (lane >= o) inc[e] += t;
+            }
+        }
+        if (lane == 31) {
+#pragma unroll
+            for (int e = 0; e < 3; e++) s_sum[e][warp] = inc[e];
+        }
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t x[3];
+#pragma unroll
+            for (int e = 0; e < 3; e++) x[e] = lane < NWARP ? s_sum[e][lane] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+                for (int e = 0; e < 3; e++) {
+                    const uint32_t t = __shfl_up_sync(0xffffffffu, x[e], o);
+                    if (lane >= o) x[e] += t;
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < 3; e++) s_sum[e][lane] = x[e];
+        }
+        __syncthreads();
+        uint32_t ex[3];
+#pragma unroll
+        for (int e = 0; e < 3; e++) ex[e] = base[e] + (warp ? s_sum[e][warp - 1] : 0u) + inc[e] - v[e];
+        uint32_t o = ex[0], it2 = ex[2], wb = ex[1];
+#pragma unroll
+        for (int gg = 0; gg < PER / GROUP; gg++) {
+            const uint32_t gstart = o;
+#pragma unroll
+            for (int k = gg * GROUP; k < (gg + 1) * GROUP; k++) {
+                if (b0 + k < ns) {
+                    s_a[b0 + k] = o;
+                    s_b[b0 + k] = it2;
+                }
+                o += n[k];
+                if (a.item2) it2 += (n[k] + a.cap2 - 1) / a.cap2;
+            }
+            if (a.work) {
+                const uint32_t ng = o - gstart;
+                const int gidx = (s0 + b0) / GROUP + gg;
+                for (uint32_t s = 0; s < ng; s += a.cap) {
+                    if ((int)wb < a.max_work)
+                        a.work[wb] = make_int4(gidx, (int)(gstart + s), (int)(gstart + min(ng, s + a.cap)), 0);
+                    wb++;
+                }
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < ns; i += NT) {
+            a.offset[s0 + i] = s_a[i];
+            if (a.item2) a.item2[s0 + i] = s_b[i];
+        }
+#pragma unroll
+        for (int e = 0; e < 3; e++) base[e] += s_sum[e][NWARP - 1];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        a.offset[a.nbins] = base[0];
+        if (a.work) {
+            int nw = (int)base[1];
+            if (nw > a.max_work) { atomicOr(status, ST_WORKLIST); nw = a.max_work; }
+            *a.nwork = nw;
+        }
+        if (a.item2) {
+            int nw = (int)base[2];
+            if (nw > a.max_work2) { atomicOr(status, ST_WORKLIST); nw = a.max_work2; }
+            *a.nwork2 = nw;
+        }
+    }
+}
+
 // Pass 1: bin key, rank inside the bin (atomic counter), unsorted record,
-// per-block sums of q^2 and q (for the self and background terms).  The
+// per-block sums of q^2 and q (for the self and background terms); the
+// last block to finish then runs pass 2 (scan_bins_block).  The
 // counter of bin b is count[b * cs]: with few bins, a stride of one 128-byte
 // line per counter spreads the atomics over many L2 lines instead of a few
 // hot ones.
-template <typename R>
+template <typename R, int GROUP>
 __global__ void __launch_bounds__(256) k_bin_keys(int N, const R* __restrict__ pos, const R* __restrict__ q,
                                                   BinGeom g, uint32_t* __restrict__ key,
                                                   uint32_t* __restrict__ rank,
-                                                  typename Rec<R>::T* __restrict__ rec,
-                                                  uint32_t* __restrict__ count, int cs, int* __restrict__ status,
-                                                  double* __restrict__ qpart)
+                                                  typename Rec<R>::T* __restrict__ rec, ScanArgs sa,
+                                                  int* __restrict__ status, double* __restrict__ qpart)
 {
     __shared__ double red[32 * 2];
+    __shared__ uint32_t s_scan[2 * 256 * kScanPer];
+    __shared__ uint32_t s_sum[3][32];
+    __shared__ bool s_last;
+    uint32_t* __restrict__ count = sa.count;
+    const int cs = sa.cs;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     R qq = R(0);
     if (i < N) {
@@ -108,140 +269,15 @@ __global__ void __launch_bounds__(256) k_bin_keys(int N, const R* __restrict__ p
         R v[2] = {qq * qq, qq};
         block_reduce_to_double<R, 2>(v, qpart + 2 * (size_t)blockIdx.x, red);
     }
-}
-
-// Pass 2 (one block of 1024 threads): exclusive scan of the bin counts into
-// offsets, the work list `work` of (group, begin, end) items over groups of
-// GROUP consecutive bins (the tiles) with at most `cap` particles per item
-// (heavy groups are split, empty ones get no item), and, for the per-bin
-// work list that the scatter pass writes, the index item2[b] of bin b's
-// first item when bins are cut into items of at most `cap2` particles.
-// The bins go through shared memory in segments of kScanSeg: one coalesced
-// read of the counts (which are cleared, ready for the next evaluation), 8
-// bins per thread, a shuffle scan of the per-thread totals, and coalesced
-// writes of the offsets and item indices.
-constexpr int kScanSeg = 8192;
-constexpr size_t kScanSmem = 2 * kScanSeg * sizeof(uint32_t);
-
-template <int GROUP>
-__global__ void __launch_bounds__(1024) k_scan_bins(int nbins, uint32_t* __restrict__ count, int cs,
-                                                    uint32_t* __restrict__ offset, int cap, int4* __restrict__ work,
-                                                    int* __restrict__ nwork, int max_work, int cap2,
-                                                    uint32_t* __restrict__ item2, int* __restrict__ nwork2,
-                                                    int max_work2, int* __restrict__ status)
-{
-    constexpr int PER = kScanSeg / 1024;
-    static_assert(PER % GROUP == 0, "a thread's bins hold whole groups");
-    extern __shared__ __align__(16) uint32_t s_scan[];
-    __shared__ uint32_t s_sum[3][32];
-    uint32_t* s_a = s_scan;             // counts, then offsets
-    uint32_t* s_b = s_scan + kScanSeg;  // item indices
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
-    uint32_t base[3] = {0u, 0u, 0u};  // particles, items of work, items of the per-bin list
-    for (int s0 = 0; s0 < nbins; s0 += kScanSeg) {
-        const int ns = min(kScanSeg, nbins - s0);
-        for (int i = tid; i < ns; i += nt) {
-            const size_t gi = (size_t)(s0 + i) * cs;
-            s_a[i] = count[gi];
-            count[gi] = 0u;
-        }
-        __syncthreads();
-        const int b0 = tid * PER;
-        uint32_t n[PER];
-        uint32_t v[3] = {0u, 0u, 0u};
-#pragma unroll
-        for (int k = 0; k < PER; k++) {
-            n[k] = b0 + k < ns ? s_a[b0 + k] : 0u;
-            v[0] += n[k];
-            if (item2) v[2] += (n[k] + cap2 - 1) / cap2;
-        }
-        if (work) {
-#pragma unroll
-            for (int gg = 0; gg < PER / GROUP; gg++) {
-                uint32_t ng = 0;
-#pragma unroll
-                for (int k = 0; k < GROUP; k++) ng += n[gg * GROUP + k];
-                v[1] += (ng + cap - 1) / cap;
-            }
-        }
-        // inclusive scans inside each warp, then over the warp totals
-        uint32_t inc[3] = {v[0], v[1], v[2]};
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-#pragma unroll
-            for (int e = 0; e < 3; e++) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, inc[e], o);
-                if (lane >= o) inc[e] += t;
-            }
-        }
-        if (lane == 31) {
-#pragma unroll
-            for (int e = 0; e < 3; e++) s_sum[e][warp] = inc[e];
-        }
-        __syncthreads();
-        if (warp == 0) {
-            uint32_t x[3];
-#pragma unroll
-            for (int e = 0; e < 3; e++) x[e] = lane < nwarp ? s_sum[e][lane] : 0u;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-#pragma unroll
-                for (int e = 0; e < 3; e++) {
-                    const uint32_t t = __shfl_up_sync(0xffffffffu, x[e], o);
-                    if (lane >= o) x[e] += t;
-                }
-            }
-#pragma unroll
-            for (int e = 0; e < 3; e++) s_sum[e][lane] = x[e];
-        }
-        __syncthreads();
-        uint32_t ex[3];
-#pragma unroll
-        for (int e = 0; e < 3; e++) ex[e] = base[e] + (warp ? s_sum[e][warp - 1] : 0u) + inc[e] - v[e];
-        uint32_t o = ex[0], it2 = ex[2], wb = ex[1];
-#pragma unroll
-        for (int gg = 0; gg < PER / GROUP; gg++) {
-            const uint32_t gstart = o;
-#pragma unroll
-            for (int k = gg * GROUP; k < (gg + 1) * GROUP; k++) {
-                if (b0 + k < ns) {
-                    s_a[b0 + k] = o;
-                    s_b[b0 + k] = it2;
-                }
-                o += n[k];
-                if (item2) it2 += (n[k] + cap2 - 1) / cap2;
-            }
-            if (work) {
-                const uint32_t ng = o - gstart;
-                const int gidx = (s0 + b0) / GROUP + gg;
-                for (uint32_t s = 0; s < ng; s += cap) {
-                    if ((int)wb < max_work) work[wb] = make_int4(gidx, (int)(gstart + s), (int)(gstart + min(ng, s + cap)), 0);
-                    wb++;
-                }
-            }
-        }
-        __syncthreads();
-        for (int i = tid; i < ns; i += nt) {
-            offset[s0 + i] = s_a[i];
-            if (item2) item2[s0 + i] = s_b[i];
-        }
-#pragma unroll
-        for (int e = 0; e < 3; e++) base[e] += s_sum[e][nwarp - 1];
-        __syncthreads();
-    }
-    if (tid == 0) {
-        offset[nbins] = base[0];
-        if (work) {
-            int nw = (int)base[1];
-            if (nw > max_work) { atomicOr(status, ST_WORKLIST); nw = max_work; }
-            *nwork = nw;
-        }
-        if (item2) {
-            int nw = (int)base[2];
-            if (nw > max_work2) { atomicOr(status, ST_WORKLIST); nw = max_work2; }
-            *nwork2 = nw;
-        }
-    }
+    // the last block to finish scans the bins (no block waits for another)
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(sa.done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    scan_bins_block<GROUP, 256>(sa, status, s_scan, s_scan + 256 * kScanPer, s_sum);
+    if (threadIdx.x == 0) *sa.done = 0u;  // ready for the next evaluation
 }
 
 // Pass 3: scatter the records into bin order; perm[sorted] = original index.
