@@ -32,6 +32,37 @@ __device__ __forceinline__ double derfc(double x) { return erfc(x); }
 __device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
 
+// Asynchronous global -> shared copies (cp.async): a thread issues all of
+// its copies before waiting, so their latencies overlap instead of following
+// one another.  Copies of !valid elements read nothing and fill zeros.
+// cp_async_wait_all waits for all of the thread's copies (a barrier then
+// publishes them to the CTA).
+__device__ __forceinline__ void cp_async_bytes8(void* dst, const void* src, bool valid)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(valid ? 8u : 0u)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_bytes16(void* dst, const void* src, bool valid)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(valid ? 16u : 0u)
+                 : "memory");
+}
+// one complex value (8 bytes in single, 16 in double precision)
+__device__ __forceinline__ void cp_async_cpx(float2* dst, const float2* src, bool valid)
+{
+    cp_async_bytes8(dst, src, valid);
+}
+__device__ __forceinline__ void cp_async_cpx(double2* dst, const double2* src, bool valid)
+{
+    cp_async_bytes16(dst, src, valid);
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 template <typename R> __device__ __forceinline__ R warp_sum(R v)
 {
 #pragma unroll

@@ -2,15 +2,16 @@
 // frequency cube |n_t| <= n_c, with the reciprocal-space step fused into the
 // middle (z) pass.
 //
-// Forward chain (Sec. 3.1, "spreading, FFT, and scaling"):
+// Forward chain (the spreading, transform and scaling stages of Sec. 3.1):
 //   k_fx  real rows along x -> half spectrum, keep kx = 0..n_c
 //   k_fy  along y for each kx, keep ky in the band (2 n_c + 1 values)
 //   k_fz  along z for each (ky, kx) pencil, then for every retained n:
 //         S(n) = D(n) ghat(n) (scaling by the window's Fourier coefficients),
 //         energy and virial (Eq. 38), and the subdivided spectra of the
 //         force field and potential (Eq. 41-42), then the inverse transform
-//         along z of each field ("subdividing" and the first inverse pass)
-// Inverse chain ("subdividing, inverse FFT, and interpolating"):
+//         along z of each field (the split into field spectra and the first
+//         inverse pass)
+// Inverse chain (the inverse transforms ahead of the interpolation):
 //   k_iy  along y (band -> full length) for each field and kx
 //   k_ix  half spectrum kx = 0..n_c -> real rows (complex-to-real)
 //
@@ -171,11 +172,13 @@ __device__ __forceinline__ void fft_smem_multi(V* x, int trs, int t, const V* __
     FftPasses<V, N, 1, INV, NTR, MR>::run(x, trs, t, W, ws);
 }
 
-// Copies the twiddle table exp(-2 pi i k / M), k < M, into shared memory.
+// Copies the twiddle table exp(-2 pi i k / M), k < M, into shared memory
+// (asynchronously: complete after the kernel's next cp_async_wait_all and
+// barrier).
 template <typename V>
 __device__ __forceinline__ const V* stage_twiddles(V* dst, const V* __restrict__ src, int M)
 {
-    for (int i = threadIdx.x; i < M; i += blockDim.x) dst[i] = src[i];
+    for (int i = threadIdx.x; i < M; i += blockDim.x) cp_async_cpx(dst + i, src + i, true);
     return dst;
 }
 
@@ -204,8 +207,9 @@ __global__ void __launch_bounds__(256) k_fx(R* __restrict__ grid, typename Cpx<R
     V* gin = reinterpret_cast<V*>(grid);
     for (int i = threadIdx.x; i < rows * MH; i += blockDim.x) {
         const int r = i / MH, j = i % MH, row = row0 + r;
-        s[r * RS + pidx(j)] = row < nrows ? gin[(size_t)row * MH + j] : V{R(0), R(0)};
+        cp_async_cpx(s + r * RS + pidx(j), gin + (row < nrows ? (size_t)row * MH + j : 0), row < nrows);
     }
+    cp_async_wait_all();
     __syncthreads();
     fft_smem<V, MH, false>(s + (threadIdx.x / NT) * RS, threadIdx.x % NT, sW, 2);
     const int Kx = g.Kx;
@@ -246,8 +250,9 @@ __global__ void __launch_bounds__(1024) k_fxy(R* __restrict__ grid, typename Cpx
     for (int y0 = 0; y0 < M; y0 += RB) {
         for (int i = threadIdx.x; i < RB * MH; i += blockDim.x) {
             const int r = i / MH, j = i % MH, y = y0 + r;
-            rowbuf[r * RS + pidx(j)] = y < M ? gin[(size_t)y * MH + j] : V{R(0), R(0)};
+            cp_async_cpx(rowbuf + r * RS + pidx(j), gin + (y < M ? (size_t)y * MH + j : 0), y < M);
         }
+        cp_async_wait_all();
         __syncthreads();
         fft_smem<V, MH, false>(rowbuf + (threadIdx.x / NTX) * RS, threadIdx.x % NTX, sW, 2);
         for (int i = threadIdx.x; i < RB * Kx; i += blockDim.x) {
@@ -288,8 +293,9 @@ __global__ void __launch_bounds__(1024) k_fy(const typename Cpx<R>::T* __restric
     const V* sW = stage_twiddles(s + Wc * LD, Wg, M);
     for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
         const int w = i % Wc, y = i / Wc, kx = kx0 + w;
-        s[w * LD + pidx(y)] = kx < Kx ? C1[((size_t)z * M + y) * Kx + kx] : V{R(0), R(0)};
+        cp_async_cpx(s + w * LD + pidx(y), C1 + (kx < Kx ? ((size_t)z * M + y) * Kx + kx : 0), kx < Kx);
     }
+    cp_async_wait_all();
     __syncthreads();
     fft_smem<V, M, false>(s + (threadIdx.x / NT) * LD, threadIdx.x % NT, sW, 1);
     for (int i = threadIdx.x; i < Wc * Kb; i += blockDim.x) {
@@ -346,8 +352,9 @@ __global__ void __launch_bounds__(512) k_fz(const typename Cpx<R>::T* __restrict
     const int p0 = blockIdx.x * Wc;
     for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
         const int w = i % Wc, z = i / Wc, p = p0 + w;
-        X[w * LD + pidx(z)] = p < P ? C2[(size_t)z * P + p] : V{R(0), R(0)};
+        cp_async_cpx(X + w * LD + pidx(z), C2 + (p < P ? (size_t)z * P + p : 0), p < P);
     }
+    cp_async_wait_all();
     __syncthreads();
     fft_smem<V, M, false, MR>(X + (threadIdx.x / NT) * LD, threadIdx.x % NT, sW, 1);
 
@@ -419,15 +426,14 @@ __global__ void __launch_bounds__(1024) k_iy(const typename Cpx<R>::T* __restric
     const V* src = C3 + ((size_t)f * M + z) * P;
     for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
         const int w = i % Wc, y = i / Wc, kx = kx0 + w;
-        V v = V{R(0), R(0)};
+        int kb = -1;
         if (kx < Kx) {
-            int kb = -1;
             if (y <= nc) kb = y;
             else if (y >= M - nc) kb = y - (M - Kb);
-            if (kb >= 0) v = src[(size_t)kb * Kx + kx];
         }
-        s[w * LD + pidx(y)] = v;
+        cp_async_cpx(s + w * LD + pidx(y), src + (kb >= 0 ? (size_t)kb * Kx + kx : 0), kb >= 0);
     }
+    cp_async_wait_all();
     __syncthreads();
     fft_smem<V, M, true>(s + (threadIdx.x / NT) * LD, threadIdx.x % NT, W, 1);
     V* dst = C4 + ((size_t)f * M + z) * M * Kx;
@@ -459,16 +465,15 @@ __global__ void __launch_bounds__(1024) k_iyx(const typename Cpx<R>::T* __restri
     const int z = blockIdx.x, f = blockIdx.y;
     const V* src = C3 + ((size_t)f * M + z) * P;
     for (int i = threadIdx.x; i < KxR * M; i += blockDim.x) {
-        const int kx = i / M, y = i % M;
-        V v = V{R(0), R(0)};
+        const int kx = i % KxR, y = i / KxR;  // consecutive threads read consecutive kx
+        int kb = -1;
         if (kx < Kx) {
-            int kb = -1;
             if (y <= nc) kb = y;
             else if (y >= M - nc) kb = y - (M - Kb);
-            if (kb >= 0) v = src[(size_t)kb * Kx + kx];
         }
-        plane[kx * LD + pidx(y)] = v;
+        cp_async_cpx(plane + kx * LD + pidx(y), src + (kb >= 0 ? (size_t)kb * Kx + kx : 0), kb >= 0);
     }
+    cp_async_wait_all();
     __syncthreads();
     for (int k0 = 0; k0 < Kx; k0 += CB) {
         fft_smem<V, M, true>(plane + (k0 + threadIdx.x / NTY) * LD, threadIdx.x % NTY, sW, 1);
@@ -512,6 +517,7 @@ __global__ void __launch_bounds__(256) k_ix(const typename Cpx<R>::T* __restrict
     V* s = reinterpret_cast<V*>(smraw);
     const int rows = g.rows, row0 = blockIdx.x * rows, Kx = g.Kx, nc = g.nc;
     const V* W = stage_twiddles(s + rows * RS, Wg, M);
+    cp_async_wait_all();
     __syncthreads();
     for (int i = threadIdx.x; i < rows * MH; i += blockDim.x) {
         const int r = i / MH, k = i % MH, row = row0 + r;

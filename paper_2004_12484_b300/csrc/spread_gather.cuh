@@ -5,8 +5,8 @@
 //
 // with the Gaussian window phi(u) = (pi b)^(-1/2) exp(-u^2/b) on the p grid
 // points l = floor(u) - p/2 + 1 ... floor(u) + p/2 of each dimension.  The
-// window values are computed in registers (Sec. 3.2: "values of window
-// functions ... computed in local memory").
+// window values are evaluated on the fly in registers, never tabulated in
+// global memory (as Sec. 3.2 prescribes for the GPU kernels).
 //
 // Particles were counting-sorted into sub-tiles (S^3 cells, S = min(T, 8))
 // numbered tile-major, so every tile of T^3 cells is one contiguous range.
@@ -16,10 +16,10 @@
 // updated without atomics and flushed with one global vector atomic per
 // non-zero aligned group of four cells (scalar atomics in double).
 // Interpolation gives each CTA one tile, stages the box of every field with
-// 16-byte loads and then reads only shared memory.  Inside a CTA, a group of G >= p lanes serves one
-// particle: lane a takes the x-offset a, so a group reads or writes p
-// consecutive cells of one grid row per step (no bank conflicts inside the
-// group); the group's partial sums are combined with shuffles.
+// 16-byte loads and then reads only shared memory.  In both, a group of G >=
+// p lanes serves one particle: lane a takes the x-offset a, so a group reads
+// or writes p consecutive cells of one grid row per step; the partial sums
+// are combined with shuffles.
 #pragma once
 #include "common.cuh"
 
