@@ -446,8 +446,17 @@ __global__ void __launch_bounds__(1024) k_iy(const typename Cpx<R>::T* __restric
 // ---------------------------------------------------------------- k_iyx
 // Fused inverse y and x (complex-to-real) passes: one CTA per (z-plane,
 // field) (grid: (M, NF) blocks, 1024 threads).
+// Launch bounds of k_iyx: in single precision with M = 128 the CTA has 528
+// threads (33 kept kx columns x 16) and three CTAs share an SM (at most 40
+// registers a thread), so that the 3 * 128 CTAs of three fields run in one
+// wave on 148 SMs.
+template <typename R, int M> struct IyxBounds {
+    static constexpr bool small = sizeof(R) == 4 && M == 128;
+    static constexpr int T = small ? 544 : 1024, B = small ? 3 : 1;
+};
+
 template <typename R, int M>
-__global__ void __launch_bounds__(1024) k_iyx(const typename Cpx<R>::T* __restrict__ C3, R* __restrict__ fld,
+__global__ void __launch_bounds__(IyxBounds<R, M>::T, IyxBounds<R, M>::B) k_iyx(const typename Cpx<R>::T* __restrict__ C3, R* __restrict__ fld,
                                               FftGeom g, const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
