@@ -336,12 +336,6 @@ struct Launcher {
         count++;
         return ENUF_OK;
     }
-    int memset(void* p, size_t bytes)
-    {
-        if (attr_only) return ENUF_OK;
-        CK(cudaMemsetAsync(p, 0, bytes, st));
-        return ENUF_OK;
-    }
 };
 
 #define LCHK(x)                      \
@@ -554,9 +548,8 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
               at<const uint32_t>(pl, y.rank), at<const uint32_t>(pl, y.offsets), at<const RecT>(pl, y.rec_tmp),
               at<RecT>(pl, y.rec), at<uint32_t>(pl, y.perm), at<uint32_t>(pl, y.tile_of),
               at<const uint32_t>(pl, y.item2), kSpreadCap, at<int4>(pl, y.work2), r.max_work2));
-    // (a3) spread
-    const size_t M3 = (size_t)r.prm.M * r.prm.M * r.prm.M;
-    LCHK(L.memset(at<void>(pl, y.grid), M3 * sizeof(R)));
+    // (a3) spread (into a zeroed grid: zeroed at binding, then by the
+    // forward FFT that reads it)
     LCHK(launch_spread<R>(L, pl));
     // (a4-a6) FFT chain with the fused reciprocal step
     LCHK(launch_fft_chain<R>(L, pl, nf));

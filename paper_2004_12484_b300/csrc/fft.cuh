@@ -193,7 +193,8 @@ struct FftGeom {
 };
 
 // ---------------------------------------------------------------- k_fx
-// grid: ceil(M*M / rows) blocks, rows * NT(M/2) threads.
+// grid: ceil(M*M / rows) blocks, rows * NT(M/2) threads.  Clears the grid
+// rows it reads (the spreading accumulates into a zeroed grid).
 template <typename R, int M>
 __global__ void __launch_bounds__(256) k_fx(R* __restrict__ grid, typename Cpx<R>::T* __restrict__ C1, FftGeom g,
                      const typename Cpx<R>::T* __restrict__ Wg)
@@ -210,6 +211,12 @@ __global__ void __launch_bounds__(256) k_fx(R* __restrict__ grid, typename Cpx<R
         cp_async_cpx(s + r * RS + pidx(j), gin + (row < nrows ? (size_t)row * MH + j : 0), row < nrows);
     }
     cp_async_wait_all();
+    // the grid is left zeroed for the next spreading (each element was read
+    // by the thread that clears it)
+    for (int i = threadIdx.x; i < rows * MH; i += blockDim.x) {
+        const int r = i / MH, j = i % MH, row = row0 + r;
+        if (row < nrows) gin[(size_t)row * MH + j] = V{R(0), R(0)};
+    }
     __syncthreads();
     fft_smem<V, MH, false>(s + (threadIdx.x / NT) * RS, threadIdx.x % NT, sW, 2);
     const int Kx = g.Kx;
@@ -227,7 +234,8 @@ __global__ void __launch_bounds__(256) k_fx(R* __restrict__ grid, typename Cpx<R
 
 // ---------------------------------------------------------------- k_fxy
 // Fused forward x and y passes for grids whose pruned plane fits in shared
-// memory: one CTA per z-plane (grid: M blocks, 1024 threads).  The x-rows are
+// memory: one CTA per z-plane (grid: M blocks, 1024 threads).  Clears the
+// grid plane it reads (the spreading accumulates into a zeroed grid).  The x-rows are
 // transformed in batches, the kept kx columns are stored transposed in a
 // plane buffer, transformed along y, and the band rows written to C2.
 template <typename R, int M>
@@ -253,6 +261,12 @@ __global__ void __launch_bounds__(1024) k_fxy(R* __restrict__ grid, typename Cpx
             cp_async_cpx(rowbuf + r * RS + pidx(j), gin + (y < M ? (size_t)y * MH + j : 0), y < M);
         }
         cp_async_wait_all();
+        // the grid is left zeroed for the next spreading (each element was
+        // read by the thread that clears it)
+        for (int i = threadIdx.x; i < RB * MH; i += blockDim.x) {
+            const int r = i / MH, j = i % MH, y = y0 + r;
+            if (y < M) gin[(size_t)y * MH + j] = V{R(0), R(0)};
+        }
         __syncthreads();
         fft_smem<V, MH, false>(rowbuf + (threadIdx.x / NTX) * RS, threadIdx.x % NTX, sW, 2);
         for (int i = threadIdx.x; i < RB * Kx; i += blockDim.x) {
