@@ -281,6 +281,8 @@ struct enuf_plan {
     bool own_ws = false;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t aux_stream = nullptr;  // side branch (assembly beside the interpolation)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool use_graph = true;
     bool profile = false;
     bool attrs_done = false;
@@ -553,6 +555,37 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
     LCHK(launch_spread<R>(L, pl));
     // (a4-a6) FFT chain with the fused reciprocal step
     LCHK(launch_fft_chain<R>(L, pl, nf));
+    // (a9) assembly parameters
+    FinalParams fp;
+    fp.nq = nblkN;
+    fp.nk = (r.P + r.gz.W - 1) / r.gz.W;
+    fp.nr = 0;
+    fp.ke = r.prm.coulomb_k;
+    fp.alpha = r.prm.alpha;
+    fp.V = r.prm.L[0] * r.prm.L[1] * r.prm.L[2];
+    fp.sqrt_pi = std::sqrt(kPi);
+    fp.kspace_only = konly ? 1 : 0;
+    double* o = out ? out : at<double>(pl, y.out);
+    // k-space only: the assembly needs nothing from the interpolation, so it
+    // runs on a side branch beside it (not in profiling mode, whose timing
+    // events follow one stream)
+    const bool side = konly && nf > 0 && !L.attr_only && !pl->profile;
+    if (side) {
+        CK(cudaEventRecord(pl->ev_fork, L.st));
+        CK(cudaStreamWaitEvent(pl->aux_stream, pl->ev_fork, 0));
+        const cudaStream_t main_st = L.st;
+        L.st = pl->aux_stream;
+        const int rc = L.go("finalize", k_finalize, dim3(1), dim3(512), 0, at<const double>(pl, y.qpart),
+                            at<const double>(pl, y.kpart), at<const double>(pl, y.rpart), fp, at<int>(pl, y.status), o);
+        L.st = main_st;
+        if (rc != ENUF_OK) {
+            // rejoin the side branch before returning (a capture must end joined)
+            cudaEventRecord(pl->ev_join, pl->aux_stream);
+            cudaStreamWaitEvent(L.st, pl->ev_join, 0);
+            return rc;
+        }
+        CK(cudaEventRecord(pl->ev_join, pl->aux_stream));
+    }
     // (a7) interpolation
     if (nf > 0) LCHK(launch_gather<R>(L, pl, nf, F, want_phi ? phi : (R*)nullptr));
     // (a8) real space
@@ -591,18 +624,11 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
         nr = nblkN;
     }
     // (a9) assembly
-    FinalParams fp;
-    fp.nq = nblkN;
-    fp.nk = (r.P + r.gz.W - 1) / r.gz.W;
     fp.nr = nr;
-    fp.ke = r.prm.coulomb_k;
-    fp.alpha = r.prm.alpha;
-    fp.V = r.prm.L[0] * r.prm.L[1] * r.prm.L[2];
-    fp.sqrt_pi = std::sqrt(kPi);
-    fp.kspace_only = konly ? 1 : 0;
-    double* o = out ? out : at<double>(pl, y.out);
-    LCHK(L.go("finalize", k_finalize, dim3(1), dim3(512), 0, at<const double>(pl, y.qpart), at<const double>(pl, y.kpart),
-              at<const double>(pl, y.rpart), fp, at<int>(pl, y.status), o));
+    if (side) CK(cudaStreamWaitEvent(L.st, pl->ev_join, 0));
+    else
+        LCHK(L.go("finalize", k_finalize, dim3(1), dim3(512), 0, at<const double>(pl, y.qpart),
+                  at<const double>(pl, y.kpart), at<const double>(pl, y.rpart), fp, at<int>(pl, y.status), o));
     if (want_phi && !konly)
         LCHK(L.go("phi_background", k_phi_background<R>, dim3(nblkN), dim3(256), 0, N, (const double*)o,
                   -r.prm.coulomb_k * kPi / (fp.V * r.prm.alpha * r.prm.alpha), phi));
@@ -847,7 +873,14 @@ int enuf_plan_create(const enuf_params* params, void* cuda_stream, int allocate,
         for (auto& x : pl->tevents) cudaEventCreate(&x);
     }
     cudaError_t e = cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pl->aux_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
+        if (pl->aux_stream) cudaStreamDestroy(pl->aux_stream);
+        if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
         delete pl;
         return fail(ENUF_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
     }
@@ -856,6 +889,9 @@ int enuf_plan_create(const enuf_params* params, void* cuda_stream, int allocate,
         e = cudaMalloc(&p, pl->lay.total);
         if (e != cudaSuccess) {
             cudaGetLastError();
+            cudaEventDestroy(pl->ev_fork);
+            cudaEventDestroy(pl->ev_join);
+            cudaStreamDestroy(pl->aux_stream);
             cudaStreamDestroy(pl->cap_stream);
             delete pl;
             return fail(ENUF_ENOMEM, "cudaMalloc of " + std::to_string(pl->lay.total) + " bytes failed");
@@ -905,6 +941,9 @@ int enuf_plan_destroy(enuf_plan* pl)
     if (pl->prof_exec) cudaGraphExecDestroy(pl->prof_exec);
     for (auto e : pl->tevents) cudaEventDestroy(e);
     if (pl->own_ws && pl->ws) cudaFree(pl->ws);
+    if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
+    if (pl->ev_join) cudaEventDestroy(pl->ev_join);
+    if (pl->aux_stream) cudaStreamDestroy(pl->aux_stream);
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
     delete pl;
     return ENUF_OK;
