@@ -115,11 +115,13 @@ __device__ __forceinline__ void window_rows(int a, int g, Fn&& f)
 }
 
 // Calls f(s, b, c, w) for the window rows this lane serves (see
-// window_rows), with w = wy[b] * wz[c] and s = 0, 1, ... the lane's step.  For p = 8 and p = 4 the lane's rows fall on fixed
-// y offsets, so the weights stay in registers (two shuffles per particle);
-// other widths go through the per-warp product table `wyz` in shared memory.
+// window_rows), with w = wx * wy[b] * wz[c] (wx: the lane's own x weight)
+// and s = 0, 1, ... the lane's step.  For p = 8 and p = 4 the lane's rows
+// fall on fixed y offsets, so the weights stay in registers (two shuffles
+// per particle, wx folded into the y weights); other widths go through the
+// per-warp product table `wyz` in shared memory.
 template <typename R, int P, typename Fn>
-__device__ __forceinline__ void visit_window(R dy, R dz, const WinC<R>& wc, R* wyz, int lane, Fn&& f)
+__device__ __forceinline__ void visit_window(R dy, R dz, R wx, const WinC<R>& wc, R* wyz, int lane, Fn&& f)
 {
     constexpr int G = GroupOf<P>::G;
     const int g = lane / G, a = lane % G;
@@ -127,13 +129,12 @@ __device__ __forceinline__ void visit_window(R dy, R dz, const WinC<R>& wc, R* w
         R wz[8];
         window_weights<R, 8>(dz, wc, wz);
         const R u = dy + (R)(3 - a);
-        const R wyo = win_exp(u * u, wc);
-        const R wy0 = __shfl_sync(0xffffffffu, wyo, g), wy1 = __shfl_sync(0xffffffffu, wyo, g + 4);
+        const R wya = win_exp(u * u, wc);
+        const R t0 = wx * __shfl_sync(0xffffffffu, wya, g), t1 = wx * __shfl_sync(0xffffffffu, wya, g + 4);
 #pragma unroll
-        for (int it = 0; it < 16; it++) {
-            const int c = it >> 1;
-            if (it & 1) f(it, g + 4, c, wy1 * wz[c]);
-            else f(it, g, c, wy0 * wz[c]);
+        for (int c = 0; c < 8; c++) {
+            f(2 * c, g, c, t0 * wz[c]);
+            f(2 * c + 1, g + 4, c, t1 * wz[c]);
         }
     } else if constexpr (P == 4) {
         R wz[4];
@@ -141,13 +142,13 @@ __device__ __forceinline__ void visit_window(R dy, R dz, const WinC<R>& wc, R* w
         const R u = dy + (R)(1 - a);
         const R wyo = win_exp(u * u, wc);
         const int b = g & 3, hi = g >> 2;
-        const R wyb = __shfl_sync(0xffffffffu, wyo, b);
+        const R t = wx * __shfl_sync(0xffffffffu, wyo, b);
 #pragma unroll
-        for (int it = 0; it < 2; it++) f(it, b, 2 * it + hi, wyb * (hi ? wz[2 * it + 1] : wz[2 * it]));
+        for (int it = 0; it < 2; it++) f(it, b, 2 * it + hi, t * (hi ? wz[2 * it + 1] : wz[2 * it]));
     } else {
         pair_weights<R, P>(dy, dz, wc, wyz, lane);
         __syncwarp();
-        window_rows<P>(a, g, [&](int it, int rr, int b, int c) { f(it, b, c, wyz[rr]); });
+        window_rows<P>(a, g, [&](int it, int rr, int b, int c) { f(it, b, c, wx * wyz[rr]); });
         __syncwarp();
     }
 }
@@ -280,9 +281,9 @@ __global__ void __launch_bounds__(32) k_spread(const int4* __restrict__ work, co
                 int off[NV];
                 R vv[NV];
                 unsigned valid = 0u;
-                visit_window<R, P>(dy, dz, wc, wyz, lane, [&](int st, int b, int c, R wyzv) {
+                visit_window<R, P>(dy, dz, wx, wc, wyz, lane, [&](int st, int b, int c, R wv) {
                     off[st] = c * PS + b * BX;
-                    vv[st] = wx * wyzv;
+                    vv[st] = wv;
                     valid |= 1u << st;
                 });
                 if (a < P) {
@@ -296,8 +297,8 @@ __global__ void __launch_bounds__(32) k_spread(const int4* __restrict__ work, co
                 }
             } else {
                 R* base = acc + (iz * PS) + iy * BX + ix + B::XOFF + a;
-                visit_window<R, P>(dy, dz, wc, wyz, lane, [&](int, int b, int c, R wyzv) {
-                    if (a < P) base[c * PS + b * BX] += wx * wyzv;
+                visit_window<R, P>(dy, dz, wx, wc, wyz, lane, [&](int, int b, int c, R wv) {
+                    if (a < P) base[c * PS + b * BX] += wv;
                 });
             }
             __syncwarp();
@@ -387,9 +388,8 @@ __global__ void __launch_bounds__(NTH) k_gather(const int4* __restrict__ work, c
         const R wx = win_exp(ua * ua, wc);
         const R* base = s + (iz * PT + iy) * BX + ix + B::XOFF + a;
         R acc[4] = {R(0), R(0), R(0), R(0)};
-        visit_window<R, P>(dy, dz, wc, wyz, lane, [&](int, int b, int c, R wyzv) {
+        visit_window<R, P>(dy, dz, wx, wc, wyz, lane, [&](int, int b, int c, R ww) {
             if (a < P) {
-                const R ww = wx * wyzv;
                 const int o = (c * PT + b) * BX;
 #pragma unroll
                 for (int f = 0; f < NF; f++) acc[f] += ww * base[f * C + o];
