@@ -63,6 +63,24 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
+// Division by a divisor d (1 <= d < 2^16) fixed at launch, for dividends
+// n < 2^16: q = (n m) >> 32 with m = floor(2^32 / d) + 1 is exact in that
+// range (the error n (m - 2^32 / d) / 2^32 < 2^-16 < 1 / d cannot carry the
+// fraction n / d past an integer), and costs a multiply instead of the ~20
+// instructions of a general integer division.
+struct FDiv {
+    uint32_t d;
+    unsigned long long m;
+    static FDiv make(uint32_t dv)
+    {
+        FDiv f;
+        f.d = dv;
+        f.m = 0x100000000ull / dv + 1;
+        return f;
+    }
+    __device__ __forceinline__ uint32_t div(uint32_t n) const { return (uint32_t)(((unsigned long long)n * m) >> 32); }
+};
+
 template <typename R> __device__ __forceinline__ R warp_sum(R v)
 {
 #pragma unroll

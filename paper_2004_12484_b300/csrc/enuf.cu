@@ -186,6 +186,16 @@ int resolve(const enuf_params* in, Resolved& r)
             }
         }
     }
+    // launch-time divisors of the FFT kernels' index arithmetic
+    for (FftGeom* gm : {&r.gfx, &r.gy, &r.gz}) {
+        gm->fKx = FDiv::make((uint32_t)r.Kx);
+        gm->fW = FDiv::make((uint32_t)std::max(1, gm->W));
+        gm->fKxR = FDiv::make(1);
+    }
+    if (r.fxy_threads > 0) {
+        const int CB = r.fxy_threads / ffthreads(M);
+        r.gy.fKxR = FDiv::make((uint32_t)((r.Kx + CB - 1) / CB * CB));
+    }
     return ENUF_OK;
 }
 

@@ -190,6 +190,7 @@ struct FftGeom {
     int P;     // Kb * Kx pencils along z
     int W;     // transforms (columns / pencils) per CTA in k_fy / k_fz / k_iy
     int rows;  // rows per CTA in k_fx / k_ix
+    FDiv fKx, fW, fKxR;  // division by Kx, W and (k_iyx) Kx rounded up to its column batch
 };
 
 // ---------------------------------------------------------------- k_fx
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(256) k_fx(R* __restrict__ grid, typename Cpx<R
     fft_smem<V, MH, false>(s + (threadIdx.x / NT) * RS, threadIdx.x % NT, sW, 2);
     const int Kx = g.Kx;
     for (int i = threadIdx.x; i < rows * Kx; i += blockDim.x) {
-        const int r = i / Kx, k = i % Kx, row = row0 + r;
+        const int r = (int)g.fKx.div(i), k = i - r * Kx, row = row0 + r;
         if (row >= nrows) continue;
         const V zk = s[r * RS + pidx(k % MH)];
         const V zc = cconj(s[r * RS + pidx((MH - k) % MH)]);
@@ -270,7 +271,7 @@ __global__ void __launch_bounds__(1024) k_fxy(R* __restrict__ grid, typename Cpx
         __syncthreads();
         fft_smem<V, MH, false>(rowbuf + (threadIdx.x / NTX) * RS, threadIdx.x % NTX, sW, 2);
         for (int i = threadIdx.x; i < RB * Kx; i += blockDim.x) {
-            const int r = i / Kx, k = i % Kx, y = y0 + r;
+            const int r = (int)g.fKx.div(i), k = i - r * Kx, y = y0 + r;
             if (y >= M) continue;
             const V zk = rowbuf[r * RS + pidx(k % MH)];
             const V zc = cconj(rowbuf[r * RS + pidx((MH - k) % MH)]);
@@ -286,7 +287,7 @@ __global__ void __launch_bounds__(1024) k_fxy(R* __restrict__ grid, typename Cpx
     }
     V* dst = C2 + (size_t)z * Kb * Kx;
     for (int i = threadIdx.x; i < Kb * Kx; i += blockDim.x) {
-        const int kb = i / Kx, kx = i % Kx;
+        const int kb = (int)g.fKx.div(i), kx = i - kb * Kx;
         const int ky = kb <= nc ? kb : M - Kb + kb;
         dst[i] = plane[kx * LD + pidx(ky)];
     }
@@ -306,14 +307,14 @@ __global__ void __launch_bounds__(1024) k_fy(const typename Cpx<R>::T* __restric
     const int kx0 = blockIdx.x * Wc, z = blockIdx.y;
     const V* sW = stage_twiddles(s + Wc * LD, Wg, M);
     for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
-        const int w = i % Wc, y = i / Wc, kx = kx0 + w;
+        const int y = (int)g.fW.div(i), w = i - y * Wc, kx = kx0 + w;
         cp_async_cpx(s + w * LD + pidx(y), C1 + (kx < Kx ? ((size_t)z * M + y) * Kx + kx : 0), kx < Kx);
     }
     cp_async_wait_all();
     __syncthreads();
     fft_smem<V, M, false>(s + (threadIdx.x / NT) * LD, threadIdx.x % NT, sW, 1);
     for (int i = threadIdx.x; i < Wc * Kb; i += blockDim.x) {
-        const int w = i % Wc, kb = i / Wc, kx = kx0 + w;
+        const int kb = (int)g.fW.div(i), w = i - kb * Wc, kx = kx0 + w;
         if (kx >= Kx) continue;
         const int ky = kb <= nc ? kb : M - Kb + kb;
         C2[((size_t)z * Kb + kb) * Kx + kx] = s[w * LD + pidx(ky)];
@@ -365,7 +366,7 @@ __global__ void __launch_bounds__(512) k_fz(const typename Cpx<R>::T* __restrict
     const R* td = stab + 6 * Kb;
     const int p0 = blockIdx.x * Wc;
     for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
-        const int w = i % Wc, z = i / Wc, p = p0 + w;
+        const int z = (int)g.fW.div(i), w = i - z * Wc, p = p0 + w;
         cp_async_cpx(X + w * LD + pidx(z), C2 + (p < P ? (size_t)z * P + p : 0), p < P);
     }
     cp_async_wait_all();
@@ -380,7 +381,7 @@ __global__ void __launch_bounds__(512) k_fz(const typename Cpx<R>::T* __restrict
         R kxv = R(0), kyv = R(0), kzv = R(0);
         const int nz = z <= nc ? z : (z >= M - nc ? z - M : (1 << 20));
         if (p < P && nz != (1 << 20)) {
-            const int kx = p % Kx, kb = p / Kx;
+            const int kb = (int)g.fKx.div(p), kx = p - kb * Kx;
             const int nx = kx, ny = kb <= nc ? kb : kb - Kb;
             if (nx != 0 || ny != 0 || nz != 0) {
                 kxv = tk[nx + nc];
@@ -416,7 +417,7 @@ __global__ void __launch_bounds__(512) k_fz(const typename Cpx<R>::T* __restrict
     if (NF == 0) return;
     fft_smem_multi<V, M, true, NB, MR>(X + (threadIdx.x / NT) * LD, FS, threadIdx.x % NT, sW, 1);
     for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
-        const int w = i % Wc, z = i / Wc, p = p0 + w;
+        const int z = (int)g.fW.div(i), w = i - z * Wc, p = p0 + w;
         if (p < P) {
 #pragma unroll
             for (int f = 0; f < NB; f++) C3[((size_t)f * M + z) * P + p] = X[f * FS + w * LD + pidx(z)];
@@ -439,7 +440,7 @@ __global__ void __launch_bounds__(1024) k_iy(const typename Cpx<R>::T* __restric
     const V* W = stage_twiddles(s + Wc * LD, Wg, M);
     const V* src = C3 + ((size_t)f * M + z) * P;
     for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
-        const int w = i % Wc, y = i / Wc, kx = kx0 + w;
+        const int y = (int)g.fW.div(i), w = i - y * Wc, kx = kx0 + w;
         int kb = -1;
         if (kx < Kx) {
             if (y <= nc) kb = y;
@@ -452,7 +453,7 @@ __global__ void __launch_bounds__(1024) k_iy(const typename Cpx<R>::T* __restric
     fft_smem<V, M, true>(s + (threadIdx.x / NT) * LD, threadIdx.x % NT, W, 1);
     V* dst = C4 + ((size_t)f * M + z) * M * Kx;
     for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
-        const int w = i % Wc, y = i / Wc, kx = kx0 + w;
+        const int y = (int)g.fW.div(i), w = i - y * Wc, kx = kx0 + w;
         if (kx < Kx) dst[(size_t)y * Kx + kx] = s[w * LD + pidx(y)];
     }
 }
@@ -488,7 +489,7 @@ __global__ void __launch_bounds__(IyxBounds<R, M>::T, IyxBounds<R, M>::B) k_iyx(
     const int z = blockIdx.x, f = blockIdx.y;
     const V* src = C3 + ((size_t)f * M + z) * P;
     for (int i = threadIdx.x; i < KxR * M; i += blockDim.x) {
-        const int kx = i % KxR, y = i / KxR;  // consecutive threads read consecutive kx
+        const int y = (int)g.fKxR.div(i), kx = i - y * KxR;  // consecutive threads read consecutive kx
         int kb = -1;
         if (kx < Kx) {
             if (y <= nc) kb = y;
