@@ -526,6 +526,9 @@ BinGeom make_geom(const int S[3], int T, const double L3[3], bool grid_units, in
         g.unit[t] = grid_units ? 1.0 : L3[t] / S[t];
     }
     g.T = T;
+    while ((1 << g.lT) < T) g.lT++;
+    while ((1 << g.lsub) < sub) g.lsub++;
+    for (int t = 0; t < 3; t++) g.smask[t] = (S[t] & (S[t] - 1)) == 0 ? S[t] - 1 : -1;
     return g;
 }
 

@@ -17,6 +17,8 @@ struct BinGeom {
     int nb[3];         // tiles per dimension = S / T
     int sub, lr;       // sub-tile edge and log2(T / sub): a bin is one of the
                        // (T / sub)^3 sub-tiles of a tile, numbered tile-major
+    int lT, lsub;      // log2(T), log2(sub) (both powers of two)
+    int smask[3];      // S - 1 when S is a power of two, else -1
     double scale[3];   // S_t / L_t
     float scale_hi[3]; // float split of scale: scale ~ hi + lo
     float scale_lo[3];
@@ -30,8 +32,12 @@ __device__ __forceinline__ void locate(double r, const BinGeom& g, int t, int& c
     double k = floor(u);
     f = u - k;
     if (f >= 1.0) { f = 0.0; k += 1.0; }
-    long long kk = (long long)k % g.S[t];
-    if (kk < 0) kk += g.S[t];
+    long long kk;
+    if (g.smask[t] >= 0) kk = (long long)k & g.smask[t];
+    else {
+        kk = (long long)k % g.S[t];
+        if (kk < 0) kk += g.S[t];
+    }
     c = (int)kk;
 }
 
@@ -46,8 +52,12 @@ __device__ __forceinline__ void locate(float r, const BinGeom& g, int t, int& c,
     if (f < 0.f) { f += 1.f; k -= 1.f; }
     if (f >= 1.f) { f -= 1.f; k += 1.f; }
     if (f >= 1.f || f < 0.f) f = 0.f;
-    int kk = (int)k % g.S[t];
-    if (kk < 0) kk += g.S[t];
+    int kk;
+    if (g.smask[t] >= 0) kk = (int)k & g.smask[t];
+    else {
+        kk = (int)k % g.S[t];
+        if (kk < 0) kk += g.S[t];
+    }
     c = kk;
 }
 
@@ -239,14 +249,14 @@ __global__ void __launch_bounds__(256) k_bin_keys(int N, const R* __restrict__ p
             for (int t = 0; t < 3; t++) {
                 R f;
                 locate(r3[t], g, t, c[t], f);
-                off[t] = ((R)(c[t] % g.T) + f) * (R)g.unit[t];
+                off[t] = ((R)(c[t] & (g.T - 1)) + f) * (R)g.unit[t];
             }
         } else {
             atomicOr(status, ST_NONFINITE);
             qq = R(0);
         }
-        uint32_t b = (uint32_t)(c[0] / g.T) +
-                     (uint32_t)g.nb[0] * ((uint32_t)(c[1] / g.T) + (uint32_t)g.nb[1] * (uint32_t)(c[2] / g.T));
+        uint32_t b = (uint32_t)(c[0] >> g.lT) +
+                     (uint32_t)g.nb[0] * ((uint32_t)(c[1] >> g.lT) + (uint32_t)g.nb[1] * (uint32_t)(c[2] >> g.lT));
         if (g.lr > 0) {
             // sub-tile of the cell index the kernels split from the stored
             // offset (same truncation and clamp as split_offset)
@@ -255,7 +265,7 @@ __global__ void __launch_bounds__(256) k_bin_keys(int N, const R* __restrict__ p
             for (int t = 0; t < 3; t++) {
                 int ci = (int)off[t];
                 if (ci > g.T - 1) ci = g.T - 1;
-                sb |= (uint32_t)(ci / g.sub) << (g.lr * t);
+                sb |= (uint32_t)(ci >> g.lsub) << (g.lr * t);
             }
             b = (b << (3 * g.lr)) | sb;
         }
