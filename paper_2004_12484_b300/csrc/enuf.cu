@@ -113,7 +113,10 @@ int resolve(const enuf_params* in, Resolved& r)
         const int m = p.p / 2, XA = (m - 1 + 3) / 4 * 4, BX = (XA + T + m + 3) / 4 * 4, PT = T + p.p - 1;
         return ((size_t)BX * PT * PT * 4 + (size_t)32 * p.p * p.p) * r.rsz + (size_t)kWorkCap * (4 * r.rsz + 4);
     };
-    r.T = (!r.fp64 && p.M >= 128) ? 16 : 8;
+    // windows of p <= 6 interpolate faster straight from L2-resident fields
+    // (8-cell tiles) than from a staged 16-cell box
+    const bool fields_in_l2 = (size_t)4 * p.M * p.M * p.M * r.rsz <= (size_t)64 << 20;
+    r.T = (!r.fp64 && p.M >= 128 && !(p.p <= 6 && fields_in_l2)) ? 16 : 8;
     if (const char* tv = std::getenv("ENUF_TILE")) {  // tuning knob: tile edge 4, 8 or 16
         const int t = std::atoi(tv);
         if ((t == 4 || t == 8 || t == 16) && t <= p.M) r.T = t;
