@@ -137,6 +137,55 @@ def test_rpm_config_kspace_full_size():
     assert np.abs(Wv - Wk).max() < 1e-5 * np.abs(Wk).max()
 
 
+def test_rpm_1e4_kspace_full_size():
+    """The benchmark's workload (RPM electrolyte, N = 65,536, grid 128^3,
+    p = 8, mixed) at full size in the launch configuration the benchmark
+    times (16-cell tiles of 8^3 sub-tiles, staged interpolation): reciprocal
+    part element by element against the oracle."""
+    d = W.rpm_1e4()
+    pos, q = W.as_fp32(d["pos"], d["q"])
+    parts, F, Wv, ph = run(pos, q, d["L"], d["alpha"], d["r_c"], d["M"], d["p"], d["n_c"], "mixed",
+                           kspace_only=True)
+    Ek, Fk, phik, Wk = O.kspace_nfft(pos, q, d["L"], d["alpha"], d["M"], d["p"], d["n_c"])
+    assert abs(parts["E"] / Ek - 1) < 1e-6
+    assert rel_rms(F, Fk) < 1e-5
+    assert rel_rms(ph, phik) < 1e-5
+    assert np.abs(Wv - Wk).max() < 1e-5 * np.abs(Wk).max()
+
+
+def check_kspace(pos, q, L, alpha, M, p, nc):
+    """Mixed-precision reciprocal part (E, F, phi, virial) against the oracle."""
+    pos, q = W.as_fp32(pos, q)
+    parts, F, Wv, ph = run(pos, q, L, alpha, 0.45 * min(L), M, p, nc, "mixed", kspace_only=True)
+    Ek, Fk, phik, Wk = O.kspace_nfft(pos, q, L, alpha, M, p, nc)
+    assert abs(parts["E"] / Ek - 1) < 1e-6
+    assert rel_rms(F, Fk) < 1e-5
+    assert rel_rms(ph, phik) < 1e-5
+    assert np.abs(Wv - Wk).max() < 1e-5 * np.abs(Wk).max()
+
+
+@pytest.mark.parametrize("p", [2, 4, 6, 8])
+def test_sixteen_cell_tiles_small_grid(p, monkeypatch):
+    """16-cell tiles split into 8^3 sub-tiles (the layout of float grids of
+    edge >= 128) forced on a 32^3 grid: a random system with wrapping, and a
+    heavy tile whose sub-tiles are cut into several spreading items and
+    whose tile into several interpolation items.  The reciprocal part is
+    compared (the tile layout only concerns it; the real-space sum of these
+    dense random systems carries the float error of its closest pairs)."""
+    monkeypatch.setenv("ENUF_TILE", "16")
+    g = np.random.default_rng(30 + p)
+    L = np.array([22.0, 25.0, 27.0])
+    pos = g.uniform(-1.0, 2.0, size=(2500, 3)) * L
+    q = g.normal(size=2500)
+    q -= q.mean()
+    check_kspace(pos, q, L, 0.4, 32, p, 8)
+    h = L / 32
+    pos = (3.0 + g.uniform(0, 12.0, size=(1500, 3))) * h  # inside one 16-cell tile
+    q = g.normal(size=1500)
+    q -= q.mean()
+    check_kspace(pos, q, L, 0.4, 32, p, 8)
+
+
 def test_rpm_config_real_space_sampled():
     """Full RPM step: the real-space part on sampled particles (the oracle
     sums every pair for each sampled particle)."""
