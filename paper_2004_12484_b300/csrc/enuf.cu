@@ -208,6 +208,7 @@ struct Layout {
     size_t counts, offsets, work, nwork, work2, nwork2, item2;
     size_t key, rank, rec_tmp, rec, perm, tile_of;
     size_t rcounts, roffsets, rrec, rperm, rcell;
+    size_t rkey, rrank, rrec_tmp, Fr, phir;  // real-space sort scratch and outputs
     size_t qpart, kpart, rpart, fpart;
     size_t twid, tk, te, td;
     size_t grid, C1, C2, C3, C4, fld;
@@ -254,6 +255,11 @@ Layout layout(const Resolved& r)
     L.rrec = take(N * recsz);
     L.rperm = take(N * 4);
     L.rcell = take(N * 4);
+    L.rkey = take(N * 4);
+    L.rrank = take(N * 4);
+    L.rrec_tmp = take(N * recsz);
+    L.Fr = take(3 * N * rs);
+    L.phir = take(N * rs);
     L.qpart = take(nblkN * 2 * 8);
     L.kpart = take(nblkZ * 8 * 8);
     L.rpart = take(nblkN * 8 * 8);
@@ -551,6 +557,60 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
     // the status word, the bin counts and the block counters are kept
     // zeroed between calls by the kernels that consume them (k_finalize, the
     // scan in the last block of k_bin_keys)
+    // (a8) real space: its own sort scratch and output buffers, so that it
+    // can run on a side branch beside the whole reciprocal chain; the
+    // outputs are added to the reciprocal ones after both
+    auto real_space = [&]() -> int {
+        const BinGeom gr = make_geom(r.ncell, 1, r.prm.L, false);
+        ScanArgs sr{r.nrbins, at<uint32_t>(pl, y.rcounts), count_stride(r.nrbins), at<uint32_t>(pl, y.roffsets),
+                    kWorkCap, (int4*)nullptr, (int*)nullptr, 0, kSpreadCap, (uint32_t*)nullptr, (int*)nullptr, 0,
+                    at<unsigned>(pl, y.status + 12)};
+        LCHK(L.go("real_bin_keys", k_bin_keys<R, 1>, dim3(nblkN), dim3(256), 0, N, pos, q, gr, at<uint32_t>(pl, y.rkey),
+                  at<uint32_t>(pl, y.rrank), at<RecT>(pl, y.rrec_tmp), sr, at<int>(pl, y.status), (double*)nullptr));
+        LCHK(L.go("real_scatter", k_scatter<R>, dim3(nblkN), dim3(256), 0, N, at<const uint32_t>(pl, y.rkey),
+                  at<const uint32_t>(pl, y.rrank), at<const uint32_t>(pl, y.roffsets), at<const RecT>(pl, y.rrec_tmp),
+                  at<RecT>(pl, y.rrec), at<uint32_t>(pl, y.rperm), at<uint32_t>(pl, y.rcell), (const uint32_t*)nullptr,
+                  kSpreadCap, (int4*)nullptr, 0));
+        RealParams<R> rp;
+        for (int t = 0; t < 3; t++) {
+            rp.nc[t] = r.ncell[t];
+            rp.h[t] = (R)r.h[t];
+            rp.L[t] = (R)r.prm.L[t];
+        }
+        rp.rc2 = (R)(r.prm.r_c * r.prm.r_c);
+        rp.alpha = (R)r.prm.alpha;
+        rp.two_a_sqpi = (R)(2.0 * r.prm.alpha / std::sqrt(kPi));
+        rp.ke = (R)r.prm.coulomb_k;
+        rp.self_phi = (R)(-2.0 * r.prm.alpha / std::sqrt(kPi));
+        R* Fo = F ? at<R>(pl, y.Fr) : nullptr;
+        R* po = want_phi ? at<R>(pl, y.phir) : nullptr;
+        if (r.cells)
+            LCHK(L.go("realspace", k_realspace_cells<R>, dim3(nblkN), dim3(256), 0, N, at<const RecT>(pl, y.rrec),
+                      at<const uint32_t>(pl, y.rcell), at<const uint32_t>(pl, y.roffsets), at<const uint32_t>(pl, y.rperm),
+                      rp, Fo, po, at<double>(pl, y.rpart)));
+        else
+            LCHK(L.go("realspace", k_realspace_allpairs<R>, dim3(nblkN), dim3(256), 0, N, at<const RecT>(pl, y.rrec),
+                      at<const uint32_t>(pl, y.rperm), rp, Fo, po, at<double>(pl, y.rpart)));
+        return ENUF_OK;
+    };
+    const int nr = konly ? 0 : nblkN;
+    const bool real_side = !konly && !L.attr_only && !pl->profile;
+    if (real_side) {
+        CK(cudaEventRecord(pl->ev_fork, L.st));
+        CK(cudaStreamWaitEvent(pl->aux_stream, pl->ev_fork, 0));
+        const cudaStream_t main_st = L.st;
+        L.st = pl->aux_stream;
+        const int rc = real_space();
+        L.st = main_st;
+        cudaEventRecord(pl->ev_join, pl->aux_stream);
+        if (rc != ENUF_OK) {
+            cudaStreamWaitEvent(L.st, pl->ev_join, 0);  // a capture must end joined
+            return rc;
+        }
+    } else if (!konly) {
+        LCHK(real_space());
+    }
+
     // (a1, a2) counting sort into grid tiles
     const int Sg[3] = {r.prm.M, r.prm.M, r.prm.M};
     const BinGeom gg = make_geom(Sg, r.T, r.prm.L, true, r.S, r.lr);
@@ -604,43 +664,12 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
     }
     // (a7) interpolation
     if (nf > 0) LCHK(launch_gather<R>(L, pl, nf, F, want_phi ? phi : (R*)nullptr));
-    // (a8) real space
-    int nr = 0;
-    if (!konly) {
-        const BinGeom gr = make_geom(r.ncell, 1, r.prm.L, false);
-        ScanArgs sr{r.nrbins, at<uint32_t>(pl, y.rcounts), count_stride(r.nrbins), at<uint32_t>(pl, y.roffsets),
-                    kWorkCap, (int4*)nullptr, (int*)nullptr, 0, kSpreadCap, (uint32_t*)nullptr, (int*)nullptr, 0,
-                    at<unsigned>(pl, y.status + 12)};
-        LCHK(L.go("real_bin_keys", k_bin_keys<R, 1>, dim3(nblkN), dim3(256), 0, N, pos, q, gr, at<uint32_t>(pl, y.key),
-                  at<uint32_t>(pl, y.rank), at<RecT>(pl, y.rec_tmp), sr, at<int>(pl, y.status), (double*)nullptr));
-        LCHK(L.go("real_scatter", k_scatter<R>, dim3(nblkN), dim3(256), 0, N, at<const uint32_t>(pl, y.key),
-                  at<const uint32_t>(pl, y.rank), at<const uint32_t>(pl, y.roffsets), at<const RecT>(pl, y.rec_tmp),
-                  at<RecT>(pl, y.rrec), at<uint32_t>(pl, y.rperm), at<uint32_t>(pl, y.rcell), (const uint32_t*)nullptr,
-                  kSpreadCap, (int4*)nullptr, 0));
-        RealParams<R> rp;
-        for (int t = 0; t < 3; t++) {
-            rp.nc[t] = r.ncell[t];
-            rp.h[t] = (R)r.h[t];
-            rp.L[t] = (R)r.prm.L[t];
-        }
-        rp.rc2 = (R)(r.prm.r_c * r.prm.r_c);
-        rp.alpha = (R)r.prm.alpha;
-        rp.two_a_sqpi = (R)(2.0 * r.prm.alpha / std::sqrt(kPi));
-        rp.ke = (R)r.prm.coulomb_k;
-        rp.self_phi = (R)(-2.0 * r.prm.alpha / std::sqrt(kPi));
-        R* Fo = F;
-        R* po = want_phi ? phi : nullptr;
-        if (r.cells)
-            LCHK(L.go("realspace", k_realspace_cells<R>, dim3(nblkN), dim3(256), 0, N, at<const RecT>(pl, y.rrec),
-                      at<const uint32_t>(pl, y.rcell), at<const uint32_t>(pl, y.roffsets), at<const uint32_t>(pl, y.rperm),
-                      rp, Fo, po, at<double>(pl, y.rpart)));
-        else
-            LCHK(L.go("realspace", k_realspace_allpairs<R>, dim3(nblkN), dim3(256), 0, N, at<const RecT>(pl, y.rrec),
-                      at<const uint32_t>(pl, y.rperm), rp, Fo, po, at<double>(pl, y.rpart)));
-        nr = nblkN;
-    }
     // (a9) assembly
     fp.nr = nr;
+    if (real_side) CK(cudaStreamWaitEvent(L.st, pl->ev_join, 0));
+    if (!konly && (F || want_phi))
+        LCHK(L.go("combine", k_combine<R>, dim3(nblkN), dim3(256), 0, N, (const R*)at<R>(pl, y.Fr),
+                  (const R*)at<R>(pl, y.phir), F, want_phi ? phi : (R*)nullptr));
     if (side) CK(cudaStreamWaitEvent(L.st, pl->ev_join, 0));
     else
         LCHK(L.go("finalize", k_finalize, dim3(1), dim3(512), 0, at<const double>(pl, y.qpart),

@@ -47,7 +47,7 @@ __device__ __forceinline__ void pair_term(R dx, R dy, R dz, R qi, R qj, const Re
     acc[6] += R(0.5) * fs * dy * dz;
 }
 
-// Adds the real-space force and potential (and the self term of phi) to F
+// Writes the real-space force and potential (and the self term of phi) to F
 // and phi in the caller's particle order; part[block] gets (E, W..) partials.
 template <typename R>
 __global__ void __launch_bounds__(256) k_realspace_cells(int N, const typename Rec<R>::T* __restrict__ rec,
@@ -84,11 +84,11 @@ __global__ void __launch_bounds__(256) k_realspace_cells(int N, const typename R
         }
         const uint32_t oi = perm[i];
         if (F) {
-            F[3 * (size_t)oi] += rp.ke * f[0];
-            F[3 * (size_t)oi + 1] += rp.ke * f[1];
-            F[3 * (size_t)oi + 2] += rp.ke * f[2];
+            F[3 * (size_t)oi] = rp.ke * f[0];
+            F[3 * (size_t)oi + 1] = rp.ke * f[1];
+            F[3 * (size_t)oi + 2] = rp.ke * f[2];
         }
-        if (phi) phi[oi] += rp.ke * (ph + rp.self_phi * ri.w);
+        if (phi) phi[oi] = rp.ke * (ph + rp.self_phi * ri.w);
     }
     block_reduce_to_double<R, 7>(acc, part + 8 * (size_t)blockIdx.x, red);
 }
@@ -119,13 +119,29 @@ __global__ void __launch_bounds__(256) k_realspace_allpairs(int N, const typenam
         }
         const uint32_t oi = perm[i];
         if (F) {
-            F[3 * (size_t)oi] += rp.ke * f[0];
-            F[3 * (size_t)oi + 1] += rp.ke * f[1];
-            F[3 * (size_t)oi + 2] += rp.ke * f[2];
+            F[3 * (size_t)oi] = rp.ke * f[0];
+            F[3 * (size_t)oi + 1] = rp.ke * f[1];
+            F[3 * (size_t)oi + 2] = rp.ke * f[2];
         }
-        if (phi) phi[oi] += rp.ke * (ph + rp.self_phi * ri.w);
+        if (phi) phi[oi] = rp.ke * (ph + rp.self_phi * ri.w);
     }
     block_reduce_to_double<R, 7>(acc, part + 8 * (size_t)blockIdx.x, red);
+}
+
+// Adds the real-space force and potential (computed beside the reciprocal
+// part into their own buffers) to the reciprocal ones.
+template <typename R>
+__global__ void __launch_bounds__(256) k_combine(int N, const R* __restrict__ Fr, const R* __restrict__ phir,
+                                                 R* __restrict__ F, R* __restrict__ phi)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    if (F) {
+        F[3 * (size_t)i] += Fr[3 * (size_t)i];
+        F[3 * (size_t)i + 1] += Fr[3 * (size_t)i + 1];
+        F[3 * (size_t)i + 2] += Fr[3 * (size_t)i + 2];
+    }
+    if (phi) phi[i] += phir[i];
 }
 
 // ---------------------------------------------------------------- assembly
