@@ -70,6 +70,7 @@ struct Resolved {
     int S, lr, nbins, max_work2;      // sub-tiles of S^3 (the sort's bins), lr = log2(T/S), spreading items
     bool cells;    // linked cells (else all pairs)
     int ncell[3], nrbins;
+    int sr;        // stencil radius of the linked cells: 2 (edge >= r_c / 2) or 1 (edge >= r_c)
     double h[3];
     FftGeom gfx, gy, gz;
     int fxy_threads;  // > 0: fused x-y kernels with this block size
@@ -131,11 +132,17 @@ int resolve(const enuf_params* in, Resolved& r)
     r.nbins = r.ntiles << (3 * r.lr);
     r.max_work2 = (int)std::min<int64_t>(r.nbins, p.N) + (int)(p.N / kSpreadCap) + 1;
     // linked cells of edge >= r_c, at least 3 per dimension
+    // linked cells of edge >= r_c / 2 with a 5^3 stencil where every
+    // dimension holds at least 5 of them (the stencil's volume is 15.6 r_c^3
+    // instead of 27 r_c^3), else of edge >= r_c with 3^3
     r.cells = true;
+    r.sr = 2;
+    for (int t = 0; t < 3; t++)
+        if ((int)std::floor(2.0 * p.L[t] / p.r_c) < 5 || std::getenv("ENUF_CELL_STENCIL3")) r.sr = 1;
     for (int t = 0; t < 3; t++) {
-        r.ncell[t] = (int)std::floor(p.L[t] / p.r_c);
+        r.ncell[t] = (int)std::floor(r.sr * p.L[t] / p.r_c);
         if (r.ncell[t] > 256) r.ncell[t] = 256;
-        if (r.ncell[t] < 3) r.cells = false;
+        if (r.ncell[t] < 2 * r.sr + 1) r.cells = false;
     }
     if (!r.cells) r.ncell[0] = r.ncell[1] = r.ncell[2] = 1;
     for (int t = 0; t < 3; t++) r.h[t] = p.L[t] / r.ncell[t];
@@ -262,7 +269,7 @@ Layout layout(const Resolved& r)
     L.phir = take(N * rs);
     L.qpart = take(nblkN * 2 * 8);
     L.kpart = take(nblkZ * 8 * 8);
-    L.rpart = take(nblkN * 8 * 8);
+    L.rpart = take(nblkN * 5 * 8 * 8);  // up to 5 stencil layers of blocks
     L.fpart = take(nblkN * 4 * 8);
     L.twid = take(M * vs);
     L.tk = take(3 * r.Kb * rs);
@@ -584,8 +591,12 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
         rp.self_phi = (R)(-2.0 * r.prm.alpha / std::sqrt(kPi));
         R* Fo = F ? at<R>(pl, y.Fr) : nullptr;
         R* po = want_phi ? at<R>(pl, y.phir) : nullptr;
-        if (r.cells)
-            LCHK(L.go("realspace", k_realspace_cells<R>, dim3(nblkN), dim3(256), 0, N, at<const RecT>(pl, y.rrec),
+        if (r.cells && r.sr == 2)
+            LCHK(L.go("realspace", k_realspace_cells<R, 2>, dim3(nblkN, 5), dim3(256), 0, N, at<const RecT>(pl, y.rrec),
+                      at<const uint32_t>(pl, y.rcell), at<const uint32_t>(pl, y.roffsets), at<const uint32_t>(pl, y.rperm),
+                      rp, Fo, po, at<double>(pl, y.rpart)));
+        else if (r.cells)
+            LCHK(L.go("realspace", k_realspace_cells<R, 1>, dim3(nblkN, 3), dim3(256), 0, N, at<const RecT>(pl, y.rrec),
                       at<const uint32_t>(pl, y.rcell), at<const uint32_t>(pl, y.roffsets), at<const uint32_t>(pl, y.rperm),
                       rp, Fo, po, at<double>(pl, y.rpart)));
         else
@@ -593,7 +604,7 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
                       at<const uint32_t>(pl, y.rperm), rp, Fo, po, at<double>(pl, y.rpart)));
         return ENUF_OK;
     };
-    const int nr = konly ? 0 : nblkN;
+    const int nr = konly ? 0 : nblkN * (r.cells ? 2 * r.sr + 1 : 1);
     const bool real_side = !konly && !L.attr_only && !pl->profile;
     if (real_side) {
         CK(cudaEventRecord(pl->ev_fork, L.st));
@@ -668,8 +679,8 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
     fp.nr = nr;
     if (real_side) CK(cudaStreamWaitEvent(L.st, pl->ev_join, 0));
     if (!konly && (F || want_phi))
-        LCHK(L.go("combine", k_combine<R>, dim3(nblkN), dim3(256), 0, N, (const R*)at<R>(pl, y.Fr),
-                  (const R*)at<R>(pl, y.phir), F, want_phi ? phi : (R*)nullptr));
+        LCHK(L.go("combine", k_combine<R>, dim3(nblkN), dim3(256), 0, N, at<R>(pl, y.Fr), at<R>(pl, y.phir), F,
+                  want_phi ? phi : (R*)nullptr));
     if (side) CK(cudaStreamWaitEvent(L.st, pl->ev_join, 0));
     else
         LCHK(L.go("finalize", k_finalize, dim3(1), dim3(512), 0, at<const double>(pl, y.qpart),
@@ -777,6 +788,8 @@ void reset_zeroed(enuf_plan* pl)
     cudaMemsetAsync(pl->ws + y.counts, 0, (size_t)(r.nbins + 1) * 4 * count_stride(r.nbins), pl->stream);
     cudaMemsetAsync(pl->ws + y.rcounts, 0, (size_t)(r.nrbins + 1) * 4 * count_stride(r.nrbins), pl->stream);
     cudaMemsetAsync(pl->ws + y.grid, 0, M3 * r.rsz, pl->stream);
+    cudaMemsetAsync(pl->ws + y.Fr, 0, (size_t)3 * r.prm.N * r.rsz, pl->stream);
+    cudaMemsetAsync(pl->ws + y.phir, 0, (size_t)r.prm.N * r.rsz, pl->stream);
     cudaGetLastError();
 }
 

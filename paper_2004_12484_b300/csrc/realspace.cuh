@@ -6,8 +6,9 @@
 //              r_ij / r^2                  (Eq. 29, textbook form)
 // Potential    phi_i += q_j erfc(alpha r) / r
 // within r < r_c.  Particles are counting-sorted into linked cells of edge
-// >= r_c (at least 3 per dimension); one thread serves one particle and
-// visits the 27 neighbouring cells (Sec. 3.2: linked-cell list).  Each ordered
+// >= r_c / 2 (at least 5 per dimension; else edge >= r_c, at least 3); one
+// thread serves one particle and visits the 125 (27) neighbouring cells
+// (Sec. 3.2: linked-cell list).  Each ordered
 // pair is visited from both ends, so no atomics are needed; the energy and
 // virial take half of each visit.  Boxes too small for 3 cells per dimension
 // use the all-pairs kernel with the minimum image (r_c <= L/2 is required).
@@ -47,9 +48,13 @@ __device__ __forceinline__ void pair_term(R dx, R dy, R dz, R qi, R qj, const Re
     acc[6] += R(0.5) * fs * dy * dz;
 }
 
-// Writes the real-space force and potential (and the self term of phi) to F
-// and phi in the caller's particle order; part[block] gets (E, W..) partials.
-template <typename R>
+// Adds the real-space force and potential (and the self term of phi) to F
+// and phi in the caller's particle order (zeroed buffers; global atomics);
+// part[block] gets (E, W..) partials.  SR: stencil radius in cells ((2 SR +
+// 1)^3 cells of edge >= r_c / SR).  Block row blockIdx.y = dz + SR takes one
+// z-layer of the stencil, so a particle is served by 2 SR + 1 threads and
+// small systems still fill the GPU.
+template <typename R, int SR>
 __global__ void __launch_bounds__(256) k_realspace_cells(int N, const typename Rec<R>::T* __restrict__ rec,
                                                          const uint32_t* __restrict__ cell_of,
                                                          const uint32_t* __restrict__ offset,
@@ -65,11 +70,12 @@ __global__ void __launch_bounds__(256) k_realspace_cells(int N, const typename R
         const uint32_t c = cell_of[i];
         const int cx = c % rp.nc[0], cy = (c / rp.nc[0]) % rp.nc[1], cz = c / (rp.nc[0] * rp.nc[1]);
         R f[3] = {R(0), R(0), R(0)}, ph = R(0);
-        for (int dz = -1; dz <= 1; dz++) {
+        {
+            const int dz = (int)blockIdx.y - SR;
             const int nz = (cz + dz + rp.nc[2]) % rp.nc[2];
-            for (int dy = -1; dy <= 1; dy++) {
+            for (int dy = -SR; dy <= SR; dy++) {
                 const int ny = (cy + dy + rp.nc[1]) % rp.nc[1];
-                for (int dx = -1; dx <= 1; dx++) {
+                for (int dx = -SR; dx <= SR; dx++) {
                     const int nx = (cx + dx + rp.nc[0]) % rp.nc[0];
                     const uint32_t nb = nx + rp.nc[0] * (ny + rp.nc[1] * nz);
                     const R sx = ri.x - (R)dx * rp.h[0], sy = ri.y - (R)dy * rp.h[1], sz = ri.z - (R)dz * rp.h[2];
@@ -84,13 +90,13 @@ __global__ void __launch_bounds__(256) k_realspace_cells(int N, const typename R
         }
         const uint32_t oi = perm[i];
         if (F) {
-            F[3 * (size_t)oi] = rp.ke * f[0];
-            F[3 * (size_t)oi + 1] = rp.ke * f[1];
-            F[3 * (size_t)oi + 2] = rp.ke * f[2];
+            atomicAdd(F + 3 * (size_t)oi, rp.ke * f[0]);
+            atomicAdd(F + 3 * (size_t)oi + 1, rp.ke * f[1]);
+            atomicAdd(F + 3 * (size_t)oi + 2, rp.ke * f[2]);
         }
-        if (phi) phi[oi] = rp.ke * (ph + rp.self_phi * ri.w);
+        if (phi) atomicAdd(phi + oi, rp.ke * (ph + (blockIdx.y == 0 ? rp.self_phi * ri.w : R(0))));
     }
-    block_reduce_to_double<R, 7>(acc, part + 8 * (size_t)blockIdx.x, red);
+    block_reduce_to_double<R, 7>(acc, part + 8 * ((size_t)blockIdx.y * gridDim.x + blockIdx.x), red);
 }
 
 // All pairs with the minimum image; records hold wrapped absolute positions.
@@ -129,19 +135,25 @@ __global__ void __launch_bounds__(256) k_realspace_allpairs(int N, const typenam
 }
 
 // Adds the real-space force and potential (computed beside the reciprocal
-// part into their own buffers) to the reciprocal ones.
+// part into their own buffers) to the reciprocal ones, and clears those
+// buffers for the next evaluation.
 template <typename R>
-__global__ void __launch_bounds__(256) k_combine(int N, const R* __restrict__ Fr, const R* __restrict__ phir,
+__global__ void __launch_bounds__(256) k_combine(int N, R* __restrict__ Fr, R* __restrict__ phir,
                                                  R* __restrict__ F, R* __restrict__ phi)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     if (F) {
-        F[3 * (size_t)i] += Fr[3 * (size_t)i];
-        F[3 * (size_t)i + 1] += Fr[3 * (size_t)i + 1];
-        F[3 * (size_t)i + 2] += Fr[3 * (size_t)i + 2];
+#pragma unroll
+        for (int t = 0; t < 3; t++) {
+            F[3 * (size_t)i + t] += Fr[3 * (size_t)i + t];
+            Fr[3 * (size_t)i + t] = R(0);
+        }
     }
-    if (phi) phi[i] += phir[i];
+    if (phi) {
+        phi[i] += phir[i];
+        phir[i] = R(0);
+    }
 }
 
 // ---------------------------------------------------------------- assembly
