@@ -31,10 +31,20 @@ __device__ __forceinline__ void pair_term(R dx, R dy, R dz, R qi, R qj, const Re
 {
     const R r2 = dx * dx + dy * dy + dz * dz;
     if (r2 >= rp.rc2 || r2 <= R(0)) return;
-    const R r = dsqrt(r2);
-    const R ar = rp.alpha * r;
-    const R ec = derfc(ar) / r;
-    const R fs = qi * qj * (ec + rp.two_a_sqpi * dexp(-ar * ar)) / r2;
+    R ec, fs;
+    if constexpr (sizeof(R) == 4) {
+        // single precision: one reciprocal square root instead of a square
+        // root and two divisions (rsqrtf is within 2 ulp)
+        const float rinv = rsqrtf(r2);
+        const float ar = rp.alpha * (r2 * rinv);
+        ec = erfcf(ar) * rinv;
+        fs = qi * qj * (ec + rp.two_a_sqpi * expf(-ar * ar)) * (rinv * rinv);
+    } else {
+        const R r = dsqrt(r2);
+        const R ar = rp.alpha * r;
+        ec = derfc(ar) / r;
+        fs = qi * qj * (ec + rp.two_a_sqpi * dexp(-ar * ar)) / r2;
+    }
     f[0] += fs * dx;
     f[1] += fs * dy;
     f[2] += fs * dz;
