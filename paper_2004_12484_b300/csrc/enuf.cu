@@ -309,6 +309,7 @@ struct enuf_plan {
     cudaStream_t cap_stream = nullptr;
     cudaStream_t aux_stream = nullptr;  // side branch (assembly beside the interpolation)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    double* hout = nullptr;  // pinned host copy of the results (host-buffer entry point)
     bool use_graph = true;
     bool profile = false;
     bool attrs_done = false;
@@ -934,6 +935,10 @@ int enuf_plan_create(const enuf_params* params, void* cuda_stream, int allocate,
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pl->aux_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess && cudaMallocHost((void**)&pl->hout, ENUF_NOUT * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();  // pinned memory is an optimisation: fall back to a pageable copy
+        pl->hout = nullptr;
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
@@ -1003,6 +1008,7 @@ int enuf_plan_destroy(enuf_plan* pl)
     if (pl->ev_join) cudaEventDestroy(pl->ev_join);
     if (pl->aux_stream) cudaStreamDestroy(pl->aux_stream);
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+    if (pl->hout) cudaFreeHost(pl->hout);
     delete pl;
     return ENUF_OK;
 }
@@ -1018,12 +1024,13 @@ int enuf_energy_forces(enuf_plan* pl, const void* pos, const void* q, double* E_
     if (!pl) return fail(ENUF_EINVAL, "plan is NULL");
     double* dout = at<double>(pl, pl->lay.out);
     LCHK(compute_impl(pl, pos, q, F, phi, dout, flags));
-    double h[ENUF_NOUT];
-    CK(cudaMemcpyAsync(h, dout, sizeof(h), cudaMemcpyDeviceToHost, pl->stream));
+    double hl[ENUF_NOUT];
+    double* h = pl->hout ? pl->hout : hl;  // pinned: the copy queues behind the evaluation
+    CK(cudaMemcpyAsync(h, dout, ENUF_NOUT * sizeof(double), cudaMemcpyDeviceToHost, pl->stream));
     CK(cudaStreamSynchronize(pl->stream));
     if (E_host) *E_host = h[ENUF_OUT_E];
     if (virial_host) std::memcpy(virial_host, h + ENUF_OUT_VIRIAL, 9 * sizeof(double));
-    if (parts_host) std::memcpy(parts_host, h, sizeof(h));
+    if (parts_host) std::memcpy(parts_host, h, ENUF_NOUT * sizeof(double));
     return check_status(h);
 }
 
@@ -1041,10 +1048,14 @@ int enuf_energy_forces_host(enuf_plan* pl, const void* pos_host, const void* q_h
     if ((flags & ENUF_WANT_PHI) && !phi) flags &= ~ENUF_WANT_PHI;
     double* dout = at<double>(pl, y.out);
     LCHK(compute_impl(pl, pl->ws + y.s_pos, pl->ws + y.s_q, F, phi, dout, flags));
-    double h[ENUF_NOUT];
-    CK(cudaMemcpyAsync(h, dout, sizeof(h), cudaMemcpyDeviceToHost, pl->stream));
+    // every copy queued behind the evaluation, one synchronisation (the
+    // results go to the plan's pinned buffer: a copy into pageable memory
+    // would return only when it is done)
     if (F_host) CK(cudaMemcpyAsync(F_host, F, 3 * N * rs, cudaMemcpyDeviceToHost, pl->stream));
     if (phi) CK(cudaMemcpyAsync(phi_host, phi, N * rs, cudaMemcpyDeviceToHost, pl->stream));
+    double hl[ENUF_NOUT];
+    double* h = pl->hout ? pl->hout : hl;
+    CK(cudaMemcpyAsync(h, dout, ENUF_NOUT * sizeof(double), cudaMemcpyDeviceToHost, pl->stream));
     CK(cudaStreamSynchronize(pl->stream));
     if (E_host) *E_host = h[ENUF_OUT_E];
     if (virial_host) std::memcpy(virial_host, h + ENUF_OUT_VIRIAL, 9 * sizeof(double));
