@@ -24,6 +24,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -149,7 +150,9 @@ class Clocks:
 
     def __init__(self, index):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples: a scratch file (ENUF_CLOCKS_DIR keeps them somewhere chosen)
+        d = os.environ.get("ENUF_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"enuf_clocks_{os.getpid()}.csv")
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
