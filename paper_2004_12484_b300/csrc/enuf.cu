@@ -213,10 +213,11 @@ int resolve(const enuf_params* in, Resolved& r)
 struct Layout {
     size_t status, out, mean;
     size_t counts, offsets, work, nwork, work2, nwork2, item2;
+    size_t csum_g, cbase_g, csum_r, cbase_r;  // chunk totals / bases of the chunked scans
     size_t key, rank, rec_tmp, rec, perm, tile_of;
     size_t rcounts, roffsets, rrec, rperm, rcell;
     size_t rkey, rrank, rrec_tmp, Fr, phir;  // real-space sort scratch and outputs
-    size_t qpart, kpart, rpart, fpart;
+    size_t qpart, kpart, rpart, fpart, fscratch;
     size_t twid, tk, te, td;
     size_t grid, C1, C2, C3, C4, fld;
     size_t s_pos, s_q, s_F, s_phi;
@@ -241,7 +242,7 @@ Layout layout(const Resolved& r)
     const size_t recsz = r.fp64 ? sizeof(d4) : sizeof(f4);
     const size_t nblkN = (N + 255) / 256;
     const size_t nblkZ = ((size_t)r.P + r.gz.W - 1) / r.gz.W;
-    L.status = take(16);  // status word; at +8 and +12 the block counters of the two sorts
+    L.status = take(16);  // status word; at +4 the assembly's block counter, at +8 and +12 those of the two sorts
     L.out = take(ENUF_NOUT * 8);
     L.mean = take(4 * 8);
     L.counts = take((size_t)(r.nbins + 1) * 4 * count_stride(r.nbins));
@@ -251,6 +252,11 @@ Layout layout(const Resolved& r)
     L.work2 = take((size_t)r.max_work2 * 16);
     L.nwork2 = take(4);
     L.item2 = take((size_t)r.nbins * 4);
+    const size_t nchg = (size_t)(r.nbins + kScanChunk - 1) / kScanChunk, nchr = (size_t)(r.nrbins + kScanChunk - 1) / kScanChunk;
+    L.csum_g = take(nchg * 12);
+    L.cbase_g = take(nchg * 12);
+    L.csum_r = take(nchr * 12);
+    L.cbase_r = take(nchr * 12);
     L.key = take(N * 4);
     L.rank = take(N * 4);
     L.rec_tmp = take(N * recsz);
@@ -271,6 +277,7 @@ Layout layout(const Resolved& r)
     L.kpart = take(nblkZ * 8 * 8);
     L.rpart = take(nblkN * 5 * 8 * 8);  // up to 5 stencil layers of blocks
     L.fpart = take(nblkN * 4 * 8);
+    L.fscratch = take(64 * 16 * 8);  // assembly: 16 sums per block, at most 64 blocks
     L.twid = take(M * vs);
     L.tk = take(3 * r.Kb * rs);
     L.te = take(3 * r.Kb * rs);
@@ -529,6 +536,32 @@ template <typename R> int launch_fft_chain(Launcher& L, enuf_plan* pl, int nf)
     }
 }
 
+// Bin counts above this are scanned by the chunked passes (k_scan_sums,
+// k_scan_bases, k_scan_apply) rather than by the key pass's last block.
+constexpr int kFusedScanMax = 16384;
+
+int launch_chunked_scan(Launcher& L, enuf_plan* pl, const ScanArgs& sa, int group, size_t csum_off,
+                        size_t cbase_off)
+{
+    const int nch = (sa.nbins + kScanChunk - 1) / kScanChunk;
+    uint32_t* cs = at<uint32_t>(pl, csum_off);
+    uint32_t* cb = at<uint32_t>(pl, cbase_off);
+    int* status = at<int>(pl, pl->lay.status);
+    if (group == 8) LCHK(L.go("scan_sums", k_scan_sums<8>, dim3(nch), dim3(256), 0, sa, cs));
+    else LCHK(L.go("scan_sums", k_scan_sums<1>, dim3(nch), dim3(256), 0, sa, cs));
+    LCHK(L.go("scan_bases", k_scan_bases, dim3(1), dim3(1024), 0, sa, nch, (const uint32_t*)cs, cb, status));
+    if (group == 8) LCHK(L.go("scan_apply", k_scan_apply<8>, dim3(nch), dim3(256), 0, sa, (const uint32_t*)cb, status));
+    else LCHK(L.go("scan_apply", k_scan_apply<1>, dim3(nch), dim3(256), 0, sa, (const uint32_t*)cb, status));
+    return ENUF_OK;
+}
+
+// Blocks of the assembly: one up to 4096 partials of a quantity, at most 64.
+int fin_blocks(const FinalParams& fp)
+{
+    const int n = std::max(fp.nq, std::max(fp.nk, fp.nr));
+    return std::max(1, std::min(64, (n + 4095) / 4096));
+}
+
 BinGeom make_geom(const int S[3], int T, const double L3[3], bool grid_units, int sub = 1, int lr = 0)
 {
     BinGeom g{};
@@ -570,11 +603,13 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
     // outputs are added to the reciprocal ones after both
     auto real_space = [&]() -> int {
         const BinGeom gr = make_geom(r.ncell, 1, r.prm.L, false);
+        const bool rbig = r.nrbins > kFusedScanMax;
         ScanArgs sr{r.nrbins, at<uint32_t>(pl, y.rcounts), count_stride(r.nrbins), at<uint32_t>(pl, y.roffsets),
                     kWorkCap, (int4*)nullptr, (int*)nullptr, 0, kSpreadCap, (uint32_t*)nullptr, (int*)nullptr, 0,
-                    at<unsigned>(pl, y.status + 12)};
+                    rbig ? (unsigned*)nullptr : at<unsigned>(pl, y.status + 12)};
         LCHK(L.go("real_bin_keys", k_bin_keys<R, 1>, dim3(nblkN), dim3(256), 0, N, pos, q, gr, at<uint32_t>(pl, y.rkey),
                   at<uint32_t>(pl, y.rrank), at<RecT>(pl, y.rrec_tmp), sr, at<int>(pl, y.status), (double*)nullptr));
+        if (rbig) LCHK(launch_chunked_scan(L, pl, sr, 1, y.csum_r, y.cbase_r));
         LCHK(L.go("real_scatter", k_scatter<R>, dim3(nblkN), dim3(256), 0, N, at<const uint32_t>(pl, y.rkey),
                   at<const uint32_t>(pl, y.rrank), at<const uint32_t>(pl, y.roffsets), at<const RecT>(pl, y.rrec_tmp),
                   at<RecT>(pl, y.rrec), at<uint32_t>(pl, y.rperm), at<uint32_t>(pl, y.rcell), (const uint32_t*)nullptr,
@@ -627,12 +662,15 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
     const int Sg[3] = {r.prm.M, r.prm.M, r.prm.M};
     const BinGeom gg = make_geom(Sg, r.T, r.prm.L, true, r.S, r.lr);
     {
+        const bool big = r.nbins > kFusedScanMax;
         ScanArgs sa{r.nbins, at<uint32_t>(pl, y.counts), count_stride(r.nbins), at<uint32_t>(pl, y.offsets),
                     kWorkCap, at<int4>(pl, y.work), at<int>(pl, y.nwork), r.max_work, kSpreadCap,
-                    at<uint32_t>(pl, y.item2), at<int>(pl, y.nwork2), r.max_work2, at<unsigned>(pl, y.status + 8)};
+                    at<uint32_t>(pl, y.item2), at<int>(pl, y.nwork2), r.max_work2,
+                    big ? (unsigned*)nullptr : at<unsigned>(pl, y.status + 8)};
         LCHK(L.go("bin_keys", r.lr ? k_bin_keys<R, 8> : k_bin_keys<R, 1>, dim3(nblkN), dim3(256), 0, N, pos, q, gg,
                   at<uint32_t>(pl, y.key), at<uint32_t>(pl, y.rank), at<RecT>(pl, y.rec_tmp), sa, at<int>(pl, y.status),
                   at<double>(pl, y.qpart)));
+        if (big) LCHK(launch_chunked_scan(L, pl, sa, r.lr ? 8 : 1, y.csum_g, y.cbase_g));
     }
     LCHK(L.go("scatter", k_scatter<R>, dim3(nblkN), dim3(256), 0, N, at<const uint32_t>(pl, y.key),
               at<const uint32_t>(pl, y.rank), at<const uint32_t>(pl, y.offsets), at<const RecT>(pl, y.rec_tmp),
@@ -663,8 +701,9 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
         CK(cudaStreamWaitEvent(pl->aux_stream, pl->ev_fork, 0));
         const cudaStream_t main_st = L.st;
         L.st = pl->aux_stream;
-        const int rc = L.go("finalize", k_finalize, dim3(1), dim3(512), 0, at<const double>(pl, y.qpart),
-                            at<const double>(pl, y.kpart), at<const double>(pl, y.rpart), fp, at<int>(pl, y.status), o);
+        const int rc = L.go("finalize", k_finalize, dim3(fin_blocks(fp)), dim3(512), 0, at<const double>(pl, y.qpart),
+                            at<const double>(pl, y.kpart), at<const double>(pl, y.rpart), fp, at<int>(pl, y.status), o,
+                            at<double>(pl, y.fscratch), at<unsigned>(pl, y.status + 4));
         L.st = main_st;
         if (rc != ENUF_OK) {
             // rejoin the side branch before returning (a capture must end joined)
@@ -684,8 +723,9 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
                   want_phi ? phi : (R*)nullptr));
     if (side) CK(cudaStreamWaitEvent(L.st, pl->ev_join, 0));
     else
-        LCHK(L.go("finalize", k_finalize, dim3(1), dim3(512), 0, at<const double>(pl, y.qpart),
-                  at<const double>(pl, y.kpart), at<const double>(pl, y.rpart), fp, at<int>(pl, y.status), o));
+        LCHK(L.go("finalize", k_finalize, dim3(fin_blocks(fp)), dim3(512), 0, at<const double>(pl, y.qpart),
+                  at<const double>(pl, y.kpart), at<const double>(pl, y.rpart), fp, at<int>(pl, y.status), o,
+                  at<double>(pl, y.fscratch), at<unsigned>(pl, y.status + 4)));
     if (want_phi && !konly)
         LCHK(L.go("phi_background", k_phi_background<R>, dim3(nblkN), dim3(256), 0, N, (const double*)o,
                   -r.prm.coulomb_k * kPi / (fp.V * r.prm.alpha * r.prm.alpha), phi));

@@ -173,29 +173,59 @@ struct FinalParams {
     int kspace_only;
 };
 
-// One block of 512 threads (16 warps): warp w sums quantity w over all
-// per-block partials in a fixed order (lane-strided, then a fixed shuffle
-// tree), so the result is deterministic.  Adds the self energy (Eq. 24) and
-// the background term and writes the ENUF_NOUT results.
+// Blocks of 512 threads (16 warps): in block b, warp w sums quantity w over
+// block b's fixed chunk of the per-block partials (lane-strided, then a
+// fixed shuffle tree); the last block to finish (no block waits for another)
+// adds the blocks' sums in block order, so the result is deterministic, adds
+// the self energy (Eq. 24) and the background term and writes the ENUF_NOUT
+// results.  scratch: 16 doubles per block; done: kept zero between calls.
 __global__ void __launch_bounds__(512) k_finalize(const double* __restrict__ qpart, const double* __restrict__ kpart,
                                                   const double* __restrict__ rpart, FinalParams fp,
-                                                  int* __restrict__ status, double* __restrict__ out)
+                                                  int* __restrict__ status, double* __restrict__ out,
+                                                  double* __restrict__ scratch, unsigned* __restrict__ done)
 {
     __shared__ double s[16];
+    __shared__ bool s_last;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nb = gridDim.x, b = blockIdx.x;
+    auto chunk = [&](int n, int& lo, int& hi) {
+        const int c = (n + nb - 1) / nb;
+        lo = min(n, b * c);
+        hi = min(n, lo + c);
+    };
     double a = 0.0;
+    int lo, hi;
     if (w < 2) {
-        for (int b = lane; b < fp.nq; b += 32) a += qpart[2 * b + w];
+        chunk(fp.nq, lo, hi);
+        for (int k = lo + lane; k < hi; k += 32) a += qpart[2 * k + w];
     } else if (w < 9) {
-        for (int b = lane; b < fp.nk; b += 32) a += kpart[8 * b + (w - 2)];
+        chunk(fp.nk, lo, hi);
+        for (int k = lo + lane; k < hi; k += 32) a += kpart[8 * k + (w - 2)];
     } else {
-        for (int b = lane; b < fp.nr; b += 32) a += rpart[8 * b + (w - 9)];
+        chunk(fp.nr, lo, hi);
+        for (int k = lo + lane; k < hi; k += 32) a += rpart[8 * k + (w - 9)];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (lane == 0) s[w] = a;
+    if (nb > 1) {
+        if (lane == 0) scratch[16 * b + w] = a;
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == (unsigned)nb - 1;
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+        if (threadIdx.x < 16) {
+            double t = 0.0;
+            for (int k = 0; k < nb; k++) t += __ldcg(scratch + 16 * k + threadIdx.x);
+            s[threadIdx.x] = t;
+        }
+    } else if (lane == 0) {
+        s[w] = a;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
+        if (nb > 1) *done = 0u;  // ready for the next evaluation
         const double q2 = s[0], Q = s[1];
         const double Ek = s[2];
         const double Er = fp.nr ? fp.ke * s[9] : 0.0;

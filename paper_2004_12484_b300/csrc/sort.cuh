@@ -90,16 +90,24 @@ struct ScanArgs {
 
 constexpr int kScanPer = 8;  // bins per thread and segment
 
+// Scans bins [lo, hi) starting from the running totals base0 (particles,
+// items of `work`, items of the per-bin list; NULL: zero); `final`: this
+// block ends the scan and writes the totals.
 template <int GROUP, int NT>
 __device__ __forceinline__ void scan_bins_block(const ScanArgs& a, int* status, uint32_t* s_a, uint32_t* s_b,
-                                                uint32_t (*s_sum)[32])
+                                                uint32_t (*s_sum)[32], int lo, int hi, const uint32_t* base0,
+                                                bool final)
 {
     constexpr int PER = kScanPer, SEG = NT * PER, NWARP = NT / 32;
     static_assert(PER % GROUP == 0, "a thread's bins hold whole groups");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t base[3] = {0u, 0u, 0u};  // particles, items of work, items of the per-bin list
-    for (int s0 = 0; s0 < a.nbins; s0 += SEG) {
-        const int ns = min(SEG, a.nbins - s0);
+    if (base0) {
+#pragma unroll
+        for (int e = 0; e < 3; e++) base[e] = base0[e];
+    }
+    for (int s0 = lo; s0 < hi; s0 += SEG) {
+        const int ns = min(SEG, hi - s0);
         {
             // all of the thread's loads in flight at once
             uint32_t t[PER];
@@ -202,7 +210,7 @@ __device__ __forceinline__ void scan_bins_block(const ScanArgs& a, int* status, 
         for (int e = 0; e < 3; e++) base[e] += s_sum[e][NWARP - 1];
         __syncthreads();
     }
-    if (tid == 0) {
+    if (final && tid == 0) {
         a.offset[a.nbins] = base[0];
         if (a.work) {
             int nw = (int)base[1];
@@ -279,15 +287,140 @@ __global__ void __launch_bounds__(256) k_bin_keys(int N, const R* __restrict__ p
         R v[2] = {qq * qq, qq};
         block_reduce_to_double<R, 2>(v, qpart + 2 * (size_t)blockIdx.x, red);
     }
-    // the last block to finish scans the bins (no block waits for another)
+    // the last block to finish scans the bins (no block waits for another);
+    // large bin counts are scanned by the k_scan_* passes instead
+    if (!sa.done) return;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) s_last = atomicAdd(sa.done, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    scan_bins_block<GROUP, 256>(sa, status, s_scan, s_scan + 256 * kScanPer, s_sum);
+    scan_bins_block<GROUP, 256>(sa, status, s_scan, s_scan + 256 * kScanPer, s_sum, 0, sa.nbins, nullptr, true);
     if (threadIdx.x == 0) *sa.done = 0u;  // ready for the next evaluation
+}
+
+// Pass 2 for large bin counts, in three launches over chunks of
+// kScanChunk bins: (a) per-chunk totals, (b) one block scans the totals
+// into chunk bases and writes the overall totals, (c) every chunk is scanned
+// from its base (offsets, item indices, work items; counts cleared).
+constexpr int kScanChunk = 256 * kScanPer;
+
+template <int GROUP>
+__global__ void __launch_bounds__(256) k_scan_sums(ScanArgs a, uint32_t* __restrict__ csum)
+{
+    constexpr int PER = kScanPer;
+    __shared__ uint32_t s_red[3][8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lo = blockIdx.x * kScanChunk, hi = min(a.nbins, lo + kScanChunk);
+    const int b0 = lo + tid * PER;
+    uint32_t n[PER];
+    uint32_t v[3] = {0u, 0u, 0u};
+#pragma unroll
+    for (int k = 0; k < PER; k++) {
+        n[k] = b0 + k < hi ? __ldcg(a.count + (size_t)(b0 + k) * a.cs) : 0u;
+        v[0] += n[k];
+        if (a.item2) v[2] += (n[k] + a.cap2 - 1) / a.cap2;
+    }
+    if (a.work) {
+#pragma unroll
+        for (int gg = 0; gg < PER / GROUP; gg++) {
+            uint32_t ng = 0;
+#pragma unroll
+            for (int k = 0; k < GROUP; k++) ng += n[gg * GROUP + k];
+            v[1] += (ng + a.cap - 1) / a.cap;
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 3; e++) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[e] += __shfl_xor_sync(0xffffffffu, v[e], o);
+        if (lane == 0) s_red[e][warp] = v[e];
+    }
+    __syncthreads();
+    if (tid < 3) {
+        uint32_t t = 0;
+        for (int w = 0; w < 8; w++) t += s_red[tid][w];
+        csum[3 * blockIdx.x + tid] = t;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_bases(ScanArgs a, int nchunks, const uint32_t* __restrict__ csum,
+                                                     uint32_t* __restrict__ cbase, int* __restrict__ status)
+{
+    __shared__ uint32_t s_sum[3][32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int per = (nchunks + 1023) / 1024;
+    const int c0 = min(nchunks, tid * per), c1 = min(nchunks, c0 + per);
+    uint32_t v[3] = {0u, 0u, 0u};
+    for (int c = c0; c < c1; c++) {
+#pragma unroll
+        for (int e = 0; e < 3; e++) v[e] += csum[3 * c + e];
+    }
+    uint32_t inc[3] = {v[0], v[1], v[2]};
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+        for (int e = 0; e < 3; e++) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, inc[e], o);
+            if (lane >= o) inc[e] += t;
+        }
+    }
+    if (lane == 31) {
+#pragma unroll
+        for (int e = 0; e < 3; e++) s_sum[e][warp] = inc[e];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t x[3];
+#pragma unroll
+        for (int e = 0; e < 3; e++) x[e] = s_sum[e][lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+            for (int e = 0; e < 3; e++) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, x[e], o);
+                if (lane >= o) x[e] += t;
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < 3; e++) s_sum[e][lane] = x[e];
+    }
+    __syncthreads();
+    uint32_t run[3];
+#pragma unroll
+    for (int e = 0; e < 3; e++) run[e] = (warp ? s_sum[e][warp - 1] : 0u) + inc[e] - v[e];
+    for (int c = c0; c < c1; c++) {
+#pragma unroll
+        for (int e = 0; e < 3; e++) {
+            cbase[3 * c + e] = run[e];
+            run[e] += csum[3 * c + e];
+        }
+    }
+    if (tid == 1023) {
+        a.offset[a.nbins] = s_sum[0][31];
+        if (a.work) {
+            int nw = (int)s_sum[1][31];
+            if (nw > a.max_work) { atomicOr(status, ST_WORKLIST); nw = a.max_work; }
+            *a.nwork = nw;
+        }
+        if (a.item2) {
+            int nw = (int)s_sum[2][31];
+            if (nw > a.max_work2) { atomicOr(status, ST_WORKLIST); nw = a.max_work2; }
+            *a.nwork2 = nw;
+        }
+    }
+}
+
+template <int GROUP>
+__global__ void __launch_bounds__(256) k_scan_apply(ScanArgs a, const uint32_t* __restrict__ cbase,
+                                                    int* __restrict__ status)
+{
+    __shared__ uint32_t s_scan[2 * 256 * kScanPer];
+    __shared__ uint32_t s_sum[3][32];
+    const int lo = blockIdx.x * kScanChunk, hi = min(a.nbins, lo + kScanChunk);
+    scan_bins_block<GROUP, 256>(a, status, s_scan, s_scan + 256 * kScanPer, s_sum, lo, hi, cbase + 3 * blockIdx.x,
+                                false);
 }
 
 // Pass 3: scatter the records into bin order; perm[sorted] = original index.
