@@ -392,14 +392,16 @@ def main():
         for _ in range(3):
             plan.energy_forces_host(ph, qh, F_host=Fh, kspace_only=True)
         t_e2e = []
-        for _ in range(20):
+        for _ in range(50):
             flush.fill_(1.0)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             plan.energy_forces_host(ph, qh, F_host=Fh, kspace_only=True)
             t_e2e.append(time.perf_counter() - t0)
         e2e = {"value": N / float(np.mean(t_e2e)) / 1e6, "unit": UNIT, "h2d_bytes_per_step": 16 * N,
-               "d2h_bytes_per_step": 12 * N + 16 * 8, "ms_per_step": float(np.mean(t_e2e)) * 1e3}
+               "d2h_bytes_per_step": 12 * N + 16 * 8, "ms_per_step": float(np.mean(t_e2e)) * 1e3,
+               "ms_median": float(np.median(t_e2e)) * 1e3, "ms_min": float(np.min(t_e2e)) * 1e3,
+               "calls": len(t_e2e)}
         # ---- oracle on the host cores
         cv, cores, runs, el = time_oracle(d)
         cpu = {"value": cv, "unit": UNIT, "cores": cores, "kind": "oracle",

@@ -834,6 +834,27 @@ void reset_zeroed(enuf_plan* pl)
     cudaGetLastError();
 }
 
+// Instantiates a captured graph, adds it to the plan's cache (evicting the
+// least recently used of 8) and launches it on the plan's stream.
+int cache_and_launch(enuf_plan* pl, GraphEntry ge, cudaGraph_t graph)
+{
+    cudaError_t e = cudaGraphInstantiate(&ge.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ENUF_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    if (pl->graphs.size() >= 8) {
+        auto old = std::min_element(pl->graphs.begin(), pl->graphs.end(),
+                                    [](const GraphEntry& a, const GraphEntry& b) { return a.stamp < b.stamp; });
+        cudaGraphExecDestroy(old->exec);
+        pl->graphs.erase(old);
+    }
+    pl->graphs.push_back(ge);
+    CK(cudaGraphLaunch(ge.exec, pl->stream));
+    return ENUF_OK;
+}
+
 int compute_impl(enuf_plan* pl, const void* pos, const void* q, void* F, void* phi, double* out, int flags)
 {
     if (!pl) return fail(ENUF_EINVAL, "plan is NULL");
@@ -898,21 +919,62 @@ int compute_impl(enuf_plan* pl, const void* pos, const void* q, void* F, void* p
         return fail(ENUF_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
     }
     GraphEntry ge{pos, q, F, phi, out, flags, nullptr, ++pl->stamp};
-    e = cudaGraphInstantiate(&ge.exec, graph, 0);
-    cudaGraphDestroy(graph);
+    return cache_and_launch(pl, ge, graph);
+}
+
+// Host-buffer call as one graph: the copies of positions and charges in,
+// the evaluation, and the copies of forces, potentials and results out
+// (pinned host buffers only; cached by the host pointers, flag bit 30 marks
+// these entries).
+int host_graph_call(enuf_plan* pl, const void* pos_host, const void* q_host, void* F_host, void* phi_host,
+                    int flags, void* F, void* phi, double* dout)
+{
+    const size_t N = (size_t)pl->r.prm.N, rs = pl->r.rsz;
+    const Layout& y = pl->lay;
+    const int key = flags | (1 << 30);
+    for (auto& g : pl->graphs) {
+        if (g.pos == pos_host && g.q == q_host && g.F == F_host && g.phi == phi_host && g.out == pl->hout &&
+            g.flags == key) {
+            g.stamp = ++pl->stamp;
+            CK(cudaGraphLaunch(g.exec, pl->stream));
+            return ENUF_OK;
+        }
+    }
+    const cudaStream_t cs = pl->cap_stream;
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaMemcpyAsync(pl->ws + y.s_pos, pos_host, 3 * N * rs, cudaMemcpyHostToDevice, cs);
+    cudaMemcpyAsync(pl->ws + y.s_q, q_host, N * rs, cudaMemcpyHostToDevice, cs);
+    int rc = run_sequence(pl, cs, false, pl->ws + y.s_pos, pl->ws + y.s_q, F, phi, dout, flags);
+    if (rc == ENUF_OK) {
+        if (F_host) cudaMemcpyAsync(F_host, F, 3 * N * rs, cudaMemcpyDeviceToHost, cs);
+        if (phi) cudaMemcpyAsync(phi_host, phi, N * rs, cudaMemcpyDeviceToHost, cs);
+        cudaMemcpyAsync(pl->hout, dout, ENUF_NOUT * sizeof(double), cudaMemcpyDeviceToHost, cs);
+    }
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    if (rc != ENUF_OK) {
+        if (e == cudaSuccess) cudaGraphDestroy(graph);
+        return rc;
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return fail(ENUF_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+        return fail(ENUF_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
     }
-    if (pl->graphs.size() >= 8) {
-        auto old = std::min_element(pl->graphs.begin(), pl->graphs.end(),
-                                    [](const GraphEntry& a, const GraphEntry& b) { return a.stamp < b.stamp; });
-        cudaGraphExecDestroy(old->exec);
-        pl->graphs.erase(old);
+    GraphEntry ge{pos_host, q_host, F_host, phi_host, pl->hout, key, nullptr, ++pl->stamp};
+    return cache_and_launch(pl, ge, graph);
+}
+
+// True for host memory the GPU can copy to and from directly (pinned or
+// registered); a NULL pointer counts as such.
+bool host_pinned(const void* p)
+{
+    if (!p) return true;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
     }
-    pl->graphs.push_back(ge);
-    CK(cudaGraphLaunch(ge.exec, pl->stream));
-    return ENUF_OK;
+    return a.type == cudaMemoryTypeHost;
 }
 
 int check_status(const double* parts)
@@ -1081,12 +1143,24 @@ int enuf_energy_forces_host(enuf_plan* pl, const void* pos_host, const void* q_h
     if (!pos_host || !q_host) return fail(ENUF_EINVAL, "pos_host and q_host are required");
     const size_t N = (size_t)pl->r.prm.N, rs = pl->r.rsz;
     const Layout& y = pl->lay;
-    CK(cudaMemcpyAsync(pl->ws + y.s_pos, pos_host, 3 * N * rs, cudaMemcpyHostToDevice, pl->stream));
-    CK(cudaMemcpyAsync(pl->ws + y.s_q, q_host, N * rs, cudaMemcpyHostToDevice, pl->stream));
     void* F = F_host ? (void*)(pl->ws + y.s_F) : nullptr;
     void* phi = (phi_host && (flags & ENUF_WANT_PHI)) ? (void*)(pl->ws + y.s_phi) : nullptr;
     if ((flags & ENUF_WANT_PHI) && !phi) flags &= ~ENUF_WANT_PHI;
     double* dout = at<double>(pl, y.out);
+    if (flags & ~(ENUF_WANT_VIRIAL | ENUF_WANT_PHI | ENUF_REMOVE_NET_FORCE | ENUF_KSPACE_ONLY))
+        return fail(ENUF_EINVAL, "unknown flag bits");
+    if (pl->use_graph && !pl->profile && pl->hout && host_pinned(pos_host) && host_pinned(q_host) &&
+        host_pinned(F_host) && host_pinned(phi ? phi_host : nullptr)) {
+        // one graph launch and one synchronisation per call
+        LCHK(host_graph_call(pl, pos_host, q_host, F_host, phi ? phi_host : nullptr, flags, F, phi, dout));
+        CK(cudaStreamSynchronize(pl->stream));
+        const double* h = pl->hout;
+        if (E_host) *E_host = h[ENUF_OUT_E];
+        if (virial_host) std::memcpy(virial_host, h + ENUF_OUT_VIRIAL, 9 * sizeof(double));
+        return check_status(h);
+    }
+    CK(cudaMemcpyAsync(pl->ws + y.s_pos, pos_host, 3 * N * rs, cudaMemcpyHostToDevice, pl->stream));
+    CK(cudaMemcpyAsync(pl->ws + y.s_q, q_host, N * rs, cudaMemcpyHostToDevice, pl->stream));
     LCHK(compute_impl(pl, pl->ws + y.s_pos, pl->ws + y.s_q, F, phi, dout, flags));
     // every copy queued behind the evaluation, one synchronisation (the
     // results go to the plan's pinned buffer: a copy into pageable memory

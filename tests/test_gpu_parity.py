@@ -277,6 +277,38 @@ def test_host_buffer_entry_point_matches_device_call():
     assert np.abs(Wv - W2).max() < 1e-5 * np.abs(W2).max()
 
 
+def test_host_buffer_entry_point_pageable_pinned_and_repeated():
+    """Pageable host buffers (copies issued one by one) and pinned ones (the
+    copies captured in the cached graph) give the same results; a second call
+    on the same pinned buffers after the positions were rewritten in place
+    sees the new positions (the graph copies at every launch)."""
+    a = W.rpm(N=4096, seed=15, M=32, p=6, r_c=10.0, alpha=0.3)
+    b = W.rpm(N=4096, seed=16, M=32, p=6, r_c=10.0, alpha=0.3)
+    pos_a, q = W.as_fp32(a["pos"], a["q"])
+    pos_b, _ = W.as_fp32(b["pos"], b["q"])
+    plan = P.Plan(L=a["L"], N=4096, alpha=0.3, r_c=10.0, M=32, p=6, precision="mixed", device=DEV)
+    F1 = np.empty((4096, 3), dtype=np.float32)
+    phi1 = np.empty(4096, dtype=np.float32)
+    E1, W1 = plan.energy_forces_host(np.ascontiguousarray(pos_a, dtype=np.float32),
+                                     np.ascontiguousarray(q, dtype=np.float32), phi_host=phi1, F_host=F1)
+    ph = torch.tensor(pos_a, dtype=torch.float32).pin_memory()
+    qh = torch.tensor(q, dtype=torch.float32).pin_memory()
+    Fh = torch.empty((4096, 3), dtype=torch.float32).pin_memory()
+    phih = torch.empty(4096, dtype=torch.float32).pin_memory()
+    E2, W2 = plan.energy_forces_host(ph, qh, phi_host=phih, F_host=Fh)
+    assert abs(E2 / E1 - 1) < 1e-6
+    assert rel_rms(Fh.double().numpy(), F1.astype(np.float64)) < 1e-5
+    assert rel_rms(phih.double().numpy(), phi1.astype(np.float64)) < 1e-5
+    assert np.abs(W2 - W1).max() < 1e-5 * np.abs(W1).max()
+    ph.copy_(torch.tensor(pos_b, dtype=torch.float32))
+    E3, W3 = plan.energy_forces_host(ph, qh, phi_host=phih, F_host=Fh)
+    parts, F, Wd, phid = plan.energy_forces(ph.to(DEV), qh.to(DEV), phi=True)
+    assert abs(E3 / parts["E"] - 1) < 1e-6 and abs(E3 / E2 - 1) > 1e-4
+    assert rel_rms(Fh.double().numpy(), F.cpu().double().numpy()) < 1e-5
+    assert rel_rms(phih.double().numpy(), phid.cpu().double().numpy()) < 1e-5
+    assert np.abs(W3 - Wd).max() < 1e-5 * np.abs(Wd).max()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_unfused_fft_passes_match_fused(precision, monkeypatch):
     """Grids up to 256 use the fused x-y FFT kernels; the separate-pass
