@@ -385,6 +385,22 @@ def main():
                     "frac": (achieved / peak if achieved else None), "peak_source": src,
                     "traffic": ncu_traffic(dom, d["name"]), "algorithmic_bytes": alg,
                     "kernel_ms": acc[dom]}
+        # FMA roofline of spreading and interpolation (p^3 and f p^3 multiply-
+        # adds per particle, window evaluations not counted) against the FMA
+        # rate measured on this GPU by the library's probe kernel
+        try:
+            fpk = P.fma_peak_tflops()
+
+            def fma_line(kernel, fmas_per_particle):
+                flops = 2.0 * fmas_per_particle * N
+                t = acc.get(kernel)
+                ach = flops / (t * 1e-3) / 1e12 if t else None
+                return {"flops": flops, "achieved_tflops": ach, "frac": (ach / fpk if ach else None), "kernel_ms": t}
+
+            extra["fma_roof"] = {"unit": "TFLOP/s", "peak": fpk, "peak_source": "measured (enuf_fma_peak_tflops)",
+                                 "spread": fma_line("spread", p ** 3), "gather": fma_line("gather", 3 * p ** 3)}
+        except Exception as e:  # report, do not lose the headline line
+            extra["fma_roof"] = {"error": str(e)[:200]}
         # ---- end to end through the host-buffer entry point
         ph = torch.from_numpy(pos32.astype(np.float32)).pin_memory()
         qh = torch.from_numpy(q32.astype(np.float32)).pin_memory()

@@ -213,6 +213,16 @@ int enuf_mlp_train_step(float* w_master, void* w_bf16, float* adam_m, float* ada
                         float beta2, float eps, int step, float* loss_out, float* grad_out, int apply_update,
                         void* stream);
 
+/* ---------------------------------------------------------------------
+ * Measurement helper (not part of the method): the single-precision FMA
+ * rate of the current device, measured by a kernel of independent fused
+ * multiply-add chains, in TFLOP/s (2 flops per FMA).  It is the peak the
+ * FMA roofline of the spreading and interpolation kernels is reported
+ * against.  Synchronous (waits for its kernels on cuda_stream, NULL = legacy
+ * stream); allocates no device memory; runs for a few milliseconds.
+ * --------------------------------------------------------------------- */
+int enuf_fma_peak_tflops(double* tflops, void* cuda_stream);
+
 /* Thread-local description of the last failure ("" if none). */
 const char* enuf_last_error(void);
 

@@ -81,6 +81,7 @@ def lib():
         L.enuf_real_space_noalloc.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
                                               ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                               _vp, _vp, _vp, _vp]
+        L.enuf_fma_peak_tflops.argtypes = [ctypes.POINTER(ctypes.c_double), _vp]
         _lib = L
     return _lib
 
@@ -88,6 +89,14 @@ def lib():
 def _check(rc):
     if rc != 0:
         raise EnufError(f"enuf error {rc}: {lib().enuf_last_error().decode()}")
+
+
+def fma_peak_tflops(stream=None) -> float:
+    """Measured single-precision FMA rate of the current device (TFLOP/s),
+    the peak of the FMA roofline of the spreading and interpolation kernels."""
+    v = ctypes.c_double()
+    _check(lib().enuf_fma_peak_tflops(ctypes.byref(v), _vp(stream or 0)))
+    return v.value
 
 
 def version() -> str:

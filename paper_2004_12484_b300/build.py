@@ -1,4 +1,4 @@
-"""Build step of the CUDA library: compiles ``csrc/enuf.cu`` for sm_103a into
+"""Build step of the CUDA library: compiles the ``csrc`` sources for sm_103a into
 ``libenuf.so`` inside the package directory (in-tree, so that the built
 library travels with the source tree).
 
@@ -49,7 +49,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc(), *NVCC_FLAGS, "-o", tmp, os.path.join(SRC_DIR, "enuf.cu"), os.path.join(SRC_DIR, "noalloc.cu"),
-           os.path.join(SRC_DIR, "mlp.cu")]
+           os.path.join(SRC_DIR, "mlp.cu"), os.path.join(SRC_DIR, "probe.cu")]
     if verbose:
         print(" ".join(cmd), flush=True)
     subprocess.check_call(cmd)

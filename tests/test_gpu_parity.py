@@ -262,6 +262,37 @@ def test_nonfinite_input_is_reported():
     plan.energy_forces(tp, tq)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_reciprocal_part_is_linear_over_a_particle_partition(precision):
+    """The spread grid, its spectrum and hence the reciprocal potential are
+    linear in the charges (the structure factor is additive over any
+    partition of the particles, which a particle-sharded multi-GPU run
+    relies on): with the charges of two disjoint subsets evaluated
+    separately (the other subset's charges zero), the reciprocal potentials
+    sum to those of the whole system, and the energies satisfy
+    E(A + B) = E(A) + E(B) + cross term with cross = sum_{i in B} q_i phi_A(i)."""
+    g = np.random.default_rng(41)
+    L = np.array([24.0, 26.0, 28.0])
+    N = 3000
+    pos = g.uniform(0, 1, size=(N, 3)) * L
+    q = g.normal(size=N)
+    q -= q.mean()
+    pos, q = inputs(pos, q, precision)
+    inA = g.random(N) < 0.4
+    qA = np.where(inA, q, 0.0)
+    qB = np.where(inA, 0.0, q)
+    res = {}
+    for name, qq in (("all", q), ("A", qA), ("B", qB)):
+        parts, F, Wv, ph = run(pos, qq, L, 0.4, 8.0, 32, 6, 8, precision, kspace_only=True)
+        res[name] = (parts["E"], ph)
+    tol = 1e-11 if precision == "fp64" else 2e-6
+    phi_sum = res["A"][1] + res["B"][1]
+    assert rel_rms(phi_sum, res["all"][1]) < tol
+    cross = float((qB * res["A"][1]).sum())
+    E_sum = res["A"][0] + res["B"][0] + cross
+    assert abs(E_sum - res["all"][0]) < tol * 10 * (abs(res["A"][0]) + abs(res["B"][0]) + abs(cross))
+
+
 def test_host_buffer_entry_point_matches_device_call():
     d = W.rpm(N=4096, seed=15, M=32, p=6, r_c=10.0, alpha=0.3)
     pos, q = W.as_fp32(d["pos"], d["q"])
