@@ -12,6 +12,9 @@ arrays.  Functions follow the paper (Yang et al., arXiv:2004.12484):
   29, 41 in textbook form), optionally on a sampled subset of particles.
 * :func:`nfft_ewald` -- O2, the reciprocal part by transposed / conjugated
   NFFT (Eq. 36-38, 41-42) plus the same real-space and self terms.
+* :func:`nfft_ewald_ad`, :func:`kspace_nfft_ad` -- O2 with the forces as the
+  analytic gradient of Eq. 38 (window derivative in the interpolation, one
+  inverse FFT), the variant beside the ik forces of Eq. 41-42.
 * :func:`structure_factor_direct`, :func:`structure_factor_nfft`,
   :func:`fft1d`, :func:`fft3d`, :func:`window`, :func:`window_hat`,
   :func:`window_b`, :func:`image_sum` -- the individual steps, exposed so the
@@ -72,6 +75,10 @@ def lib():
         L.orc_spread.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D]
         L.orc_kspace_nfft.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]
+        L.orc_kspace_nfft_ad.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]
+        L.orc_window_deriv.restype = ctypes.c_double
+        L.orc_window_deriv.argtypes = [ctypes.c_double, ctypes.c_double]
         L.orc_image_sum.restype = ctypes.c_double
         L.orc_image_sum.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_double, ctypes.c_int]
         L.orc_num_threads.restype = ctypes.c_int
@@ -246,6 +253,33 @@ def kspace_nfft(pos, q, L, alpha, M, p, nc=None, ke=1.0):
     if rc != 0:
         raise ValueError(f"bad NFFT parameters or allocation failure ({rc})")
     return float(E[0]), F, phi, W.reshape(3, 3)
+
+
+def kspace_nfft_ad(pos, q, L, alpha, M, p, nc=None, ke=1.0):
+    """O2-ad: the NFFT reciprocal energy of Eq. 38 with forces by analytic
+    differentiation (one inverse FFT of the potential, window gradient in the
+    interpolation); returns (E_K, F_K, phi_K, W_K) like :func:`kspace_nfft`."""
+    pos = _arr(pos, (-1, 3)); q = _arr(q); L = _box(L)
+    if nc is None:
+        nc = M // 4
+    N = len(q)
+    E = np.zeros(1); F = np.zeros((N, 3)); phi = np.zeros(N); W = np.zeros(9)
+    rc = lib().orc_kspace_nfft_ad(N, _dp(pos), _dp(q), _dp(L), alpha, ke, M, p, nc, _dp(E), _dp(F), _dp(phi),
+                                  _dp(W))
+    if rc != 0:
+        raise ValueError(f"bad NFFT parameters or allocation failure ({rc})")
+    return float(E[0]), F, phi, W.reshape(3, 3)
+
+
+def window_deriv(u, b: float):
+    """d phi/du of the Gaussian window in grid units."""
+    u = np.atleast_1d(np.asarray(u, dtype=np.float64))
+    return np.array([lib().orc_window_deriv(float(x), b) for x in u])
+
+
+def nfft_ewald_ad(pos, q, L, alpha, rc, M, p, nc=None, ke=1.0) -> EwaldResult:
+    """O2 with the reciprocal forces by analytic differentiation."""
+    return _assemble(pos, q, L, alpha, rc, ke, kspace_nfft_ad(pos, q, L, alpha, M, p, nc, ke))
 
 
 def _assemble(pos, q, L, alpha, rc, ke, kpart, idx=None):

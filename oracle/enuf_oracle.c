@@ -578,6 +578,93 @@ int orc_kspace_nfft(int64_t N, const double *pos, const double *q, const double 
 }
 
 /* ------------------------------------------------------------------ */
+/* O2-ad: the same reciprocal energy with forces by analytic             */
+/* differentiation.  E~ of Eq. 38 depends on r_j only through the window */
+/* values phi(u_{j,t} - l_t), u_{j,t} = M x_{j,t}/L_t, so its gradient is */
+/*   dE~/dx_{j,t} = q_j (ke 4 pi/V) (M/L_t) sum_l d_t[prod_s phi] A_l,    */
+/* with A_l = sum_n G(k_n) S~(n)/(M c(n)) exp(2 pi i n.l/M) the potential  */
+/* on the grid (one inverse FFT instead of the three of Eq. 41-42).  The  */
+/* forces F = -grad E~ are then the exact gradient of the approximated    */
+/* energy, the variant beside the ik forces of Eq. 41-42.                */
+/* ------------------------------------------------------------------ */
+
+/* d phi/du in grid units: -(2u/b) phi(u). */
+double orc_window_deriv(double u, double b)
+{
+    return -2.0 * u / b * orc_window(u, b);
+}
+
+int orc_kspace_nfft_ad(int64_t N, const double *pos, const double *q, const double *L,
+                       double alpha, double ke, int M, int p, int nc,
+                       double *E, double *F, double *phi, double *vir)
+{
+    if (2 * nc >= M || p > M || p < 2 || (p & 1) || p > 64) return -1;
+    int64_t M2 = (int64_t)M * M, M3 = M2 * M;
+    double b = orc_window_b(M, nc, p);
+    double V = L[0] * L[1] * L[2];
+    double *grid = (double *)malloc(sizeof(double) * 2 * (size_t)M3);
+    double *A = (double *)calloc(2 * (size_t)M3, sizeof(double));
+    if (!grid || !A) { free(grid); free(A); return -2; }
+
+    /* forward: spreading, FFT, scaling (Eq. 36-37); energy and virial
+     * (Eq. 38); potential coefficients G S~(n) / (M c(n)) */
+    orc_spread(N, pos, q, L, M, p, b, grid);
+    orc_fft3d(M, grid, -1);
+    double Eacc = 0.0, W[9] = {0};
+    for (int c = -nc; c <= nc; c++)
+        for (int bb = -nc; bb <= nc; bb++)
+            for (int a = -nc; a <= nc; a++) {
+                if (a == 0 && bb == 0 && c == 0) continue;
+                int n[3] = {a, bb, c};
+                int64_t cell = imod(a, M) + M * imod(bb, M) + M2 * imod(c, M);
+                double chat = orc_window_hat(a, M, b) * orc_window_hat(bb, M, b) * orc_window_hat(c, M, b);
+                double Sr = grid[2 * cell] / chat, Si = grid[2 * cell + 1] / chat;
+                double k[3];
+                wave_vector(n, L, k);
+                double G = green(k, alpha);
+                add_energy_virial(k, G, Sr * Sr + Si * Si, ke * 2.0 * M_PI / V, alpha, &Eacc, W);
+                A[2 * cell] = G * Sr / chat;
+                A[2 * cell + 1] = G * Si / chat;
+            }
+    if (E) *E = Eacc;
+    if (vir) for (int u = 0; u < 9; u++) vir[u] = W[u];
+
+    /* one inverse FFT: the potential on the grid */
+    orc_fft3d(M, A, +1);
+
+    /* interpolation of the potential and of its gradient: the window
+     * product and its three partial derivatives in u */
+    double cF = ke * 4.0 * M_PI / V;
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < N; j++) {
+        double w[3][64], d[3][64];
+        int64_t l0[3];
+        for (int t = 0; t < 3; t++) {
+            double u = M * wrap01(pos[3 * j + t] / L[t]);
+            particle_window(u, p, b, &l0[t], w[t]);
+            for (int a = 0; a < p; a++) d[t][a] = orc_window_deriv(u - (double)(l0[t] + a), b);
+        }
+        double s = 0.0, g[3] = {0.0, 0.0, 0.0};
+        for (int c = 0; c < p; c++)
+            for (int bb = 0; bb < p; bb++)
+                for (int a = 0; a < p; a++) {
+                    int64_t cell = imod(l0[0] + a, M) + M * imod(l0[1] + bb, M) + M2 * imod(l0[2] + c, M);
+                    double v = A[2 * cell];  /* the potential grid is real */
+                    s += w[0][a] * w[1][bb] * w[2][c] * v;
+                    g[0] += d[0][a] * w[1][bb] * w[2][c] * v;
+                    g[1] += w[0][a] * d[1][bb] * w[2][c] * v;
+                    g[2] += w[0][a] * w[1][bb] * d[2][c] * v;
+                }
+        if (phi) phi[j] = cF * s;
+        if (F)
+            for (int t = 0; t < 3; t++) F[3 * j + t] = -q[j] * cF * ((double)M / L[t]) * g[t];
+    }
+    free(grid);
+    free(A);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* Brute-force image sum (Eq. 1), spherical summation order: all image */
 /* vectors n with |n| <= shell (in box units), E = 1/2 sum_n sum_{i,j}'  */
 /* q_i q_j / |r_ij + nL|.  Used only to pin O1 on tiny boxes.           */

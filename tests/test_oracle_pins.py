@@ -327,6 +327,83 @@ def test_nfft_ewald_approaches_direct_with_p():
     assert eF[2] < 5e-6
 
 
+def test_window_derivative_by_central_difference():
+    """d phi/du of the Gaussian window against a central difference of the
+    window itself (closed form -(2u/b) phi(u))."""
+    b = O.window_b(32, 8, 8)
+    u = np.linspace(-4.2, 4.3, 23)
+    h = 1e-5
+    fd = (O.window(u + h, b) - O.window(u - h, b)) / (2 * h)
+    assert np.abs(O.window_deriv(u, b) - fd).max() < 1e-9
+
+
+def _ad_system(seed=21, N=16):
+    g = np.random.default_rng(seed)
+    L = np.array([9.0, 10.0, 11.0])
+    pos = g.uniform(0, 1, size=(N, 3)) * L
+    q = g.normal(size=N); q -= q.mean()
+    return pos, q, L
+
+
+def test_ad_forces_are_minus_gradient_of_nfft_energy():
+    """The analytic-differentiation forces are the exact gradient of the NFFT
+    energy of Eq. 38 (the ik oracle's E, itself pinned against direct Ewald):
+    a central difference of that energy reproduces them to rounding, for any
+    window width, although they differ from the ik forces of Eq. 41-42."""
+    pos, q, L = _ad_system()
+    M, nc = 16, 5
+    for p, alpha in [(4, 0.5), (6, 0.6)]:
+        E, F, _, _ = O.kspace_nfft_ad(pos, q, L, alpha, M, p, nc)
+        _, Fik, _, _ = O.kspace_nfft(pos, q, L, alpha, M, p, nc)
+        h = 1e-5
+        for i in [0, 7, 15]:
+            for t in range(3):
+                u = M * pos[i, t] / L[t]
+                assert abs(u - np.round(u)) > 1e-3  # no window-support change inside the stencil
+                pp = pos.copy(); pp[i, t] += h
+                pm = pos.copy(); pm[i, t] -= h
+                fd = -(O.kspace_nfft(pp, q, L, alpha, M, p, nc)[0] - O.kspace_nfft(pm, q, L, alpha, M, p, nc)[0]) / (2 * h)
+                assert abs(fd - F[i, t]) < 1e-8 * (1 + np.abs(F).max())
+        # the variant is a different discretisation: at p = 4 it measurably
+        # differs from the ik forces
+        if p == 4:
+            assert np.abs(F - Fik).max() > 1e-6 * np.abs(F).max()
+
+
+def test_ad_energy_virial_phi_equal_ik_oracle():
+    """Only the forces differ between the two variants: E~ (Eq. 38), the
+    virial and phi = dE/dq come from the same spectrum."""
+    pos, q, L = _ad_system(seed=22, N=24)
+    kw = dict(alpha=0.55, M=32, p=6, nc=8)
+    Ea, _, pa, Wa = O.kspace_nfft_ad(pos, q, L, **kw)
+    Ei, _, pi_, Wi = O.kspace_nfft(pos, q, L, **kw)
+    assert abs(Ea / Ei - 1) < 1e-13
+    assert np.abs(Wa - Wi).max() < 1e-13 * np.abs(Wi).max()
+    assert np.abs(pa - pi_).max() < 1e-12 * np.abs(pi_).max()
+
+
+def test_ad_forces_approach_direct_with_p_and_grid_shift_invariance():
+    """With the window widened the analytic-differentiation forces converge to
+    the direct reciprocal forces on the same cube (Eq. 41 summed exactly),
+    and like O2 they are exactly invariant under shifts by whole grid cells
+    (Eq. 18)."""
+    d = W.nacl()
+    pos, q, L = d["pos"], d["q"], d["L"]
+    r1 = O.kspace_direct(pos, q, L, 0.35, 8, sphere=False)
+    eF = []
+    for p in [4, 8, 12]:
+        _, F, _, _ = O.kspace_nfft_ad(pos, q, L, 0.35, 32, p, 8)
+        eF.append(np.sqrt(((F - r1[1]) ** 2).sum() / (r1[1] ** 2).sum()))
+    assert eF[1] < eF[0] / 10 and eF[2] < eF[1] / 10
+    # (the ik forces reach 4.1e-6 here; the window derivative costs a factor
+    # of 1.2-2 at every p)
+    assert eF[2] < 1e-5
+    _, F0, _, _ = O.kspace_nfft_ad(pos, q, L, 0.35, 32, 6, 8)
+    h = np.asarray(L) / 32
+    _, F1, _, _ = O.kspace_nfft_ad(pos + np.array([2, -3, 5]) * h, q, L, 0.35, 32, 6, 8)
+    assert np.abs(F1 - F0).max() < 1e-10 * np.abs(F0).max()
+
+
 def test_real_space_subset_matches_full():
     """The sampled evaluation path returns the same per-particle values as
     the full pair loop."""
