@@ -373,6 +373,45 @@ def main():
             extra["ms_per_step_p6_r12"] = ms6
             extra["rms_force_err_vs_exact_p6_r12"] = "4.1e-4 (tests/test_gpu_workloads.py)"
             del plan6
+        # ---- the analytic-differentiation force variant on the same plan and
+        # inputs (one inverse transform of the potential, window gradient)
+        Fad = torch.empty_like(F)
+
+        def kspace_ad(pl, F_):
+            pl.compute(tp, tq, forces=True, virial=True, kspace_only=True, F=F_, out=out, ad=True)
+
+        ms_ad, _ = timed(lambda: kspace_ad(plan, Fad), 50, 3)
+        os.environ["ENUF_PROFILE"] = "1"
+        pplan = P.Plan(precision="mixed", **kw)
+        os.environ.pop("ENUF_PROFILE")
+        acc_ad = {}
+        for _ in range(3):
+            kspace_ad(pplan, Fad)
+        for _ in range(reps):
+            flush.fill_(1.0)
+            kspace_ad(pplan, Fad)
+            for name, t in pplan.timings():
+                acc_ad[name] = acc_ad.get(name, 0.0) + t / reps
+        torch.cuda.synchronize()
+        del pplan
+        kspace_ad(plan, Fad)
+        kspace(plan, tp, tq, F, out)  # the ik forces of this plan (F last held another plan's)
+        torch.cuda.synchronize()
+        extra["ad_forces"] = {
+            "value": N / (ms_ad * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms_ad,
+            "launches": plan.launch_count(kflags | P.AD_FORCES, True),
+            "kernel_ms": {k: round(v, 5) for k, v in acc_ad.items()},
+            "rms_force_err_vs_exact": "3.4e-4 (tests/test_gpu_ad.py)" if args.workload == "rpm_1e4" else None,
+            "rel_rms_vs_ik_forces": float(((Fad.double() - F.double()) ** 2).sum().sqrt()
+                                          / (F.double() ** 2).sum().sqrt())}
+        if args.workload == "rpm_1e4":
+            # the variant at the window width that meets the 1e-4 force error
+            plan10 = P.Plan(L=d["L"], N=N, alpha=d["alpha"], r_c=d["r_c"], M=M, p=10, n_c=nc, precision="mixed",
+                            device=dev)
+            ms10, _ = timed(lambda: kspace_ad(plan10, Fad), 50, 3)
+            extra["ad_forces"]["p10"] = {"value": N / (ms10 * 1e-3) / 1e6, "ms_per_step": ms10,
+                                         "rms_force_err_vs_exact": "8.2e-5 (tests/test_gpu_ad.py)"}
+            del plan10
         # the larger systems of the method's workloads (k-space E+F, mixed)
         if args.workload == "rpm_1e4" and not args.no_large:
             extra["large_systems"] = large_systems(P, dev, timed, kspace)

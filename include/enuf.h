@@ -54,6 +54,13 @@ extern "C" {
 #define ENUF_WANT_PHI 2          /* fill phi_i = dE/dq_i (a 4th inverse transform)    */
 #define ENUF_REMOVE_NET_FORCE 4  /* subtract (1/N) sum_i F_i from every force         */
 #define ENUF_KSPACE_ONLY 8       /* reciprocal part only (no real-space, self, bg)    */
+/* Reciprocal forces by analytic differentiation instead of the ik scheme of
+ * Eq. 41-42: one inverse transform of the potential (G S~ on the grid) and
+ * the window's gradient in the interpolation, F_i = -q_i grad phi~(r_i).  The
+ * forces are then the exact gradient of the approximated energy of Eq. 38
+ * (the ik forces are not), at one inverse transform instead of three; phi
+ * comes from the same grid.  Energy and virial are unchanged. */
+#define ENUF_AD_FORCES 16
 
 /* error codes */
 #define ENUF_OK 0

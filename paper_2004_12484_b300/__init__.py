@@ -29,6 +29,7 @@ WANT_VIRIAL = 1
 WANT_PHI = 2
 REMOVE_NET_FORCE = 4
 KSPACE_ONLY = 8
+AD_FORCES = 16
 NOUT = 16
 OUT = dict(E=0, E_real=1, E_recip=2, E_self=3, E_bg=4, Q=5, virial=6, status=15)
 
@@ -179,16 +180,17 @@ class Plan:
         return t
 
     @staticmethod
-    def flags(virial=True, phi=False, kspace_only=False, remove_net_force=False) -> int:
+    def flags(virial=True, phi=False, kspace_only=False, remove_net_force=False, ad=False) -> int:
         return ((WANT_VIRIAL if virial else 0) | (WANT_PHI if phi else 0) | (KSPACE_ONLY if kspace_only else 0)
-                | (REMOVE_NET_FORCE if remove_net_force else 0))
+                | (REMOVE_NET_FORCE if remove_net_force else 0) | (AD_FORCES if ad else 0))
 
     # ----------------------------------------------------------- calls
     def compute(self, pos, q, forces=True, phi=False, virial=True, kspace_only=False, remove_net_force=False,
-                F=None, phi_out=None, out=None):
+                F=None, phi_out=None, out=None, ad=False):
         """Asynchronous evaluation on the current stream.  Returns
         (out[16] float64, F (N,3) or None, phi (N,) or None), all on the
-        device."""
+        device.  ``ad=True`` takes the reciprocal forces by analytic
+        differentiation (one inverse transform, window gradient)."""
         torch = self.torch
         self._dev(pos, (self.N, 3), "pos")
         self._dev(q, (self.N,), "q")
@@ -199,16 +201,16 @@ class Plan:
         if out is None:
             out = torch.empty((NOUT,), dtype=torch.float64, device=self.device)
         self._sync_stream()
-        fl = self.flags(virial, phi, kspace_only, remove_net_force)
+        fl = self.flags(virial, phi, kspace_only, remove_net_force, ad)
         _check(lib().enuf_compute(self._h, _vp(pos.data_ptr()), _vp(q.data_ptr()),
                                   _vp(F.data_ptr() if forces else 0), _vp(phi_out.data_ptr() if phi else 0),
                                   _vp(out.data_ptr()), fl))
         return out, (F if forces else None), (phi_out if phi else None)
 
-    def energy_forces(self, pos, q, phi=False, kspace_only=False, remove_net_force=False):
+    def energy_forces(self, pos, q, phi=False, kspace_only=False, remove_net_force=False, ad=False):
         """Synchronous: returns (parts dict of floats, F tensor, virial 3x3
         numpy array, phi tensor or None)."""
-        out, F, ph = self.compute(pos, q, True, phi, True, kspace_only, remove_net_force)
+        out, F, ph = self.compute(pos, q, True, phi, True, kspace_only, remove_net_force, ad=ad)
         h = out.cpu().numpy()
         st = int(h[OUT["status"]])
         if st & 1:
@@ -218,11 +220,11 @@ class Plan:
         parts = {k: float(h[i]) for k, i in OUT.items() if k not in ("virial", "status")}
         return parts, F, h[6:15].reshape(3, 3).copy(), ph
 
-    def energy_forces_host(self, pos_host, q_host, phi_host=None, F_host=None, kspace_only=False):
+    def energy_forces_host(self, pos_host, q_host, phi_host=None, F_host=None, kspace_only=False, ad=False):
         """End-to-end call with host (numpy or pinned torch CPU) buffers; the
         copies in and out are part of the call."""
         torch = self.torch
-        fl = self.flags(True, phi_host is not None, kspace_only)
+        fl = self.flags(True, phi_host is not None, kspace_only, ad=ad)
         E = ctypes.c_double()
         W = (ctypes.c_double * 9)()
 

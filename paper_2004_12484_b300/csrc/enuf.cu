@@ -425,6 +425,34 @@ int launch_gather_t(Launcher& L, enuf_plan* pl, int nf, R* F, R* phi)
                 r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), (R)pl->cnorm3, at<const R>(pl, y.fld), F, phi);
 }
 
+// Interpolation of the potential grid with the window gradient (forces by
+// analytic differentiation); 512 threads for the 16-cell tiles (the box of
+// one grid lets several CTAs share an SM), 256 for the smaller tiles.
+template <typename R, int P, int T>
+int launch_gather_ad_t(Launcher& L, enuf_plan* pl, R* F, R* phi)
+{
+    const Resolved& r = pl->r;
+    const Layout& y = pl->lay;
+    const R cn = (R)pl->cnorm3;
+    R fa[3];
+    for (int t = 0; t < 3; t++) fa[t] = (R)(pl->cnorm3 * r.prm.M / r.prm.L[t] * 2.0 / pl->b);
+    if (r.gather_direct) {
+        constexpr int G = GroupOf<P>::G;
+        const int N = (int)r.prm.N;
+        const dim3 grid((unsigned)(((size_t)N * G + 255) / 256));
+        return L.go("gather", k_gather_direct_ad<R, P, T>, grid, dim3(256), 0, N,
+                    at<const typename Rec<R>::T>(pl, y.rec), at<const uint32_t>(pl, y.tile_of),
+                    at<const uint32_t>(pl, y.perm), r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), cn, fa[0], fa[1], fa[2],
+                    at<const R>(pl, y.fld), F, phi);
+    }
+    constexpr int NTH = T == 16 ? 512 : 256;
+    const size_t smem = ((size_t)Box<P, T>::CELLS + (NTH / 32) * P * P) * sizeof(R) +
+                        (size_t)kWorkCap * (sizeof(typename Rec<R>::T) + 4);
+    return L.go("gather", k_gather_ad<R, P, T, NTH>, dim3(r.max_work), dim3(NTH), smem, at<const int4>(pl, y.work),
+                at<const int>(pl, y.nwork), at<const typename Rec<R>::T>(pl, y.rec), at<const uint32_t>(pl, y.perm),
+                r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), cn, fa[0], fa[1], fa[2], at<const R>(pl, y.fld), F, phi);
+}
+
 #define DISPATCH_P(T_, FN, ...)                                           \
     switch (pl->r.prm.p) {                                                \
     case 2: return FN<R, 2, T_>(__VA_ARGS__);                             \
@@ -448,6 +476,13 @@ template <typename R> int launch_gather(Launcher& L, enuf_plan* pl, int nf, R* F
     if (pl->r.T == 16) { DISPATCH_P(16, launch_gather_t, L, pl, nf, F, phi) }
     if (pl->r.T == 4) { DISPATCH_P(4, launch_gather_t, L, pl, nf, F, phi) }
     DISPATCH_P(8, launch_gather_t, L, pl, nf, F, phi)
+}
+
+template <typename R> int launch_gather_ad(Launcher& L, enuf_plan* pl, R* F, R* phi)
+{
+    if (pl->r.T == 16) { DISPATCH_P(16, launch_gather_ad_t, L, pl, F, phi) }
+    if (pl->r.T == 4) { DISPATCH_P(4, launch_gather_ad_t, L, pl, F, phi) }
+    DISPATCH_P(8, launch_gather_ad_t, L, pl, F, phi)
 }
 
 template <typename R, int M>
@@ -493,6 +528,9 @@ int launch_fft_chain_m(Launcher& L, enuf_plan* pl, int nf)
         const int NT = M >= 4 ? M / 4 : 1;  // threads per pencil in k_fz (radix-4 passes)
         if (nf == 0)
             LCHK(L.go("fft_z_kspace", k_fz<R, M, 0>, g, dim3(Wc * NT), smem, at<const V>(pl, y.C2), at<V>(pl, y.C3), r.gz,
+                      W, kt, at<double>(pl, y.kpart)));
+        else if (nf == 1)
+            LCHK(L.go("fft_z_kspace", k_fz<R, M, 1>, g, dim3(Wc * NT), smem, at<const V>(pl, y.C2), at<V>(pl, y.C3), r.gz,
                       W, kt, at<double>(pl, y.kpart)));
         else if (nf == 3)
             LCHK(L.go("fft_z_kspace", k_fz<R, M, 3>, g, dim3(Wc * NT), smem, at<const V>(pl, y.C2), at<V>(pl, y.C3), r.gz,
@@ -592,7 +630,9 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
     const int nblkN = (N + 255) / 256;
     const bool want_phi = (flags & ENUF_WANT_PHI) && phi;
     const bool konly = flags & ENUF_KSPACE_ONLY;
-    const int nf = want_phi ? 4 : (F ? 3 : 0);
+    // forces by analytic differentiation: the potential's grid alone
+    const bool ad = (flags & ENUF_AD_FORCES) && (F || want_phi);
+    const int nf = ad ? 1 : (want_phi ? 4 : (F ? 3 : 0));
     using RecT = typename Rec<R>::T;
 
     // the status word, the bin counts and the block counters are kept
@@ -714,7 +754,8 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
         CK(cudaEventRecord(pl->ev_join, pl->aux_stream));
     }
     // (a7) interpolation
-    if (nf > 0) LCHK(launch_gather<R>(L, pl, nf, F, want_phi ? phi : (R*)nullptr));
+    if (ad) LCHK(launch_gather_ad<R>(L, pl, F, want_phi ? phi : (R*)nullptr));
+    else if (nf > 0) LCHK(launch_gather<R>(L, pl, nf, F, want_phi ? phi : (R*)nullptr));
     // (a9) assembly
     fp.nr = nr;
     if (real_side) CK(cudaStreamWaitEvent(L.st, pl->ev_join, 0));
@@ -755,8 +796,8 @@ int prepare_attrs(enuf_plan* pl)
 {
     if (pl->attrs_done) return ENUF_OK;
     // walk every variant once in attribute-only mode (no launches)
-    int flags[3] = {ENUF_WANT_PHI, 0, ENUF_REMOVE_NET_FORCE};
-    for (int k = 0; k < 3; k++) {
+    int flags[4] = {ENUF_WANT_PHI, 0, ENUF_REMOVE_NET_FORCE, ENUF_AD_FORCES | ENUF_WANT_PHI};
+    for (int k = 0; k < 4; k++) {
         void* dummy = (void*)pl->ws;
         int rc = run_sequence(pl, pl->stream, true, dummy, dummy, dummy, dummy, nullptr, flags[k]);
         if (rc != ENUF_OK) return rc;
@@ -861,7 +902,7 @@ int compute_impl(enuf_plan* pl, const void* pos, const void* q, void* F, void* p
     if (!pl->ws) return fail(ENUF_EINVAL, "plan has no workspace");
     if (!pos || !q) return fail(ENUF_EINVAL, "pos and q are required");
     if ((flags & ENUF_WANT_PHI) && !phi) return fail(ENUF_EINVAL, "ENUF_WANT_PHI needs a phi buffer");
-    if (flags & ~(ENUF_WANT_VIRIAL | ENUF_WANT_PHI | ENUF_REMOVE_NET_FORCE | ENUF_KSPACE_ONLY))
+    if (flags & ~(ENUF_WANT_VIRIAL | ENUF_WANT_PHI | ENUF_REMOVE_NET_FORCE | ENUF_KSPACE_ONLY | ENUF_AD_FORCES))
         return fail(ENUF_EINVAL, "unknown flag bits");
     if (!(flags & ENUF_WANT_PHI)) phi = nullptr;
     if (pl->profile) {
@@ -1147,7 +1188,7 @@ int enuf_energy_forces_host(enuf_plan* pl, const void* pos_host, const void* q_h
     void* phi = (phi_host && (flags & ENUF_WANT_PHI)) ? (void*)(pl->ws + y.s_phi) : nullptr;
     if ((flags & ENUF_WANT_PHI) && !phi) flags &= ~ENUF_WANT_PHI;
     double* dout = at<double>(pl, y.out);
-    if (flags & ~(ENUF_WANT_VIRIAL | ENUF_WANT_PHI | ENUF_REMOVE_NET_FORCE | ENUF_KSPACE_ONLY))
+    if (flags & ~(ENUF_WANT_VIRIAL | ENUF_WANT_PHI | ENUF_REMOVE_NET_FORCE | ENUF_KSPACE_ONLY | ENUF_AD_FORCES))
         return fail(ENUF_EINVAL, "unknown flag bits");
     if (pl->use_graph && !pl->profile && pl->hout && host_pinned(pos_host) && host_pinned(q_host) &&
         host_pinned(F_host) && host_pinned(phi ? phi_host : nullptr)) {

@@ -337,7 +337,9 @@ template <typename R> struct KTables {
 // grid: ceil(P / W) blocks, W * NT(M) threads (a multiple of 32).
 // Writes NF inverse-z-transformed field spectra C3[f][z][kb][kx] and the
 // block's energy/virial partials part[blockIdx][0..6] =
-// (E, Wxx, Wyy, Wzz, Wxy, Wxz, Wyz).  NF = 0 gives the energy only.
+// (E, Wxx, Wyy, Wzz, Wxy, Wxz, Wyz).  NF = 0 gives the energy only, NF = 1
+// the potential's spectrum alone, NF = 3 the field -i k (ik forces), NF = 4
+// the field and the potential.
 // Shared memory: max(NF, 1) buffers of W pencils (the first also holds the
 // forward transform), the twiddles, the reciprocal tables, the reduction.
 template <typename R, int M, int NF>
@@ -405,7 +407,10 @@ __global__ void __launch_bounds__(512) k_fz(const typename Cpx<R>::T* __restrict
                 val = V{f * gh.x, f * gh.y};
             }
         }
-        if (NF > 0) {
+        if (NF == 1) {
+            // the potential alone (forces by analytic differentiation)
+            X[w * LD + pidx(z)] = val;
+        } else if (NF > 0) {
             // -i k_t val for the three field components, val for the potential
             X[w * LD + pidx(z)] = V{kxv * val.y, -kxv * val.x};
             if (NF > 1) X[FS + w * LD + pidx(z)] = V{kyv * val.y, -kyv * val.x};

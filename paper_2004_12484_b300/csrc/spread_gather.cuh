@@ -411,6 +411,116 @@ __global__ void __launch_bounds__(NTH) k_gather(const int4* __restrict__ work, c
     }
 }
 
+// Interpolation for the analytic-differentiation forces: one real potential
+// grid A (plane of M^3) and, per particle, the window sum of A together with
+// the three sums weighted by the window's derivative, d phi/du = -(2u/b) phi
+// (u = particle minus grid point, in grid units).  With
+//   s = sum_l w_l A_l,   g_t = sum_l u_t w_l A_l,
+// the potential is phi_i = cnorm3 s and the force F_{i,t} = q_i fa_t g_t,
+// fa_t = cnorm3 (M / L_t) (2 / b): the gradient of the approximated energy
+// through the window values.  The staged box holds the one grid, so the
+// tile's staging is a third of the three-field interpolation's and every
+// window point costs one shared-memory load.
+template <typename R, int P, int T, int NTH>
+__global__ void __launch_bounds__(NTH) k_gather_ad(const int4* __restrict__ work, const int* __restrict__ nwork,
+                                                   const typename Rec<R>::T* __restrict__ rec,
+                                                   const uint32_t* __restrict__ perm, int M, int lnbx, int lnby,
+                                                   WinC<R> wc, R cnorm3, R fa0, R fa1, R fa2,
+                                                   const R* __restrict__ fld, R* __restrict__ F, R* __restrict__ phi)
+{
+    using B = Box<P, T>;
+    constexpr int PT = B::PT, BX = B::BX, C = B::CELLS, m = P / 2, G = GroupOf<P>::G;
+    extern __shared__ __align__(32) unsigned char smraw_sg[];
+    R* s = reinterpret_cast<R*>(smraw_sg);
+    if ((int)blockIdx.x >= *nwork) return;
+    const int4 w = work[blockIdx.x];
+    const int tile = w.x;
+    const int tx = tile & ((1 << lnbx) - 1), ty = (tile >> lnbx) & ((1 << lnby) - 1), tz = tile >> (lnbx + lnby);
+    const int ox = tx * T - B::XA, oy = ty * T - (m - 1), oz = tz * T - (m - 1);
+    const int mask = M - 1;
+    constexpr int EV = 16 / sizeof(R);
+    constexpr int NV = BX / EV;
+    for (int i = threadIdx.x; i < NV * PT * PT; i += blockDim.x) {
+        const int vx = i % NV, ly = (i / NV) % PT, lz = i / (NV * PT);
+        const size_t gi = ((size_t)((oz + lz) & mask) * M + ((oy + ly) & mask)) * M + ((ox + EV * vx) & mask);
+        *reinterpret_cast<float4*>(s + (lz * PT + ly) * BX + EV * vx) = __ldg(reinterpret_cast<const float4*>(fld + gi));
+    }
+    using RecT = typename Rec<R>::T;
+    RecT* srec = reinterpret_cast<RecT*>(s + C + (blockDim.x >> 5) * (P * P));
+    uint32_t* sperm = reinterpret_cast<uint32_t*>(srec + (w.z - w.y));
+    for (int i = threadIdx.x; i < w.z - w.y; i += blockDim.x) {
+        srec[i] = rec[w.y + i];
+        sperm[i] = perm[w.y + i];
+    }
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int g = lane / G, a = lane % G;
+    R* wyz = s + C + warp * (P * P);
+    for (int j = w.y + warp; j < w.z; j += nwarp) {
+        const RecT r = srec[j - w.y];
+        int ix, iy, iz;
+        R dx, dy, dz;
+        split_offset<R, T>(r.x, ix, dx);
+        split_offset<R, T>(r.y, iy, dy);
+        split_offset<R, T>(r.z, iz, dz);
+        const R ux = dx + (R)(m - 1 - (a % P));
+        const R wx = win_exp(ux * ux, wc);
+        const R* base = s + (iz * PT + iy) * BX + ix + B::XOFF + a;
+        // acc = (s, g_x, g_y, g_z) partials of this lane
+        R acc[4];
+        if constexpr (P == 8) {
+            // lane (g, a): rows y = g and g + 4, all eight z; the z sums
+            // with weights wz and u_z wz, then the y weights
+            R wz[8];
+            window_weights<R, 8>(dz, wc, wz);
+            const R uya = dy + (R)(3 - a);
+            const R wya = win_exp(uya * uya, wc);
+            const R wy0 = __shfl_sync(0xffffffffu, wya, g), wy1 = __shfl_sync(0xffffffffu, wya, g + 4);
+            const R uy0 = dy + (R)(3 - g), uy1 = dy - (R)(1 + g);
+            R s0 = R(0), d0 = R(0), s1 = R(0), d1 = R(0);
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+                const R wzu = wz[c] * (dz + (R)(3 - c));
+                const R v0 = base[(c * PT + g) * BX], v1 = base[(c * PT + g + 4) * BX];
+                s0 += wz[c] * v0;
+                d0 += wzu * v0;
+                s1 += wz[c] * v1;
+                d1 += wzu * v1;
+            }
+            acc[0] = wx * (wy0 * s0 + wy1 * s1);
+            acc[1] = ux * acc[0];
+            acc[2] = wx * (wy0 * uy0 * s0 + wy1 * uy1 * s1);
+            acc[3] = wx * (wy0 * d0 + wy1 * d1);
+        } else {
+            R sa = R(0), sy = R(0), sz = R(0);
+            visit_window<R, P>(dy, dz, wx, wc, wyz, lane, [&](int, int b, int c, R ww) {
+                if (a < P) {
+                    const R t = ww * base[(c * PT + b) * BX];
+                    sa += t;
+                    sy += t * (dy + (R)(m - 1 - b));
+                    sz += t * (dz + (R)(m - 1 - c));
+                }
+            });
+            acc[0] = sa;
+            acc[1] = a < P ? ux * sa : R(0);
+            acc[2] = sy;
+            acc[3] = sz;
+        }
+        const R tot = warp_sum4(acc, lane);
+        if ((lane & 7) == 0) {
+            const int f = lane >> 3;
+            const uint32_t oi = sperm[j - w.y];
+            if (f == 0) {
+                if (phi) phi[oi] = cnorm3 * tot;
+            } else if (F) {
+                F[3 * (size_t)oi + f - 1] = r.w * (f == 1 ? fa0 : (f == 2 ? fa1 : fa2)) * tot;
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // Interpolation without staging, for grids whose field planes stay resident
 // in L2 (the whole set is at most a few tens of MB): one group of G lanes per
 // particle in sorted order, reading each window row of p consecutive cells
@@ -478,6 +588,80 @@ __global__ void __launch_bounds__(256) k_gather_direct(int N, const typename Rec
             F[3 * (size_t)oi + 2] = qc * acc[2];
         }
         if (NF == 4 && phi) phi[oi] = cnorm3 * acc[NF - 1];
+    }
+}
+
+// The analytic-differentiation interpolation without staging (same
+// selection rule as k_gather_direct): one group of G lanes per particle,
+// lane a < P the x offset a; the row sums over y carry the weights wy and
+// u_y wy, the plane sums over z the weights wz and u_z wz.
+template <typename R, int P, int T>
+__global__ void __launch_bounds__(256) k_gather_direct_ad(int N, const typename Rec<R>::T* __restrict__ rec,
+                                                          const uint32_t* __restrict__ tile_of,
+                                                          const uint32_t* __restrict__ perm, int M, int lnbx,
+                                                          int lnby, WinC<R> wc, R cnorm3, R fa0, R fa1, R fa2,
+                                                          const R* __restrict__ fld, R* __restrict__ F,
+                                                          R* __restrict__ phi)
+{
+    constexpr int m = P / 2, G = GroupOf<P>::G;
+    const int lane = threadIdx.x % G;
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+    if (j >= N) return;  // whole groups leave together
+    const unsigned gmask = (G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G)));
+    const int mask = M - 1;
+    const typename Rec<R>::T r = rec[j];
+    const int tile = (int)tile_of[j];
+    const int tx = tile & ((1 << lnbx) - 1), ty = (tile >> lnbx) & ((1 << lnby) - 1), tz = tile >> (lnbx + lnby);
+    int ix, iy, iz;
+    R dx, dy, dz;
+    split_offset<R, T>(r.x, ix, dx);
+    split_offset<R, T>(r.y, iy, dy);
+    split_offset<R, T>(r.z, iz, dz);
+    R wy[P], wz[P];
+    window_weights<R, P>(dy, wc, wy);
+    window_weights<R, P>(dz, wc, wz);
+    R acc[4] = {R(0), R(0), R(0), R(0)};
+    if (lane < P) {
+        const R ux = dx + (R)(m - 1 - lane);
+        const R wx = win_exp(ux * ux, wc);
+        const int gx = (tx * T + ix - (m - 1) + lane) & mask;
+        const int y0 = ty * T + iy - (m - 1), z0 = tz * T + iz - (m - 1);
+        int yo[P];
+#pragma unroll
+        for (int b = 0; b < P; b++) yo[b] = ((y0 + b) & mask) * M;
+        R sa = R(0), sy = R(0), sz = R(0);
+#pragma unroll
+        for (int c = 0; c < P; c++) {
+            const R* zb = fld + (((z0 + c) & mask) * M * M + gx);
+            R rs = R(0), ry = R(0);
+#pragma unroll
+            for (int b = 0; b < P; b++) {
+                const R v = __ldg(zb + yo[b]);
+                rs += wy[b] * v;
+                ry += wy[b] * (dy + (R)(m - 1 - b)) * v;
+            }
+            sa += wz[c] * rs;
+            sy += wz[c] * ry;
+            sz += wz[c] * (dz + (R)(m - 1 - c)) * rs;
+        }
+        acc[0] = wx * sa;
+        acc[1] = ux * acc[0];
+        acc[2] = wx * sy;
+        acc[3] = wx * sz;
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+#pragma unroll
+        for (int f = 0; f < 4; f++) acc[f] += __shfl_xor_sync(gmask, acc[f], o, G);
+    }
+    if (lane == 0) {
+        const uint32_t oi = perm[j];
+        if (F) {
+            F[3 * (size_t)oi] = r.w * fa0 * acc[1];
+            F[3 * (size_t)oi + 1] = r.w * fa1 * acc[2];
+            F[3 * (size_t)oi + 2] = r.w * fa2 * acc[3];
+        }
+        if (phi) phi[oi] = cnorm3 * acc[0];
     }
 }
 
