@@ -319,6 +319,7 @@ struct enuf_plan {
     double* hout = nullptr;  // pinned host copy of the results (host-buffer entry point)
     bool use_graph = true;
     bool profile = false;
+    bool pdl = true;  // programmatic dependent launch along the chain (ENUF_NO_PDL=1 turns it off)
     bool attrs_done = false;
     std::vector<GraphEntry> graphs;
     unsigned long long stamp = 0;
@@ -348,6 +349,17 @@ template <typename R> WinC<R> winc(const enuf_plan* pl)
 }
 
 // ------------------------------------------------------------------ launching
+// Kernels that begin with pdl_wait() and may therefore be
+// launched with programmatic stream serialisation.
+inline bool pdl_kernel(const char* name)
+{
+    static const char* const names[] = {"bin_keys", "real_bin_keys", "scatter", "real_scatter", "spread",
+                                        "fft_xy", "fft_z_kspace", "ifft_yx", "gather", "finalize"};
+    for (const char* n : names)
+        if (std::strcmp(n, name) == 0) return true;
+    return false;
+}
+
 struct Launcher {
     enuf_plan* pl;
     cudaStream_t st;
@@ -366,8 +378,26 @@ struct Launcher {
             CK(cudaEventRecordWithFlags(pl->tevents[pl->tnames.size()], st, cudaEventRecordExternal));
             pl->tnames.push_back(name);
         }
-        k<<<grid, block, smem, st>>>(args...);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e;
+        if (pl->pdl && pdl_kernel(name)) {
+            // may start while the previous kernel on the stream finishes; the
+            // kernel waits for it (pdl_wait) before using its data
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = grid;
+            cfg.blockDim = block;
+            cfg.dynamicSmemBytes = smem;
+            cfg.stream = st;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            at[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            e = cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+            if (e == cudaSuccess) e = cudaGetLastError();
+        } else {
+            k<<<grid, block, smem, st>>>(args...);
+            e = cudaGetLastError();
+        }
         if (e != cudaSuccess) return fail(ENUF_ECUDA, std::string("launch ") + name + ": " + cudaGetErrorString(e));
         count++;
         return ENUF_OK;
@@ -1070,6 +1100,8 @@ int enuf_plan_create(const enuf_params* params, void* cuda_stream, int allocate,
     pl->use_graph = !(ev && ev[0] == '1');
     ev = std::getenv("ENUF_PROFILE");
     pl->profile = ev && ev[0] == '1';
+    ev = std::getenv("ENUF_NO_PDL");
+    pl->pdl = !(ev && ev[0] == '1');
     if (pl->profile) {
         pl->tevents.resize(48);
         for (auto& x : pl->tevents) cudaEventCreate(&x);

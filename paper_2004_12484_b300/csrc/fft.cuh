@@ -254,6 +254,7 @@ __global__ void __launch_bounds__(1024) k_fxy(R* __restrict__ grid, typename Cpx
     V* plane = rowbuf + RB * RS;  // [Kx (rounded to CB)][LD]
     V* sW = plane + ((Kx + CB - 1) / CB) * CB * LD;
     stage_twiddles(sW, Wg, M);
+    pdl_wait();
     const int z = blockIdx.x;
     V* gin = reinterpret_cast<V*>(grid + (size_t)z * M * M);
     for (int y0 = 0; y0 < M; y0 += RB) {
@@ -366,6 +367,7 @@ __global__ void __launch_bounds__(512) k_fz(const typename Cpx<R>::T* __restrict
     const R* tk = stab;
     const R* te = stab + 3 * Kb;
     const R* td = stab + 6 * Kb;
+    pdl_wait();
     const int p0 = blockIdx.x * Wc;
     for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
         const int z = (int)g.fW.div(i), w = i - z * Wc, p = p0 + w;
@@ -491,6 +493,7 @@ __global__ void __launch_bounds__(IyxBounds<R, M>::T, IyxBounds<R, M>::B) k_iyx(
     const int KxR = ((Kx + CB - 1) / CB) * CB;
     V* sW = plane + KxR * LD;
     stage_twiddles(sW, Wg, M);
+    pdl_wait();
     const int z = blockIdx.x, f = blockIdx.y;
     const V* src = C3 + ((size_t)f * M + z) * P;
     for (int i = threadIdx.x; i < KxR * M; i += blockDim.x) {

@@ -186,6 +186,7 @@ __global__ void __launch_bounds__(512) k_finalize(const double* __restrict__ qpa
 {
     __shared__ double s[16];
     __shared__ bool s_last;
+    pdl_wait();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nb = gridDim.x, b = blockIdx.x;
     auto chunk = [&](int n, int& lo, int& hi) {

@@ -242,6 +242,7 @@ __global__ void __launch_bounds__(256) k_bin_keys(int N, const R* __restrict__ p
     __shared__ uint32_t s_scan[2 * 256 * kScanPer];
     __shared__ uint32_t s_sum[3][32];
     __shared__ bool s_last;
+    pdl_wait();
     uint32_t* __restrict__ count = sa.count;
     const int cs = sa.cs;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -437,6 +438,7 @@ __global__ void __launch_bounds__(256) k_scatter(int N, const uint32_t* __restri
                                                  const uint32_t* __restrict__ item2, int cap2,
                                                  int4* __restrict__ work2, int max_work2)
 {
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const uint32_t b = key[i];

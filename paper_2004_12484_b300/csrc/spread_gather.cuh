@@ -218,6 +218,7 @@ __global__ void __launch_bounds__(32) k_spread(const int4* __restrict__ work, co
     R* acc = reinterpret_cast<R*>(smraw_sg);
     R* wyz = acc + B::CELLS;  // P*P products (window widths without a register path)
     using RecT = typename Rec<R>::T;
+    pdl_wait();
     if ((int)blockIdx.x >= *nwork) return;  // uniform for the whole CTA
     const int4 w = work[blockIdx.x];
     const int lane = threadIdx.x;
@@ -346,6 +347,7 @@ __global__ void __launch_bounds__(NTH) k_gather(const int4* __restrict__ work, c
     constexpr int PT = B::PT, BX = B::BX, C = B::CELLS, m = P / 2, G = GroupOf<P>::G;
     extern __shared__ __align__(32) unsigned char smraw_sg[];
     R* s = reinterpret_cast<R*>(smraw_sg);
+    pdl_wait();
     if ((int)blockIdx.x >= *nwork) return;
     const int4 w = work[blockIdx.x];
     const int tile = w.x;
@@ -432,6 +434,7 @@ __global__ void __launch_bounds__(NTH) k_gather_ad(const int4* __restrict__ work
     constexpr int PT = B::PT, BX = B::BX, C = B::CELLS, m = P / 2, G = GroupOf<P>::G;
     extern __shared__ __align__(32) unsigned char smraw_sg[];
     R* s = reinterpret_cast<R*>(smraw_sg);
+    pdl_wait();
     if ((int)blockIdx.x >= *nwork) return;
     const int4 w = work[blockIdx.x];
     const int tile = w.x;
@@ -534,6 +537,7 @@ __global__ void __launch_bounds__(256) k_gather_direct(int N, const typename Rec
                                                        R* __restrict__ F, R* __restrict__ phi)
 {
     constexpr int m = P / 2, G = GroupOf<P>::G;
+    pdl_wait();
     const int lane = threadIdx.x % G;
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) / G;
     if (j >= N) return;  // whole groups leave together
@@ -604,6 +608,7 @@ __global__ void __launch_bounds__(256) k_gather_direct_ad(int N, const typename 
                                                           R* __restrict__ phi)
 {
     constexpr int m = P / 2, G = GroupOf<P>::G;
+    pdl_wait();
     const int lane = threadIdx.x % G;
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) / G;
     if (j >= N) return;  // whole groups leave together
