@@ -67,6 +67,10 @@ struct Resolved {
     size_t rsz;    // sizeof(real)
     int nc, Kx, Kb, P;
     int T, nbt[3], ntiles, max_work;  // tiles of T^3 cells, interpolation work items
+    // interpolation work units: z-halves of the 16-cell tiles (zhalf), the
+    // sub-tile bins per unit (ggroup) and particles per work item (gcap)
+    bool zhalf;
+    int ggroup, gcap;
     int S, lr, nbins, max_work2;      // sub-tiles of S^3 (the sort's bins), lr = log2(T/S), spreading items
     bool cells;    // linked cells (else all pairs)
     int ncell[3], nrbins;
@@ -126,9 +130,14 @@ int resolve(const enuf_params* in, Resolved& r)
     if (box_bytes(r.T) > (size_t)kMaxSmem) return fail(ENUF_EUNSUPPORTED, "window too wide for the tile box");
     for (int t = 0; t < 3; t++) r.nbt[t] = p.M / r.T;
     r.ntiles = r.nbt[0] * r.nbt[1] * r.nbt[2];
-    r.max_work = r.ntiles + (int)(p.N / kWorkCap) + 1;
     r.S = std::min(r.T, 8);
     r.lr = r.T / r.S == 2 ? 1 : 0;
+    // 16-cell tiles interpolate in z-halves (sub-tiles 0-3 and 4-7 of a tile,
+    // each a contiguous particle range): two CTAs share an SM
+    r.zhalf = r.lr == 1 && !std::getenv("ENUF_GATHER_FULL_TILE");
+    r.ggroup = r.lr ? (r.zhalf ? 4 : 8) : 1;
+    r.gcap = r.zhalf ? kWorkCap / 2 : kWorkCap;
+    r.max_work = (r.zhalf ? 2 : 1) * r.ntiles + (int)(p.N / r.gcap) + 1;
     r.nbins = r.ntiles << (3 * r.lr);
     r.max_work2 = (int)std::min<int64_t>(r.nbins, p.N) + (int)(p.N / kSpreadCap) + 1;
     // linked cells of edge >= r_c, at least 3 per dimension
@@ -441,11 +450,30 @@ int launch_gather_t(Launcher& L, enuf_plan* pl, int nf, R* F, R* phi)
                     at<const uint32_t>(pl, y.perm), r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), (R)pl->cnorm3,
                     at<const R>(pl, y.fld), F, phi);
     }
-    // 1024 threads for the large 16-cell tiles (one CTA per SM holds the
-    // box), 256 for the smaller tiles; each warp keeps P*P weight products
+    using RecT = typename Rec<R>::T;
+    if constexpr (T == 16) {
+        if (r.zhalf) {
+            // z-halves of the tiles, 512 threads: two CTAs (three-field boxes
+            // of 99 KB) share an SM
+            constexpr int NTH = 512, ZS = 8;
+            const size_t smem = ((size_t)nf * Box<P, T, ZS>::CELLS + (NTH / 32) * WyzTable<P>::N) * sizeof(R) +
+                                (size_t)r.gcap * (sizeof(RecT) + 4);
+            if (nf == 4)
+                return L.go("gather", k_gather<R, P, T, 4, NTH, ZS>, dim3(r.max_work), dim3(NTH), smem,
+                            at<const int4>(pl, y.work), at<const int>(pl, y.nwork), at<const RecT>(pl, y.rec),
+                            at<const uint32_t>(pl, y.perm), r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), (R)pl->cnorm3,
+                            at<const R>(pl, y.fld), F, phi);
+            return L.go("gather", k_gather<R, P, T, 3, NTH, ZS>, dim3(r.max_work), dim3(NTH), smem,
+                        at<const int4>(pl, y.work), at<const int>(pl, y.nwork), at<const RecT>(pl, y.rec),
+                        at<const uint32_t>(pl, y.perm), r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), (R)pl->cnorm3,
+                        at<const R>(pl, y.fld), F, phi);
+        }
+    }
+    // 1024 threads for whole 16-cell tiles (one CTA per SM holds the box),
+    // 256 for the smaller tiles
     constexpr int NTH = T == 16 ? 1024 : 256;
-    const size_t smem = ((size_t)nf * Box<P, T>::CELLS + (NTH / 32) * P * P) * sizeof(R) +
-                        (size_t)kWorkCap * (sizeof(typename Rec<R>::T) + 4);
+    const size_t smem = ((size_t)nf * Box<P, T>::CELLS + (NTH / 32) * WyzTable<P>::N) * sizeof(R) +
+                        (size_t)r.gcap * (sizeof(RecT) + 4);
     if (nf == 4)
         return L.go("gather", k_gather<R, P, T, 4, NTH>, dim3(r.max_work), dim3(NTH), smem, at<const int4>(pl, y.work),
                     at<const int>(pl, y.nwork), at<const typename Rec<R>::T>(pl, y.rec), at<const uint32_t>(pl, y.perm),
@@ -475,11 +503,23 @@ int launch_gather_ad_t(Launcher& L, enuf_plan* pl, R* F, R* phi)
                     at<const uint32_t>(pl, y.perm), r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), cn, fa[0], fa[1], fa[2],
                     at<const R>(pl, y.fld), F, phi);
     }
+    using RecT = typename Rec<R>::T;
     constexpr int NTH = T == 16 ? 512 : 256;
-    const size_t smem = ((size_t)Box<P, T>::CELLS + (NTH / 32) * P * P) * sizeof(R) +
-                        (size_t)kWorkCap * (sizeof(typename Rec<R>::T) + 4);
+    if constexpr (T == 16) {
+        if (r.zhalf) {  // the sort's work units are z-halves of the tiles
+            constexpr int ZS = 8;
+            const size_t smem = ((size_t)Box<P, T, ZS>::CELLS + (NTH / 32) * WyzTable<P>::N) * sizeof(R) +
+                                (size_t)r.gcap * (sizeof(RecT) + 4);
+            return L.go("gather", k_gather_ad<R, P, T, NTH, ZS>, dim3(r.max_work), dim3(NTH), smem,
+                        at<const int4>(pl, y.work), at<const int>(pl, y.nwork), at<const RecT>(pl, y.rec),
+                        at<const uint32_t>(pl, y.perm), r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), cn, fa[0], fa[1],
+                        fa[2], at<const R>(pl, y.fld), F, phi);
+        }
+    }
+    const size_t smem = ((size_t)Box<P, T>::CELLS + (NTH / 32) * WyzTable<P>::N) * sizeof(R) +
+                        (size_t)r.gcap * (sizeof(RecT) + 4);
     return L.go("gather", k_gather_ad<R, P, T, NTH>, dim3(r.max_work), dim3(NTH), smem, at<const int4>(pl, y.work),
-                at<const int>(pl, y.nwork), at<const typename Rec<R>::T>(pl, y.rec), at<const uint32_t>(pl, y.perm),
+                at<const int>(pl, y.nwork), at<const RecT>(pl, y.rec), at<const uint32_t>(pl, y.perm),
                 r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), cn, fa[0], fa[1], fa[2], at<const R>(pl, y.fld), F, phi);
 }
 
@@ -616,9 +656,12 @@ int launch_chunked_scan(Launcher& L, enuf_plan* pl, const ScanArgs& sa, int grou
     uint32_t* cb = at<uint32_t>(pl, cbase_off);
     int* status = at<int>(pl, pl->lay.status);
     if (group == 8) LCHK(L.go("scan_sums", k_scan_sums<8>, dim3(nch), dim3(256), 0, sa, cs));
+    else if (group == 4) LCHK(L.go("scan_sums", k_scan_sums<4>, dim3(nch), dim3(256), 0, sa, cs));
     else LCHK(L.go("scan_sums", k_scan_sums<1>, dim3(nch), dim3(256), 0, sa, cs));
     LCHK(L.go("scan_bases", k_scan_bases, dim3(1), dim3(1024), 0, sa, nch, (const uint32_t*)cs, cb, status));
     if (group == 8) LCHK(L.go("scan_apply", k_scan_apply<8>, dim3(nch), dim3(256), 0, sa, (const uint32_t*)cb, status));
+    else if (group == 4)
+        LCHK(L.go("scan_apply", k_scan_apply<4>, dim3(nch), dim3(256), 0, sa, (const uint32_t*)cb, status));
     else LCHK(L.go("scan_apply", k_scan_apply<1>, dim3(nch), dim3(256), 0, sa, (const uint32_t*)cb, status));
     return ENUF_OK;
 }
@@ -734,13 +777,14 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
     {
         const bool big = r.nbins > kFusedScanMax;
         ScanArgs sa{r.nbins, at<uint32_t>(pl, y.counts), count_stride(r.nbins), at<uint32_t>(pl, y.offsets),
-                    kWorkCap, at<int4>(pl, y.work), at<int>(pl, y.nwork), r.max_work, kSpreadCap,
+                    r.gcap, at<int4>(pl, y.work), at<int>(pl, y.nwork), r.max_work, kSpreadCap,
                     at<uint32_t>(pl, y.item2), at<int>(pl, y.nwork2), r.max_work2,
                     big ? (unsigned*)nullptr : at<unsigned>(pl, y.status + 8)};
-        LCHK(L.go("bin_keys", r.lr ? k_bin_keys<R, 8> : k_bin_keys<R, 1>, dim3(nblkN), dim3(256), 0, N, pos, q, gg,
+        LCHK(L.go("bin_keys", r.ggroup == 8 ? k_bin_keys<R, 8> : (r.ggroup == 4 ? k_bin_keys<R, 4> : k_bin_keys<R, 1>),
+                  dim3(nblkN), dim3(256), 0, N, pos, q, gg,
                   at<uint32_t>(pl, y.key), at<uint32_t>(pl, y.rank), at<RecT>(pl, y.rec_tmp), sa, at<int>(pl, y.status),
                   at<double>(pl, y.qpart)));
-        if (big) LCHK(launch_chunked_scan(L, pl, sa, r.lr ? 8 : 1, y.csum_g, y.cbase_g));
+        if (big) LCHK(launch_chunked_scan(L, pl, sa, r.ggroup, y.csum_g, y.cbase_g));
     }
     LCHK(L.go("scatter", k_scatter<R>, dim3(nblkN), dim3(256), 0, N, at<const uint32_t>(pl, y.key),
               at<const uint32_t>(pl, y.rank), at<const uint32_t>(pl, y.offsets), at<const RecT>(pl, y.rec_tmp),

@@ -29,6 +29,13 @@ template <int P> struct GroupOf {
     static constexpr int G = P <= 2 ? 2 : (P <= 4 ? 4 : (P <= 8 ? 8 : 16));
 };
 
+// Entries of the per-warp table of y-z weight products that visit_window
+// uses for the window widths without a register path (p = 4 and 8 keep the
+// weights in registers).
+template <int P> struct WyzTable {
+    static constexpr int N = (P == 4 || P == 8) ? 0 : P * P;
+};
+
 // Per-plan window constants: 1/b, log2(e)/b and c[a] = exp(-a^2 / b), a < P.
 template <typename R> struct WinC {
     R inv_b;
@@ -171,16 +178,18 @@ __device__ __forceinline__ R warp_sum4(const R (&v)[4], int lane)
     return k;
 }
 
-// Shared-memory box of a tile: x from tile_x0 - XA to tile_x0 - XA + BX
+// Shared-memory box of a work unit of T x T x ZS cells (a tile, ZS = T, or
+// one z-half of it, ZS = T / 2): x from tile_x0 - XA to tile_x0 - XA + BX
 // (XA >= m - 1 and BX multiples of 4 so that rows start on 16-byte
-// boundaries in global memory), y and z from tile origin - (m - 1) over
-// PT = T + p - 1 cells.
-template <int P, int T> struct Box {
+// boundaries in global memory), y from the tile origin - (m - 1) over
+// PT = T + p - 1 cells, z from the unit's origin - (m - 1) over PZ = ZS + p - 1.
+template <int P, int T, int ZS = T> struct Box {
     static constexpr int m = P / 2;
     static constexpr int XA = (m - 1 + 3) / 4 * 4;
     static constexpr int BX = (XA + T + m + 3) / 4 * 4;
     static constexpr int PT = T + P - 1;
-    static constexpr int CELLS = BX * PT * PT;
+    static constexpr int PZ = ZS + P - 1;
+    static constexpr int CELLS = BX * PT * PZ;
     static constexpr int XOFF = XA - (m - 1);  // box x of window point 0 minus floor(u)
 };
 
@@ -335,30 +344,35 @@ __global__ void __launch_bounds__(32) k_spread(const int4* __restrict__ work, co
 // Interpolation of NF real fields (planes of M^3, plane stride M^3).  Fields
 // 0..2 give the force per unit charge (F_i = q_i * value), field 3 (when
 // NF = 4) the potential phi_i.  F is written (not accumulated) in the
-// caller's particle order through perm.
-template <typename R, int P, int T, int NF, int NTH>
+// caller's particle order through perm.  A work item covers a whole tile
+// (ZS = T, item x = tile) or one z-half of a tile (ZS = T / 2, item x =
+// 2 tile + half): the half box lets two CTAs share an SM, so one stages its
+// box while the other interpolates.
+template <typename R, int P, int T, int NF, int NTH, int ZS = T>
 __global__ void __launch_bounds__(NTH) k_gather(const int4* __restrict__ work, const int* __restrict__ nwork,
                                                 const typename Rec<R>::T* __restrict__ rec,
                                                 const uint32_t* __restrict__ perm, int M, int lnbx, int lnby,
                                                 WinC<R> wc, R cnorm3, const R* __restrict__ fld, R* __restrict__ F,
                                                 R* __restrict__ phi)
 {
-    using B = Box<P, T>;
-    constexpr int PT = B::PT, BX = B::BX, C = B::CELLS, m = P / 2, G = GroupOf<P>::G;
+    using B = Box<P, T, ZS>;
+    constexpr int PT = B::PT, PZ = B::PZ, BX = B::BX, C = B::CELLS, m = P / 2, G = GroupOf<P>::G;
+    static_assert(ZS == T || 2 * ZS == T, "a work unit is a tile or half of one");
     extern __shared__ __align__(32) unsigned char smraw_sg[];
     R* s = reinterpret_cast<R*>(smraw_sg);
     pdl_wait();
     if ((int)blockIdx.x >= *nwork) return;
     const int4 w = work[blockIdx.x];
-    const int tile = w.x;
+    const int tile = ZS < T ? w.x >> 1 : w.x;
+    const int z0 = ZS < T ? (w.x & 1) * ZS : 0;  // the unit's first cell inside the tile
     const int tx = tile & ((1 << lnbx) - 1), ty = (tile >> lnbx) & ((1 << lnby) - 1), tz = tile >> (lnbx + lnby);
-    const int ox = tx * T - B::XA, oy = ty * T - (m - 1), oz = tz * T - (m - 1);
+    const int ox = tx * T - B::XA, oy = ty * T - (m - 1), oz = tz * T + z0 - (m - 1);
     const int mask = M - 1;
     const size_t M3 = (size_t)M * M * M;
     // stage the box of every field with 16-byte loads
     constexpr int EV = 16 / sizeof(R);  // elements per 16-byte vector
     constexpr int NV = BX / EV;
-    for (int i = threadIdx.x; i < NV * PT * PT; i += blockDim.x) {
+    for (int i = threadIdx.x; i < NV * PT * PZ; i += blockDim.x) {
         const int vx = i % NV, ly = (i / NV) % PT, lz = i / (NV * PT);
         const size_t gi = ((size_t)((oz + lz) & mask) * M + ((oy + ly) & mask)) * M + ((ox + EV * vx) & mask);
         const int si = (lz * PT + ly) * BX + EV * vx;
@@ -367,7 +381,7 @@ __global__ void __launch_bounds__(NTH) k_gather(const int4* __restrict__ work, c
             *reinterpret_cast<float4*>(s + f * C + si) = __ldg(reinterpret_cast<const float4*>(fld + f * M3 + gi));
     }
     using RecT = typename Rec<R>::T;
-    RecT* srec = reinterpret_cast<RecT*>(s + NF * C + (blockDim.x >> 5) * (P * P));
+    RecT* srec = reinterpret_cast<RecT*>(s + NF * C + (blockDim.x >> 5) * WyzTable<P>::N);
     uint32_t* sperm = reinterpret_cast<uint32_t*>(srec + (w.z - w.y));
     for (int i = threadIdx.x; i < w.z - w.y; i += blockDim.x) {
         srec[i] = rec[w.y + i];
@@ -378,7 +392,7 @@ __global__ void __launch_bounds__(NTH) k_gather(const int4* __restrict__ work, c
     // one warp per particle, rows spread over the lanes as in k_spread
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int a = lane % G;
-    R* wyz = s + NF * C + warp * (P * P);
+    R* wyz = s + NF * C + warp * WyzTable<P>::N;
     for (int j = w.y + warp; j < w.z; j += nwarp) {
         const typename Rec<R>::T r = srec[j - w.y];
         int ix, iy, iz;
@@ -386,6 +400,7 @@ __global__ void __launch_bounds__(NTH) k_gather(const int4* __restrict__ work, c
         split_offset<R, T>(r.x, ix, dx);
         split_offset<R, T>(r.y, iy, dy);
         split_offset<R, T>(r.z, iz, dz);
+        iz -= z0;
         const R ua = dx + (R)(m - 1 - (a % P));
         const R wx = win_exp(ua * ua, wc);
         const R* base = s + (iz * PT + iy) * BX + ix + B::XOFF + a;
@@ -423,33 +438,35 @@ __global__ void __launch_bounds__(NTH) k_gather(const int4* __restrict__ work, c
 // through the window values.  The staged box holds the one grid, so the
 // tile's staging is a third of the three-field interpolation's and every
 // window point costs one shared-memory load.
-template <typename R, int P, int T, int NTH>
+template <typename R, int P, int T, int NTH, int ZS = T>
 __global__ void __launch_bounds__(NTH) k_gather_ad(const int4* __restrict__ work, const int* __restrict__ nwork,
                                                    const typename Rec<R>::T* __restrict__ rec,
                                                    const uint32_t* __restrict__ perm, int M, int lnbx, int lnby,
                                                    WinC<R> wc, R cnorm3, R fa0, R fa1, R fa2,
                                                    const R* __restrict__ fld, R* __restrict__ F, R* __restrict__ phi)
 {
-    using B = Box<P, T>;
-    constexpr int PT = B::PT, BX = B::BX, C = B::CELLS, m = P / 2, G = GroupOf<P>::G;
+    using B = Box<P, T, ZS>;
+    constexpr int PT = B::PT, PZ = B::PZ, BX = B::BX, C = B::CELLS, m = P / 2, G = GroupOf<P>::G;
+    static_assert(ZS == T || 2 * ZS == T, "a work unit is a tile or half of one");
     extern __shared__ __align__(32) unsigned char smraw_sg[];
     R* s = reinterpret_cast<R*>(smraw_sg);
     pdl_wait();
     if ((int)blockIdx.x >= *nwork) return;
     const int4 w = work[blockIdx.x];
-    const int tile = w.x;
+    const int tile = ZS < T ? w.x >> 1 : w.x;
+    const int z0 = ZS < T ? (w.x & 1) * ZS : 0;  // the unit's first cell inside the tile
     const int tx = tile & ((1 << lnbx) - 1), ty = (tile >> lnbx) & ((1 << lnby) - 1), tz = tile >> (lnbx + lnby);
-    const int ox = tx * T - B::XA, oy = ty * T - (m - 1), oz = tz * T - (m - 1);
+    const int ox = tx * T - B::XA, oy = ty * T - (m - 1), oz = tz * T + z0 - (m - 1);
     const int mask = M - 1;
     constexpr int EV = 16 / sizeof(R);
     constexpr int NV = BX / EV;
-    for (int i = threadIdx.x; i < NV * PT * PT; i += blockDim.x) {
+    for (int i = threadIdx.x; i < NV * PT * PZ; i += blockDim.x) {
         const int vx = i % NV, ly = (i / NV) % PT, lz = i / (NV * PT);
         const size_t gi = ((size_t)((oz + lz) & mask) * M + ((oy + ly) & mask)) * M + ((ox + EV * vx) & mask);
         *reinterpret_cast<float4*>(s + (lz * PT + ly) * BX + EV * vx) = __ldg(reinterpret_cast<const float4*>(fld + gi));
     }
     using RecT = typename Rec<R>::T;
-    RecT* srec = reinterpret_cast<RecT*>(s + C + (blockDim.x >> 5) * (P * P));
+    RecT* srec = reinterpret_cast<RecT*>(s + C + (blockDim.x >> 5) * WyzTable<P>::N);
     uint32_t* sperm = reinterpret_cast<uint32_t*>(srec + (w.z - w.y));
     for (int i = threadIdx.x; i < w.z - w.y; i += blockDim.x) {
         srec[i] = rec[w.y + i];
@@ -459,7 +476,7 @@ __global__ void __launch_bounds__(NTH) k_gather_ad(const int4* __restrict__ work
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int g = lane / G, a = lane % G;
-    R* wyz = s + C + warp * (P * P);
+    R* wyz = s + C + warp * WyzTable<P>::N;
     for (int j = w.y + warp; j < w.z; j += nwarp) {
         const RecT r = srec[j - w.y];
         int ix, iy, iz;
@@ -467,6 +484,7 @@ __global__ void __launch_bounds__(NTH) k_gather_ad(const int4* __restrict__ work
         split_offset<R, T>(r.x, ix, dx);
         split_offset<R, T>(r.y, iy, dy);
         split_offset<R, T>(r.z, iz, dz);
+        iz -= z0;
         const R ux = dx + (R)(m - 1 - (a % P));
         const R wx = win_exp(ux * ux, wc);
         const R* base = s + (iz * PT + iy) * BX + ix + B::XOFF + a;
