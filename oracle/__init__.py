@@ -15,6 +15,9 @@ arrays.  Functions follow the paper (Yang et al., arXiv:2004.12484):
 * :func:`nfft_ewald_ad`, :func:`kspace_nfft_ad` -- O2 with the forces as the
   analytic gradient of Eq. 38 (window derivative in the interpolation, one
   inverse FFT), the variant beside the ik forces of Eq. 41-42.
+* ``slater=lambda_e`` in :func:`real_space`, :func:`direct_ewald` and
+  :func:`nfft_ewald` -- the ENUF-DPD real-space correction for smeared
+  Slater-type charges (Eq. 51-58), with :func:`slater_factors`.
 * :func:`structure_factor_direct`, :func:`structure_factor_nfft`,
   :func:`fft1d`, :func:`fft3d`, :func:`window`, :func:`window_hat`,
   :func:`window_b`, :func:`image_sum` -- the individual steps, exposed so the
@@ -65,6 +68,9 @@ def lib():
         L.orc_fft3d.argtypes = [ctypes.c_int, _D, ctypes.c_int]
         L.orc_real_space.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_int64, _I64, _D, _D, _D, _D]
+        L.orc_real_space_slater.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_double, ctypes.c_int64, _I64, _D, _D, _D, _D]
+        L.orc_slater_factors.argtypes = [ctypes.c_double, ctypes.c_double, _D, _D]
         L.orc_self_and_background.argtypes = [ctypes.c_int64, _D, _D, ctypes.c_double, ctypes.c_double,
                                               _D, _D, _D]
         L.orc_kspace_direct.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_double, ctypes.c_double,
@@ -201,9 +207,21 @@ class EwaldResult:
     Q: float
 
 
-def real_space(pos, q, L, alpha, rc, ke=1.0, idx=None):
+def slater_factors(r, lambda_e):
+    """ENUF-DPD correction factors (B_U, B_F) of Eq. 57-58 at distance r."""
+    r = np.atleast_1d(np.asarray(r, dtype=np.float64))
+    bu = np.zeros_like(r); bf = np.zeros_like(r)
+    a, b = ctypes.c_double(), ctypes.c_double()
+    for k, x in enumerate(r):
+        lib().orc_slater_factors(float(x), float(lambda_e), ctypes.byref(a), ctypes.byref(b))
+        bu[k], bf[k] = a.value, b.value
+    return bu, bf
+
+
+def real_space(pos, q, L, alpha, rc, ke=1.0, idx=None, slater=None):
     """Eq. 17 / Eq. 29: returns (E_R, F_R, phi_R, W_R); E_R and W_R are None
-    when a subset ``idx`` is requested."""
+    when a subset ``idx`` is requested.  ``slater`` = lambda_e applies the
+    ENUF-DPD factors of smeared Slater-type charges (Eq. 51-58) to every pair."""
     pos = _arr(pos, (-1, 3)); q = _arr(q); L = _box(L)
     N = len(q)
     if idx is not None:
@@ -212,8 +230,12 @@ def real_space(pos, q, L, alpha, rc, ke=1.0, idx=None):
     else:
         n = N
     E = np.zeros(1); F = np.zeros((n, 3)); phi = np.zeros(n); W = np.zeros(9)
-    lib().orc_real_space(N, _dp(pos), _dp(q), _dp(L), alpha, rc, ke, n if idx is not None else 0,
-                         _ip(idx), _dp(E), _dp(F), _dp(phi), _dp(W))
+    if slater:
+        lib().orc_real_space_slater(N, _dp(pos), _dp(q), _dp(L), alpha, rc, ke, float(slater),
+                                    n if idx is not None else 0, _ip(idx), _dp(E), _dp(F), _dp(phi), _dp(W))
+    else:
+        lib().orc_real_space(N, _dp(pos), _dp(q), _dp(L), alpha, rc, ke, n if idx is not None else 0,
+                             _ip(idx), _dp(E), _dp(F), _dp(phi), _dp(W))
     if idx is not None:
         return None, F, phi, None
     return float(E[0]), F, phi, W.reshape(3, 3)
@@ -282,9 +304,9 @@ def nfft_ewald_ad(pos, q, L, alpha, rc, M, p, nc=None, ke=1.0) -> EwaldResult:
     return _assemble(pos, q, L, alpha, rc, ke, kspace_nfft_ad(pos, q, L, alpha, M, p, nc, ke))
 
 
-def _assemble(pos, q, L, alpha, rc, ke, kpart, idx=None):
+def _assemble(pos, q, L, alpha, rc, ke, kpart, idx=None, slater=None):
     Ek, Fk, phik, Wk = kpart
-    Er, Fr, phir, Wr = real_space(pos, q, L, alpha, rc, ke, idx=idx)
+    Er, Fr, phir, Wr = real_space(pos, q, L, alpha, rc, ke, idx=idx, slater=slater)
     Es, Eb, Q = self_and_background(q, L, alpha, ke)
     qs = _arr(q) if idx is None else _arr(q)[np.asarray(idx)]
     V = float(np.prod(_box(L)))
@@ -299,14 +321,17 @@ def _assemble(pos, q, L, alpha, rc, ke, kpart, idx=None):
                        virial=W, F_real=Fr, F_recip=Fk, phi_real=phir, phi_recip=phik, Q=Q)
 
 
-def direct_ewald(pos, q, L, alpha, rc, nmax, sphere=True, ke=1.0, idx=None) -> EwaldResult:
-    """O1: full Ewald sum with an explicit wave-vector set."""
-    return _assemble(pos, q, L, alpha, rc, ke, kspace_direct(pos, q, L, alpha, nmax, sphere, ke, idx=idx), idx)
+def direct_ewald(pos, q, L, alpha, rc, nmax, sphere=True, ke=1.0, idx=None, slater=None) -> EwaldResult:
+    """O1: full Ewald sum with an explicit wave-vector set (``slater`` =
+    lambda_e: the ENUF-DPD real-space factors, Eq. 57-58)."""
+    return _assemble(pos, q, L, alpha, rc, ke, kspace_direct(pos, q, L, alpha, nmax, sphere, ke, idx=idx), idx,
+                     slater=slater)
 
 
-def nfft_ewald(pos, q, L, alpha, rc, M, p, nc=None, ke=1.0) -> EwaldResult:
-    """O2: Ewald sum with the reciprocal part by NFFT."""
-    return _assemble(pos, q, L, alpha, rc, ke, kspace_nfft(pos, q, L, alpha, M, p, nc, ke))
+def nfft_ewald(pos, q, L, alpha, rc, M, p, nc=None, ke=1.0, slater=None) -> EwaldResult:
+    """O2: Ewald sum with the reciprocal part by NFFT (``slater`` as in
+    :func:`direct_ewald`)."""
+    return _assemble(pos, q, L, alpha, rc, ke, kspace_nfft(pos, q, L, alpha, M, p, nc, ke), slater=slater)
 
 
 def image_sum(pos, q, L, shell: int, ke=1.0) -> float:

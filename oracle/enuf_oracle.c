@@ -185,10 +185,28 @@ int orc_fft3d(int M, double *a, int sign)
 /* If idx != NULL only the particles idx[0..nsub) are evaluated (all j  */
 /* are still summed) and the energy/virial outputs are not written.    */
 /* ------------------------------------------------------------------ */
-int orc_real_space(int64_t N, const double *pos, const double *q, const double *L,
-                   double alpha, double rc, double ke,
-                   int64_t nsub, const int64_t *idx,
-                   double *E, double *F, double *phi, double *vir)
+/* ENUF-DPD correction factors of Slater-type smeared charges (Eq. 51-58):
+ * with x = r / lambda_e,
+ *   B_U = 1 - (1 + x) exp(-2x)                (energy, Eq. 57),
+ *   B_F = 1 - (1 + 2x (1 + x)) exp(-2x)       (force, Eq. 58);
+ * the pair energy and force of two such charges are the point-charge ones
+ * times B_U and B_F (Eq. 53-56). */
+void orc_slater_factors(double r, double lambda_e, double *BU, double *BF)
+{
+    double x = r / lambda_e, e = exp(-2.0 * x);
+    *BU = 1.0 - (1.0 + x) * e;
+    *BF = 1.0 - (1.0 + 2.0 * x * (1.0 + x)) * e;
+}
+
+/* Real-space sum; lambda_e > 0 applies the ENUF-DPD factors to each pair's
+ * erfc terms (the real-space part of the smeared-charge interaction within
+ * r_c, the method's r_c = 3 R_c); lambda_e = 0 is the point-charge sum.
+ * Two distinct smeared charges at the same point interact with the finite
+ * limit of Eq. 59 (erfc(0) B_U/r -> 1/lambda_e) and no force (Eq. 60). */
+static int real_space_core(int64_t N, const double *pos, const double *q, const double *L,
+                           double alpha, double rc, double ke, double lambda_e,
+                           int64_t nsub, const int64_t *idx,
+                           double *E, double *F, double *phi, double *vir)
 {
     /* the nearest-image vector has |d_t| <= L_t/2, so image shells up to
      * |n_t| <= floor(r_c/L_t + 1/2) can lie inside the cutoff */
@@ -220,9 +238,22 @@ int orc_real_space(int64_t N, const double *pos, const double *q, const double *
                     double dx = d0[0] + a * L[0], dy = d0[1] + b * L[1], dz = d0[2] + c * L[2];
                     double r2 = dx * dx + dy * dy + dz * dz;
                     if (r2 >= rc2) continue;
-                    double r = sqrt(r2);
-                    double e = erfc(alpha * r) / r;
-                    double fs = ke * q[i] * q[j] * (e + two_a_sqpi * exp(-alpha * alpha * r2)) / r2;
+                    double e, fs;
+                    if (r2 == 0.0) {
+                        if (!(lambda_e > 0.0)) continue;  /* coincident point charges: no finite term */
+                        e = 1.0 / lambda_e;
+                        fs = 0.0;
+                    } else {
+                        double r = sqrt(r2);
+                        e = erfc(alpha * r) / r;
+                        fs = ke * q[i] * q[j] * (e + two_a_sqpi * exp(-alpha * alpha * r2)) / r2;
+                        if (lambda_e > 0.0) {
+                            double BU, BF;
+                            orc_slater_factors(r, lambda_e, &BU, &BF);
+                            e *= BU;
+                            fs *= BF;
+                        }
+                    }
                     fi[0] += fs * dx; fi[1] += fs * dy; fi[2] += fs * dz;
                     ph += ke * q[j] * e;
                     /* each unordered pair is seen twice (from i and from j):
@@ -247,6 +278,23 @@ int orc_real_space(int64_t N, const double *pos, const double *q, const double *
         if (vir) for (int u = 0; u < 9; u++) vir[u] = W[u];
     }
     return 0;
+}
+
+int orc_real_space(int64_t N, const double *pos, const double *q, const double *L,
+                   double alpha, double rc, double ke,
+                   int64_t nsub, const int64_t *idx,
+                   double *E, double *F, double *phi, double *vir)
+{
+    return real_space_core(N, pos, q, L, alpha, rc, ke, 0.0, nsub, idx, E, F, phi, vir);
+}
+
+int orc_real_space_slater(int64_t N, const double *pos, const double *q, const double *L,
+                          double alpha, double rc, double ke, double lambda_e,
+                          int64_t nsub, const int64_t *idx,
+                          double *E, double *F, double *phi, double *vir)
+{
+    if (!(lambda_e > 0.0)) return -1;
+    return real_space_core(N, pos, q, L, alpha, rc, ke, lambda_e, nsub, idx, E, F, phi, vir);
 }
 
 /* ------------------------------------------------------------------ */

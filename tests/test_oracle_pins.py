@@ -412,3 +412,89 @@ def test_real_space_subset_matches_full():
     idx = [3, 100, 511]
     _, Fs, phis, _ = O.real_space(d["pos"], d["q"], d["L"], 0.35, 9.0, idx=idx)
     assert np.abs(Fs - F[idx]).max() < 1e-14 and np.abs(phis - phi[idx]).max() < 1e-14
+
+
+# ------------------------------------------------------------------ ENUF-DPD (Slater-type charges)
+LAMBDA_E = 6.954  # decay length of the method's smeared charges (beta = 1.125)
+
+
+def test_slater_potential_solves_poisson_by_quadrature():
+    """B_U(r)/r is the potential of the Slater density of Eq. 51 (Eq. 52):
+    the density integrates to the charge, and the shell-theorem potential
+    (enclosed charge / r plus the outer shells' 4 pi s rho ds), computed by
+    quadrature, matches the oracle's factor."""
+    from scipy.integrate import quad
+    lam = LAMBDA_E
+    rho = lambda s: np.exp(-2.0 * s / lam) / (np.pi * lam ** 3)
+    total, _ = quad(lambda s: 4 * np.pi * s * s * rho(s), 0, np.inf, epsabs=1e-14)
+    assert abs(total - 1.0) < 1e-12
+    for r in [0.05, 1.0, 3.7, 6.954, 12.0, 23.5]:
+        inner, _ = quad(lambda s: 4 * np.pi * s * s * rho(s), 0, r, epsabs=1e-15)
+        outer, _ = quad(lambda s: 4 * np.pi * s * rho(s), r, np.inf, epsabs=1e-15)
+        BU, _ = O.slater_factors(r, lam)
+        assert abs(BU[0] / r - (inner / r + outer)) < 1e-11
+
+
+def test_slater_force_factor_is_minus_derivative_and_limits():
+    """B_F / r^2 = -d(B_U / r)/dr (Eq. 54 from Eq. 53, by central
+    differences), the finite r -> 0 limits of Eq. 59-60 (energy beta/R_c =
+    1/lambda_e, force 0) and B_U, B_F -> 1 far away."""
+    lam = LAMBDA_E
+    h = 1e-5
+    for r in [0.3, 2.0, 7.0, 15.0, 23.0]:
+        up, _ = O.slater_factors(r + h, lam)
+        um, _ = O.slater_factors(r - h, lam)
+        _, BF = O.slater_factors(r, lam)
+        dU = ((up / (r + h)) - (um / (r - h))) / (2 * h)
+        assert abs(BF[0] / r ** 2 + dU[0]) < 1e-9
+    r = 1e-4
+    BU, BF = O.slater_factors(r, lam)
+    assert abs(BU[0] / r - 1.0 / lam) < 1e-4 / lam
+    assert abs(BF[0] / r ** 2) < 1e-5
+    BU, BF = O.slater_factors(40 * lam, lam)
+    assert abs(BU[0] - 1) < 1e-15 and abs(BF[0] - 1) < 1e-15
+
+
+def test_slater_real_space_pair_equals_quadrature_potential():
+    """Two smeared charges alone within the cutoff, alpha -> 0 (erfc -> 1):
+    the oracle's real-space energy is q1 q2 phi(r) with phi from the
+    quadrature of Eq. 51, its force the central difference of that energy,
+    its potentials q_j phi(r); coincident smeared charges carry the finite
+    energy q1 q2 / lambda_e (Eq. 59) and no force (Eq. 60)."""
+    from scipy.integrate import quad
+    lam = LAMBDA_E
+    rho = lambda s: np.exp(-2.0 * s / lam) / (np.pi * lam ** 3)
+
+    def phi(r):
+        inner, _ = quad(lambda s: 4 * np.pi * s * s * rho(s), 0, r, epsabs=1e-15)
+        outer, _ = quad(lambda s: 4 * np.pi * s * rho(s), r, np.inf, epsabs=1e-15)
+        return inner / r + outer
+
+    L = np.full(3, 200.0)
+    q = np.array([1.3, -0.7])
+    for d in [0.5, 4.0, 11.0]:
+        pos = np.array([[50.0, 60.0, 70.0], [50.0 + d * 0.6, 60.0 + d * 0.8, 70.0]])
+        E, F, ph, W = O.real_space(pos, q, L, 1e-13, 30.0, slater=lam)
+        assert abs(E - q[0] * q[1] * phi(d)) < 1e-9 * abs(q[0] * q[1] / d)
+        assert abs(ph[0] - q[1] * phi(d)) < 1e-9 and abs(ph[1] - q[0] * phi(d)) < 1e-9
+        h = 1e-5
+        fd = -(q[0] * q[1] * (phi(d + h) - phi(d - h)) / (2 * h))  # radial force on particle 1
+        unit = np.array([0.6, 0.8, 0.0])
+        assert np.abs(F[1] - fd * unit).max() < 1e-7
+        assert np.abs(F[0] + F[1]).max() < 1e-14
+    pos = np.array([[50.0, 60.0, 70.0], [50.0, 60.0, 70.0]])
+    E, F, ph, W = O.real_space(pos, q, L, 1e-13, 30.0, slater=lam)
+    assert abs(E - q[0] * q[1] / lam) < 1e-12 and np.abs(F).max() == 0.0
+
+
+def test_slater_reduces_to_point_charges_for_small_decay_length():
+    """lambda_e -> 0 gives back the point-charge real-space sum."""
+    g = np.random.default_rng(31)
+    L = np.array([14.0, 15.0, 16.0])
+    pos = g.uniform(0, 1, size=(40, 3)) * L
+    q = g.normal(size=40)
+    a = O.real_space(pos, q, L, 0.4, 6.0)
+    b = O.real_space(pos, q, L, 0.4, 6.0, slater=1e-4)
+    assert abs(a[0] / b[0] - 1) < 1e-12
+    assert np.abs(a[1] - b[1]).max() < 1e-12 * np.abs(a[1]).max()
+    assert np.abs(a[3] - b[3]).max() < 1e-12 * np.abs(a[3]).max()
