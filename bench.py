@@ -247,6 +247,17 @@ def large_systems(P, dev, timed, kspace):
             ms, _ = timed(lambda: kspace(plan, tp, tq, F, out), 10, 3)
             res[name] = {"value": N / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms, "N": N, "M": d["M"],
                          "p": d["p"]}
+            if name == "polyelectrolyte":
+                # full steps (real space included, r_c = 3 sigma) with point
+                # charges and with the ENUF-DPD smeared charges (lambda_e =
+                # sigma / 1.125)
+                ms_full, _ = timed(lambda: plan.compute(tp, tq, forces=True, virial=True, F=F, out=out), 10, 3)
+                plan_s = P.Plan(L=d["L"], N=N, alpha=d["alpha"], r_c=d["r_c"], M=d["M"], p=d["p"], n_c=d["n_c"],
+                                precision="mixed", device=dev, slater_lambda=1.0 / 1.125)
+                ms_dpd, _ = timed(lambda: plan_s.compute(tp, tq, forces=True, virial=True, F=F, out=out), 10, 3)
+                res[name].update({"ms_full_step": ms_full, "ms_full_step_slater": ms_dpd,
+                                  "value_full_step_slater": N / (ms_dpd * 1e-3) / 1e6})
+                del plan_s
             del plan, tp, tq, F
             torch.cuda.empty_cache()
         except Exception as e:  # report, do not lose the headline line

@@ -94,6 +94,13 @@ typedef struct enuf_params {
     int precision;     /* ENUF_FP64 or ENUF_MIXED                                */
     double coulomb_k;  /* 1/(4 pi eps0) in the caller's units; 0 selects 1.0     */
     int flags;         /* reserved, must be 0                                    */
+    double slater_lambda; /* ENUF-DPD smeared charges (Eq. 51): decay length   */
+                       /* lambda_e > 0 of the Slater-type densities; each      */
+                       /* real-space pair energy is scaled by B_U and each     */
+                       /* pair force by B_F (Eq. 57-58), coincident charges    */
+                       /* interact with the finite limit of Eq. 59; the        */
+                       /* reciprocal part stays the point-charge one (the      */
+                       /* method takes r_c = 3 R_c for this).  0: point charges */
 } enuf_params;
 
 typedef struct enuf_plan enuf_plan;

@@ -50,6 +50,7 @@ class EnufParams(ctypes.Structure):
         ("precision", ctypes.c_int),
         ("coulomb_k", ctypes.c_double),
         ("flags", ctypes.c_int),
+        ("slater_lambda", ctypes.c_double),
     ]
 
 
@@ -104,7 +105,7 @@ def version() -> str:
     return lib().enuf_version().decode()
 
 
-def make_params(L, N, alpha, r_c, M, p, n_c=0, precision="mixed", coulomb_k=1.0) -> EnufParams:
+def make_params(L, N, alpha, r_c, M, p, n_c=0, precision="mixed", coulomb_k=1.0, slater_lambda=0.0) -> EnufParams:
     Lv = np.broadcast_to(np.asarray(L, dtype=np.float64).reshape(-1), (3,))
     prm = EnufParams()
     for t in range(3):
@@ -119,6 +120,7 @@ def make_params(L, N, alpha, r_c, M, p, n_c=0, precision="mixed", coulomb_k=1.0)
         else int(precision)
     prm.coulomb_k = float(coulomb_k)
     prm.flags = 0
+    prm.slater_lambda = float(slater_lambda)
     return prm
 
 
@@ -133,11 +135,12 @@ class Plan:
     """An ENUF plan: fixed box, particle count and method parameters.  The
     device workspace is a torch tensor owned by the plan."""
 
-    def __init__(self, L, N, alpha, r_c, M, p, n_c=0, precision="mixed", coulomb_k=1.0, device=None):
+    def __init__(self, L, N, alpha, r_c, M, p, n_c=0, precision="mixed", coulomb_k=1.0, device=None,
+                 slater_lambda=0.0):
         import torch
         self.torch = torch
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-        self.params = make_params(L, N, alpha, r_c, M, p, n_c, precision, coulomb_k)
+        self.params = make_params(L, N, alpha, r_c, M, p, n_c, precision, coulomb_k, slater_lambda)
         self.dtype = torch.float64 if self.params.precision == FP64 else torch.float32
         self.N = int(N)
         nbytes = ctypes.c_size_t()

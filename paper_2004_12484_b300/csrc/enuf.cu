@@ -102,6 +102,8 @@ int resolve(const enuf_params* in, Resolved& r)
     if (p.precision != ENUF_FP64 && p.precision != ENUF_MIXED) return fail(ENUF_EINVAL, "unknown precision");
     if (p.coulomb_k == 0.0) p.coulomb_k = 1.0;
     if (p.flags != 0) return fail(ENUF_EINVAL, "params.flags is reserved and must be 0");
+    if (!(p.slater_lambda >= 0.0) || !std::isfinite(p.slater_lambda))
+        return fail(ENUF_EINVAL, "slater_lambda must be finite and >= 0");
     const double Lmin = std::min(p.L[0], std::min(p.L[1], p.L[2]));
     if (!(p.r_c > 0.0) || p.r_c > 0.5 * Lmin) return fail(ENUF_EINVAL, "r_c must satisfy 0 < r_c <= min(L)/2");
 
@@ -740,17 +742,25 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
         rp.self_phi = (R)(-2.0 * r.prm.alpha / std::sqrt(kPi));
         R* Fo = F ? at<R>(pl, y.Fr) : nullptr;
         R* po = want_phi ? at<R>(pl, y.phir) : nullptr;
-        if (r.cells && r.sr == 2)
-            LCHK(L.go("realspace", k_realspace_cells<R, 2>, dim3(nblkN, 5), dim3(256), 0, N, at<const RecT>(pl, y.rrec),
-                      at<const uint32_t>(pl, y.rcell), at<const uint32_t>(pl, y.roffsets), at<const uint32_t>(pl, y.rperm),
-                      rp, Fo, po, at<double>(pl, y.rpart)));
-        else if (r.cells)
-            LCHK(L.go("realspace", k_realspace_cells<R, 1>, dim3(nblkN, 3), dim3(256), 0, N, at<const RecT>(pl, y.rrec),
-                      at<const uint32_t>(pl, y.rcell), at<const uint32_t>(pl, y.roffsets), at<const uint32_t>(pl, y.rperm),
-                      rp, Fo, po, at<double>(pl, y.rpart)));
-        else
-            LCHK(L.go("realspace", k_realspace_allpairs<R>, dim3(nblkN), dim3(256), 0, N, at<const RecT>(pl, y.rrec),
-                      at<const uint32_t>(pl, y.rperm), rp, Fo, po, at<double>(pl, y.rpart)));
+        rp.inv_lam = r.prm.slater_lambda > 0.0 ? (R)(1.0 / r.prm.slater_lambda) : R(0);
+        const bool sl = r.prm.slater_lambda > 0.0;
+        const RecT* rrec = at<const RecT>(pl, y.rrec);
+        const uint32_t* rperm = at<const uint32_t>(pl, y.rperm);
+        double* rpart = at<double>(pl, y.rpart);
+        if (r.cells) {
+            const uint32_t* rcell = at<const uint32_t>(pl, y.rcell);
+            const uint32_t* roff = at<const uint32_t>(pl, y.roffsets);
+            const dim3 g(nblkN, 2 * r.sr + 1);
+            if (r.sr == 2)
+                LCHK(L.go("realspace", sl ? k_realspace_cells<R, 2, true> : k_realspace_cells<R, 2, false>, g,
+                          dim3(256), 0, N, rrec, rcell, roff, rperm, rp, Fo, po, rpart));
+            else
+                LCHK(L.go("realspace", sl ? k_realspace_cells<R, 1, true> : k_realspace_cells<R, 1, false>, g,
+                          dim3(256), 0, N, rrec, rcell, roff, rperm, rp, Fo, po, rpart));
+        } else {
+            LCHK(L.go("realspace", sl ? k_realspace_allpairs<R, true> : k_realspace_allpairs<R, false>, dim3(nblkN),
+                      dim3(256), 0, N, rrec, rperm, rp, Fo, po, rpart));
+        }
         return ENUF_OK;
     };
     const int nr = konly ? 0 : nblkN * (r.cells ? 2 * r.sr + 1 : 1);

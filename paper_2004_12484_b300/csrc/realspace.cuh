@@ -2,6 +2,8 @@
 // final FP64 assembly.
 //
 // Pair energy  q_i q_j erfc(alpha r) / r                        (Eq. 17)
+// (times B_U, and the force times B_F, for the smeared charges of ENUF-DPD,
+// Eq. 51-58)
 // Pair force   q_i q_j [erfc(alpha r)/r + 2 alpha/sqrt(pi) e^{-alpha^2 r^2}]
 //              r_ij / r^2                  (Eq. 29, textbook form)
 // Potential    phi_i += q_j erfc(alpha r) / r
@@ -23,27 +25,64 @@ template <typename R> struct RealParams {
     R L[3];      // box (all-pairs kernel)
     R rc2, alpha, two_a_sqpi, ke;
     R self_phi;  // -2 alpha / sqrt(pi) (self term of dE/dq_i, times ke inside)
+    R inv_lam;   // 1 / lambda_e of Slater-type smeared charges (kernels with SL)
 };
 
-template <typename R>
+// ENUF-DPD factors of Slater-type charges (Eq. 57-58) at x = r / lambda_e:
+// B_U = 1 - (1 + x) e^{-2x}, B_F = 1 - (1 + 2x (1 + x)) e^{-2x}, written with
+// expm1 so that B_U keeps its relative accuracy for close pairs (its leading
+// term is x).
+template <typename R> __device__ __forceinline__ void slater_factors(R x, R& bu, R& bf)
+{
+    R e, em;
+    if constexpr (sizeof(R) == 4) {
+        e = expf(-2.0f * x);
+        em = -expm1f(-2.0f * x);  // 1 - e^{-2x}
+    } else {
+        e = exp(-2.0 * x);
+        em = -expm1(-2.0 * x);
+    }
+    bu = em - x * e;
+    bf = em - R(2) * x * (R(1) + x) * e;
+}
+
+// SL: smeared Slater-type charges (ENUF-DPD): the erfc pair energy scaled by
+// B_U and the pair force by B_F; coincident charges add the finite energy of
+// Eq. 59 (erfc(0) B_U / r -> 1 / lambda_e) and no force (Eq. 60).
+template <typename R, bool SL = false>
 __device__ __forceinline__ void pair_term(R dx, R dy, R dz, R qi, R qj, const RealParams<R>& rp, R (&f)[3], R& ph,
                                           R (&acc)[7])
 {
     const R r2 = dx * dx + dy * dy + dz * dz;
-    if (r2 >= rp.rc2 || r2 <= R(0)) return;
+    if (r2 >= rp.rc2) return;
+    if (r2 <= R(0)) {
+        if constexpr (SL) {
+            ph += qj * rp.inv_lam;
+            acc[0] += R(0.5) * qi * qj * rp.inv_lam;
+        }
+        return;
+    }
     R ec, fs;
+    R r;
     if constexpr (sizeof(R) == 4) {
         // single precision: one reciprocal square root instead of a square
         // root and two divisions (rsqrtf is within 2 ulp)
         const float rinv = rsqrtf(r2);
-        const float ar = rp.alpha * (r2 * rinv);
+        r = r2 * rinv;
+        const float ar = rp.alpha * r;
         ec = erfcf(ar) * rinv;
         fs = qi * qj * (ec + rp.two_a_sqpi * expf(-ar * ar)) * (rinv * rinv);
     } else {
-        const R r = dsqrt(r2);
+        r = dsqrt(r2);
         const R ar = rp.alpha * r;
         ec = derfc(ar) / r;
         fs = qi * qj * (ec + rp.two_a_sqpi * dexp(-ar * ar)) / r2;
+    }
+    if constexpr (SL) {
+        R bu, bf;
+        slater_factors<R>(r * rp.inv_lam, bu, bf);
+        ec *= bu;
+        fs *= bf;
     }
     f[0] += fs * dx;
     f[1] += fs * dy;
@@ -64,7 +103,7 @@ __device__ __forceinline__ void pair_term(R dx, R dy, R dz, R qi, R qj, const Re
 // 1)^3 cells of edge >= r_c / SR).  Block row blockIdx.y = dz + SR takes one
 // z-layer of the stencil, so a particle is served by 2 SR + 1 threads and
 // small systems still fill the GPU.
-template <typename R, int SR>
+template <typename R, int SR, bool SL = false>
 __global__ void __launch_bounds__(256) k_realspace_cells(int N, const typename Rec<R>::T* __restrict__ rec,
                                                          const uint32_t* __restrict__ cell_of,
                                                          const uint32_t* __restrict__ offset,
@@ -93,7 +132,7 @@ __global__ void __launch_bounds__(256) k_realspace_cells(int N, const typename R
                     for (uint32_t j = offset[nb]; j < e; j++) {
                         if ((int)j == i) continue;
                         const typename Rec<R>::T rj = rec[j];
-                        pair_term<R>(sx - rj.x, sy - rj.y, sz - rj.z, ri.w, rj.w, rp, f, ph, acc);
+                        pair_term<R, SL>(sx - rj.x, sy - rj.y, sz - rj.z, ri.w, rj.w, rp, f, ph, acc);
                     }
                 }
             }
@@ -110,7 +149,7 @@ __global__ void __launch_bounds__(256) k_realspace_cells(int N, const typename R
 }
 
 // All pairs with the minimum image; records hold wrapped absolute positions.
-template <typename R>
+template <typename R, bool SL = false>
 __global__ void __launch_bounds__(256) k_realspace_allpairs(int N, const typename Rec<R>::T* __restrict__ rec,
                                                             const uint32_t* __restrict__ perm, RealParams<R> rp,
                                                             R* __restrict__ F, R* __restrict__ phi,
@@ -131,7 +170,7 @@ __global__ void __launch_bounds__(256) k_realspace_allpairs(int N, const typenam
                 if (d[t] > R(0.5) * rp.L[t]) d[t] -= rp.L[t];
                 else if (d[t] < R(-0.5) * rp.L[t]) d[t] += rp.L[t];
             }
-            pair_term<R>(d[0], d[1], d[2], ri.w, rj.w, rp, f, ph, acc);
+            pair_term<R, SL>(d[0], d[1], d[2], ri.w, rj.w, rp, f, ph, acc);
         }
         const uint32_t oi = perm[i];
         if (F) {

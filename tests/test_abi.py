@@ -25,10 +25,22 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, n), n
 
 
-def test_params_struct_matches_header_layout():
-    # double L[3]; int64 N; double alpha, r_c; int M, p, n_c, precision; double coulomb_k; int flags
-    assert ctypes.sizeof(P.EnufParams) == 80
-    assert P.EnufParams.coulomb_k.offset == 64
+def test_params_struct_matches_header_layout(tmp_path):
+    """The binding's ctypes structure has the size and field offsets that
+    a C compiler gives enuf_params from the header."""
+    import subprocess
+    fields = [f[0] for f in P.EnufParams._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "enuf.h"\nint main(void) {\n'
+                   + '    printf("%zu\\n", sizeof(enuf_params));\n'
+                   + "".join(f'    printf("%zu\\n", offsetof(enuf_params, {f}));\n' for f in fields)
+                   + "    return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.dirname(HDR), "-o", str(exe), str(src)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    assert got[0] == ctypes.sizeof(P.EnufParams)
+    for f, off in zip(fields, got[1:]):
+        assert getattr(P.EnufParams, f).offset == off, f
 
 
 def base(**kw):
