@@ -498,3 +498,46 @@ def test_slater_reduces_to_point_charges_for_small_decay_length():
     assert abs(a[0] / b[0] - 1) < 1e-12
     assert np.abs(a[1] - b[1]).max() < 1e-12 * np.abs(a[1]).max()
     assert np.abs(a[3] - b[3]).max() < 1e-12 * np.abs(a[3]).max()
+
+
+# ------------------------------------------------------------------ time stepping (velocity Verlet)
+def test_verlet_free_flight_and_constant_force_are_exact():
+    """Without forces the trajectory is r0 + v t (wrapped); under a constant
+    force velocity Verlet is exact: r0 + v0 t + a t^2 / 2, v0 + a t."""
+    from oracle import md
+    g = np.random.default_rng(40)
+    L = np.array([5.0, 6.0, 7.0])
+    r0 = g.uniform(0, 1, size=(10, 3)) * L
+    v0 = g.normal(size=(10, 3))
+    im = g.uniform(0.5, 2.0, size=10)
+    dt, n = 0.01, 137
+    pos, vel, _, _ = md.verlet(r0, v0, im, L, dt, n, lambda x: (0.0, np.zeros_like(x)))
+    t = dt * n
+    want = np.mod(r0 + v0 * t, L)
+    d = np.abs(pos - want)
+    assert np.minimum(d, L - d).max() < 1e-12 and np.abs(vel - v0).max() == 0.0
+    f = g.normal(size=(10, 3))
+    rc = r0 + 5e5  # in the middle of a box too large to wrap
+    pos, vel, _, _ = md.verlet(rc, v0, im, np.full(3, 1e6), dt, n, lambda x: (0.0, f))
+    a = im[:, None] * f
+    assert np.abs(pos - (rc + v0 * t + 0.5 * a * t * t)).max() < 1e-8
+    assert np.abs(vel - (v0 + a * t)).max() < 1e-12
+
+
+def test_verlet_energy_error_is_second_order_on_a_harmonic_oscillator():
+    """Velocity Verlet on x'' = -w^2 x: the energy error stays bounded and
+    scales as dt^2 (halving dt divides it by 4)."""
+    from oracle import md
+    L = np.full(3, 1e6)
+    k = 3.0
+    forces = lambda x: (0.5 * k * ((x - 5e5) ** 2).sum(), -k * (x - 5e5))
+    r0 = np.array([[5e5 + 1.0, 5e5, 5e5]])
+    v0 = np.array([[0.0, 0.7, 0.0]])
+    errs = []
+    for dt in [0.02, 0.01]:
+        n = int(round(20.0 / dt))
+        _, _, _, en = md.verlet(r0, v0, [1.0], L, dt, n, forces)
+        E0 = 0.5 * k * 1.0 + 0.5 * 0.49
+        errs.append(np.abs(en[:, 2] - E0).max() / E0)
+    assert errs[0] < 1e-3
+    assert 3.5 < errs[0] / errs[1] < 4.5
