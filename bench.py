@@ -423,6 +423,28 @@ def main():
             extra["ad_forces"]["p10"] = {"value": N / (ms10 * 1e-3) / 1e6, "ms_per_step": ms10,
                                          "rms_force_err_vs_exact": "8.2e-5 (tests/test_gpu_ad.py)"}
             del plan10
+        # ---- time stepping (enuf_md_run, velocity Verlet, one graph launch a
+        # step) on the same plan: a one-component plasma of the same positions
+        # (every charge +1, neutralising background), k-space forces and full
+        tv = torch.zeros_like(tp)
+        tq1 = torch.ones_like(tq)
+        im = torch.ones_like(tq)
+        Fmd = torch.empty_like(F)
+        md = {}
+        for label, ks in (("kspace_forces", True), ("full_forces", False)):
+            tx = tp.clone()
+            plan.md_run(tx, tv, tq1, im, 1e-3, 10, F=Fmd, kspace_only=ks)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.md_run(tx, tv, tq1, im, 1e-3, 200, F=Fmd, have_forces=True, kspace_only=ks)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            md[label] = {"ms_per_md_step": e0.elapsed_time(e1) / 200,
+                         "value": N / (e0.elapsed_time(e1) / 200 * 1e-3) / 1e6, "unit": UNIT}
+        md["note"] = "200 velocity-Verlet steps, L2 not flushed between steps (a trajectory reuses its data)"
+        extra["md"] = md
+        del tv, tq1, im, Fmd
         # the larger systems of the method's workloads (k-space E+F, mixed)
         if args.workload == "rpm_1e4" and not args.no_large:
             extra["large_systems"] = large_systems(P, dev, timed, kspace)

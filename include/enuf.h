@@ -163,6 +163,22 @@ int enuf_energy_forces_host(enuf_plan* plan, const void* pos_host, const void* q
  * state.  dpos: N x 3, dq: N (device; either may be NULL).  Asynchronous. */
 int enuf_backward(enuf_plan* plan, const void* pos, const void* q, const double* gE, void* dpos, void* dq);
 
+/* Time stepping driven by the plan: nsteps velocity-Verlet steps
+ *   v += (dt/2) F/m;  r += dt v (wrapped into the box);  F = F(r);  v += (dt/2) F/m
+ * with the forces of enuf_compute under `flags` (ENUF_AD_FORCES,
+ * ENUF_REMOVE_NET_FORCE, ENUF_KSPACE_ONLY, ENUF_WANT_VIRIAL; not
+ * ENUF_WANT_PHI), a harness for the conservation of energy and momentum
+ * along a trajectory.  pos, vel: N x 3, updated in place; q: N; inv_mass: N
+ * values 1/m_i (0 fixes a particle); F: N x 3, the forces at pos on return,
+ * and on entry when have_forces is nonzero (else computed first); all device
+ * buffers of the plan's type.  energies: 4 * nsteps doubles on the device,
+ * per step (E_pot, E_kin, E_pot + E_kin, status word).  Units are the
+ * caller's (F in coulomb_k q^2 / length^2, dt and m consistent with them).
+ * Each step is one CUDA graph launch (captured on the first call with the
+ * same buffers, flags, dt and nsteps).  Asynchronous on the plan's stream. */
+int enuf_md_run(enuf_plan* plan, void* pos, void* vel, const void* q, const void* inv_mass, void* F,
+                int have_forces, double dt, int nsteps, int flags, double* energies);
+
 /* Per-kernel device times (milliseconds) of the last enuf_compute, measured
  * with CUDA events when ENUF_PROFILE=1 was set at plan creation (graphs are
  * then not used).  Fills up to `cap` entries; returns the count. */

@@ -69,6 +69,8 @@ def lib():
         L.enuf_last_error.restype = ctypes.c_char_p
         L.enuf_version.restype = ctypes.c_char_p
         L.enuf_plan_workspace_bytes.argtypes = [ctypes.POINTER(EnufParams), ctypes.POINTER(ctypes.c_size_t)]
+        L.enuf_md_run.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                  ctypes.c_int, _vp]
         L.enuf_plan_create.argtypes = [ctypes.POINTER(EnufParams), _vp, ctypes.c_int, ctypes.POINTER(_vp)]
         L.enuf_plan_set_workspace.argtypes = [_vp, _vp, ctypes.c_size_t]
         L.enuf_plan_set_stream.argtypes = [_vp, _vp]
@@ -244,6 +246,28 @@ class Plan:
         _check(lib().enuf_energy_forces_host(self._h, _vp(ptr(pos_host)), _vp(ptr(q_host)), ctypes.byref(E),
                                              _vp(ptr(F_host)), W, _vp(ptr(phi_host)), fl))
         return E.value, np.array(W[:]).reshape(3, 3)
+
+    def md_run(self, pos, vel, q, inv_mass, dt, nsteps, F=None, have_forces=False, ad=False,
+               remove_net_force=False, kspace_only=False, energies=None):
+        """nsteps velocity-Verlet steps on the device (pos and vel updated in
+        place).  Returns (energies (nsteps, 4) float64 tensor: E_pot, E_kin,
+        E_tot, status per step; F at the final positions)."""
+        torch = self.torch
+        self._dev(pos, (self.N, 3), "pos")
+        self._dev(vel, (self.N, 3), "vel")
+        self._dev(q, (self.N,), "q")
+        self._dev(inv_mass, (self.N,), "inv_mass")
+        if F is None:
+            F = torch.empty((self.N, 3), dtype=self.dtype, device=self.device)
+            have_forces = False
+        if energies is None:
+            energies = torch.empty((max(int(nsteps), 1), 4), dtype=torch.float64, device=self.device)
+        fl = self.flags(False, False, kspace_only, remove_net_force, ad)
+        self._sync_stream()
+        _check(lib().enuf_md_run(self._h, _vp(pos.data_ptr()), _vp(vel.data_ptr()), _vp(q.data_ptr()),
+                                 _vp(inv_mass.data_ptr()), _vp(F.data_ptr()), 1 if have_forces else 0, float(dt),
+                                 int(nsteps), fl, _vp(energies.data_ptr())))
+        return energies[:nsteps], F
 
     def backward(self, pos, q, gE=None, dpos=None, dq=None):
         """dpos = -gE F, dq = gE phi (recomputed; gE a 1-element float64

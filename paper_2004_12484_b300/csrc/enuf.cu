@@ -27,6 +27,7 @@
 #include "fft.cuh"
 #include "realspace.cuh"
 #include "sort.cuh"
+#include "md.cuh"
 #include "spread_gather.cuh"
 
 using namespace enuf;
@@ -222,7 +223,7 @@ int resolve(const enuf_params* in, Resolved& r)
 
 // ------------------------------------------------------------------ workspace
 struct Layout {
-    size_t status, out, mean;
+    size_t status, out, mean, md_step;
     size_t counts, offsets, work, nwork, work2, nwork2, item2;
     size_t csum_g, cbase_g, csum_r, cbase_r;  // chunk totals / bases of the chunked scans
     size_t key, rank, rec_tmp, rec, perm, tile_of;
@@ -256,6 +257,7 @@ Layout layout(const Resolved& r)
     L.status = take(16);  // status word; at +4 the assembly's block counter, at +8 and +12 those of the two sorts
     L.out = take(ENUF_NOUT * 8);
     L.mean = take(4 * 8);
+    L.md_step = take(16);  // step counter of the time-stepping harness
     L.counts = take((size_t)(r.nbins + 1) * 4 * count_stride(r.nbins));
     L.offsets = take((r.nbins + 1) * 4);
     L.work = take((size_t)r.max_work * 16);
@@ -333,6 +335,15 @@ struct enuf_plan {
     bool pdl = true;  // programmatic dependent launch along the chain (ENUF_NO_PDL=1 turns it off)
     bool attrs_done = false;
     std::vector<GraphEntry> graphs;
+    // one time step of the harness (enuf_md_run) as a graph, for one set of
+    // buffers, flags and step
+    struct {
+        const void *pos, *vel, *q, *inv_mass, *F;
+        double* energies;
+        int flags, cap;
+        double dt;
+        cudaGraphExec_t exec = nullptr;
+    } md;
     unsigned long long stamp = 0;
     // derived constants
     double b = 0, inv_b = 0, cnorm3 = 0;
@@ -930,6 +941,8 @@ void drop_graphs(enuf_plan* pl)
 {
     for (auto& g : pl->graphs) cudaGraphExecDestroy(g.exec);
     pl->graphs.clear();
+    if (pl->md.exec) cudaGraphExecDestroy(pl->md.exec);
+    pl->md.exec = nullptr;
 }
 
 int bind_workspace(enuf_plan* pl, void* ptr)
@@ -1223,6 +1236,105 @@ int enuf_plan_get_params(const enuf_plan* pl, enuf_params* out)
 {
     if (!pl || !out) return fail(ENUF_EINVAL, "NULL argument");
     *out = pl->r.prm;
+    return ENUF_OK;
+}
+
+// One velocity-Verlet step on stream st (see md.cuh).
+int md_step_sequence(enuf_plan* pl, cudaStream_t st, void* pos, void* vel, const void* q, const void* im, void* F,
+                     double dt, int flags, double* energies, int cap)
+{
+    const Resolved& r = pl->r;
+    const Layout& y = pl->lay;
+    const int N = (int)r.prm.N, nb = (N + 255) / 256;
+    Launcher L{pl, st, false};
+    double* out = at<double>(pl, y.out);
+    double* part = at<double>(pl, y.fpart);
+    unsigned* step = at<unsigned>(pl, y.md_step);
+    if (r.fp64) {
+        using R = double;
+        LCHK(L.go("md_kick_drift", k_md_kick_drift<R>, dim3(nb), dim3(256), 0, N, (R*)pos, (R*)vel, (const R*)F,
+                  (const R*)im, (R)(0.5 * dt), (R)dt, (R)r.prm.L[0], (R)r.prm.L[1], (R)r.prm.L[2]));
+    } else {
+        using R = float;
+        LCHK(L.go("md_kick_drift", k_md_kick_drift<R>, dim3(nb), dim3(256), 0, N, (R*)pos, (R*)vel, (const R*)F,
+                  (const R*)im, (R)(0.5 * dt), (R)dt, (R)r.prm.L[0], (R)r.prm.L[1], (R)r.prm.L[2]));
+    }
+    LCHK(run_sequence(pl, st, false, pos, q, F, nullptr, out, flags));
+    if (r.fp64) {
+        using R = double;
+        LCHK(L.go("md_kick", k_md_kick<R>, dim3(nb), dim3(256), 0, N, (R*)vel, (const R*)F, (const R*)im, (R)(0.5 * dt),
+                  part));
+    } else {
+        using R = float;
+        LCHK(L.go("md_kick", k_md_kick<R>, dim3(nb), dim3(256), 0, N, (R*)vel, (const R*)F, (const R*)im, (R)(0.5 * dt),
+                  part));
+    }
+    LCHK(L.go("md_record", k_md_record, dim3(1), dim3(256), 0, nb, (const double*)part, (const double*)out, energies,
+              step, cap));
+    return ENUF_OK;
+}
+
+int enuf_md_run(enuf_plan* pl, void* pos, void* vel, const void* q, const void* inv_mass, void* F, int have_forces,
+                double dt, int nsteps, int flags, double* energies)
+{
+    if (!pl) return fail(ENUF_EINVAL, "plan is NULL");
+    if (!pl->ws) return fail(ENUF_EINVAL, "plan has no workspace");
+    if (!pos || !vel || !q || !inv_mass || !F || !energies) return fail(ENUF_EINVAL, "a buffer is NULL");
+    if (nsteps < 0) return fail(ENUF_EINVAL, "nsteps must be >= 0");
+    if (!std::isfinite(dt)) return fail(ENUF_EINVAL, "dt must be finite");
+    if (flags & ~(ENUF_WANT_VIRIAL | ENUF_REMOVE_NET_FORCE | ENUF_KSPACE_ONLY | ENUF_AD_FORCES))
+        return fail(ENUF_EINVAL, "unknown or unsupported flag bits");
+    LCHK(prepare_attrs(pl));
+    double* out = at<double>(pl, pl->lay.out);
+    if (!have_forces) LCHK(compute_impl(pl, pos, q, F, nullptr, out, flags));
+    CK(cudaMemsetAsync(pl->ws + pl->lay.md_step, 0, 16, pl->stream));
+    if (nsteps == 0) return ENUF_OK;
+    if (!pl->use_graph || pl->profile) {
+        for (int s = 0; s < nsteps; s++) {
+            int rc = md_step_sequence(pl, pl->stream, pos, vel, q, inv_mass, F, dt, flags, energies, nsteps);
+            if (rc != ENUF_OK) {
+                reset_zeroed(pl);
+                return rc;
+            }
+        }
+        return ENUF_OK;
+    }
+    auto& m = pl->md;
+    const bool same = m.exec && m.pos == pos && m.vel == vel && m.q == q && m.inv_mass == inv_mass && m.F == F &&
+                      m.energies == energies && m.flags == flags && m.dt == dt && m.cap == nsteps;
+    if (!same) {
+        if (m.exec) cudaGraphExecDestroy(m.exec);
+        m.exec = nullptr;
+        cudaGraph_t graph;
+        CK(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal));
+        int rc = md_step_sequence(pl, pl->cap_stream, pos, vel, q, inv_mass, F, dt, flags, energies, nsteps);
+        cudaError_t e = cudaStreamEndCapture(pl->cap_stream, &graph);
+        if (rc != ENUF_OK) {
+            if (e == cudaSuccess) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ENUF_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+        }
+        e = cudaGraphInstantiate(&m.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            m.exec = nullptr;
+            return fail(ENUF_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+        }
+        m.pos = pos;
+        m.vel = vel;
+        m.q = q;
+        m.inv_mass = inv_mass;
+        m.F = F;
+        m.energies = energies;
+        m.flags = flags;
+        m.dt = dt;
+        m.cap = nsteps;
+    }
+    for (int s = 0; s < nsteps; s++) CK(cudaGraphLaunch(m.exec, pl->stream));
     return ENUF_OK;
 }
 
