@@ -341,6 +341,56 @@ __global__ void __launch_bounds__(32) k_spread(const int4* __restrict__ work, co
     }
 }
 
+// Interpolates the n particles of one staged work unit from its box s (NF
+// fields of Box<P, T, ZS>::CELLS cells; z0 = the unit's first cell inside its
+// tile): one warp per particle, rows spread over the lanes as in k_spread.
+// wyz: the warp's weight-product table; srec: the unit's records; oidx(k):
+// the caller's index of the unit's particle k.  Fields 0..2 give the force
+// per unit charge (F_i = q_i * value), field 3 (NF = 4) the potential.
+template <typename R, int P, int T, int NF, int ZS, typename OIdx>
+__device__ __forceinline__ void interp_unit(const R* s, R* wyz, const typename Rec<R>::T* srec, int n, int z0,
+                                            const WinC<R>& wc, R cnorm3, R* __restrict__ F, R* __restrict__ phi,
+                                            OIdx&& oidx)
+{
+    using B = Box<P, T, ZS>;
+    constexpr int PT = B::PT, BX = B::BX, C = B::CELLS, m = P / 2, G = GroupOf<P>::G;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int a = lane % G;
+    for (int k = warp; k < n; k += nwarp) {
+        const typename Rec<R>::T r = srec[k];
+        int ix, iy, iz;
+        R dx, dy, dz;
+        split_offset<R, T>(r.x, ix, dx);
+        split_offset<R, T>(r.y, iy, dy);
+        split_offset<R, T>(r.z, iz, dz);
+        iz -= z0;
+        const R ua = dx + (R)(m - 1 - (a % P));
+        const R wx = win_exp(ua * ua, wc);
+        const R* base = s + (iz * PT + iy) * BX + ix + B::XOFF + a;
+        R acc[4] = {R(0), R(0), R(0), R(0)};
+        visit_window<R, P>(dy, dz, wx, wc, wyz, lane, [&](int, int b, int c, R ww) {
+            if (a < P) {
+                const int o = (c * PT + b) * BX;
+#pragma unroll
+                for (int f = 0; f < NF; f++) acc[f] += ww * base[f * C + o];
+            }
+        });
+        // warp sum of the four partials, transposed: after it lane 8 f
+        // holds the total of field f
+        const R tot = warp_sum4(acc, lane);
+        if ((lane & 7) == 0) {
+            const int f = lane >> 3;
+            const uint32_t oi = oidx(k);
+            if (f < 3) {
+                if (F) F[3 * (size_t)oi + f] = r.w * cnorm3 * tot;
+            } else if (NF == 4 && phi) {
+                phi[oi] = cnorm3 * tot;
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // Interpolation of NF real fields (planes of M^3, plane stride M^3).  Fields
 // 0..2 give the force per unit charge (F_i = q_i * value), field 3 (when
 // NF = 4) the potential phi_i.  F is written (not accumulated) in the
@@ -389,43 +439,8 @@ __global__ void __launch_bounds__(NTH) k_gather(const int4* __restrict__ work, c
     }
     __syncthreads();
 
-    // one warp per particle, rows spread over the lanes as in k_spread
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    const int a = lane % G;
-    R* wyz = s + NF * C + warp * WyzTable<P>::N;
-    for (int j = w.y + warp; j < w.z; j += nwarp) {
-        const typename Rec<R>::T r = srec[j - w.y];
-        int ix, iy, iz;
-        R dx, dy, dz;
-        split_offset<R, T>(r.x, ix, dx);
-        split_offset<R, T>(r.y, iy, dy);
-        split_offset<R, T>(r.z, iz, dz);
-        iz -= z0;
-        const R ua = dx + (R)(m - 1 - (a % P));
-        const R wx = win_exp(ua * ua, wc);
-        const R* base = s + (iz * PT + iy) * BX + ix + B::XOFF + a;
-        R acc[4] = {R(0), R(0), R(0), R(0)};
-        visit_window<R, P>(dy, dz, wx, wc, wyz, lane, [&](int, int b, int c, R ww) {
-            if (a < P) {
-                const int o = (c * PT + b) * BX;
-#pragma unroll
-                for (int f = 0; f < NF; f++) acc[f] += ww * base[f * C + o];
-            }
-        });
-        // warp sum of the four partials, transposed: after it lane 8 f
-        // holds the total of field f
-        const R tot = warp_sum4(acc, lane);
-        if ((lane & 7) == 0) {
-            const int f = lane >> 3;
-            const uint32_t oi = sperm[j - w.y];
-            if (f < 3) {
-                if (F) F[3 * (size_t)oi + f] = r.w * cnorm3 * tot;
-            } else if (NF == 4 && phi) {
-                phi[oi] = cnorm3 * tot;
-            }
-        }
-        __syncwarp();
-    }
+    interp_unit<R, P, T, NF, ZS>(s, s + NF * C + (threadIdx.x >> 5) * WyzTable<P>::N, srec, w.z - w.y, z0, wc,
+                                 cnorm3, F, phi, [&](int k) { return sperm[k]; });
 }
 
 // Interpolation for the analytic-differentiation forces: one real potential

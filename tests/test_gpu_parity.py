@@ -390,3 +390,35 @@ def test_positions_on_cell_and_box_boundaries(precision):
     q = g.normal(size=len(pos))
     q -= q.mean()
     check_full(pos, q, L, 0.4, 8.0, M, 6, 8, precision, escale=True)
+
+
+@pytest.mark.parametrize("p", [2, 4, 6, 8])
+def test_persistent_interpolation_forces_only(p, monkeypatch):
+    """Forces without the potential take the persistent double-buffered
+    interpolation kernel when the tiles have 16 cells: a random system and a
+    heavy tile on a 32^3 grid, and the benchmark's workload at full size
+    (the launch configuration the benchmark times), against the oracle."""
+    monkeypatch.setenv("ENUF_TILE", "16")
+    g = np.random.default_rng(60 + p)
+    L = np.array([22.0, 25.0, 27.0])
+    for pos in (g.uniform(-1.0, 2.0, size=(2500, 3)) * L, (3.0 + g.uniform(0, 12.0, size=(2500, 3))) * (L / 32)):
+        q = g.normal(size=len(pos))
+        q -= q.mean()
+        pos, q = W.as_fp32(pos, q)
+        parts, F, Wv, _ = run(pos, q, L, 0.4, 0.45 * min(L), 32, p, 8, "mixed", phi=False, kspace_only=True)
+        Ek, Fk, _, Wk = O.kspace_nfft(pos, q, L, 0.4, 32, p, 8)
+        assert abs(parts["E"] / Ek - 1) < 1e-6
+        assert rel_rms(F, Fk) < 1e-5
+
+
+def test_rpm_1e4_forces_only_full_size():
+    """The benchmark's call (k-space energy and forces, no potential) on its
+    workload at full size: forces element by element against the oracle."""
+    d = W.rpm_1e4()
+    pos, q = W.as_fp32(d["pos"], d["q"])
+    parts, F, Wv, _ = run(pos, q, d["L"], d["alpha"], d["r_c"], d["M"], d["p"], d["n_c"], "mixed", phi=False,
+                          kspace_only=True)
+    Ek, Fk, _, Wk = O.kspace_nfft(pos, q, d["L"], d["alpha"], d["M"], d["p"], d["n_c"])
+    assert abs(parts["E"] / Ek - 1) < 1e-6
+    assert rel_rms(F, Fk) < 1e-5
+    assert np.abs(Wv - Wk).max() < 1e-5 * np.abs(Wk).max()
