@@ -279,6 +279,34 @@ def large_systems(P, dev, timed, kspace):
     return res
 
 
+def n_sweep(P, dev, timed, kspace):
+    """k-space E+F of the RPM electrolyte at the benchmark's accuracy settings
+    (p = 8, alpha = 0.215, r_c = 14.5 A, density 0.01) for N = 8,192 to
+    4,194,304, the grid edge scaled with the box (M = 64 .. 512: the same
+    spacing and k_max), to show the N log N cost of the method."""
+    import math
+    import torch
+    res = []
+    for N, M in ((8192, 64), (65536, 128), (524288, 256), (4194304, 512)):
+        try:
+            d = W.rpm_1e4(N=N, M=M)
+            pos32, q32 = W.as_fp32(d["pos"], d["q"])
+            tp = torch.tensor(pos32, dtype=torch.float32, device=dev)
+            tq = torch.tensor(q32, dtype=torch.float32, device=dev)
+            plan = P.Plan(L=d["L"], N=N, alpha=d["alpha"], r_c=d["r_c"], M=M, p=d["p"], n_c=d["n_c"],
+                          precision="mixed", device=dev)
+            F = torch.empty((N, 3), dtype=torch.float32, device=dev)
+            out = torch.empty(16, dtype=torch.float64, device=dev)
+            ms, _ = timed(lambda: kspace(plan, tp, tq, F, out), 20, 3)
+            res.append({"N": N, "M": M, "ms_per_step": ms, "value": N / (ms * 1e-3) / 1e6,
+                        "ns_per_particle_per_log2N": ms * 1e6 / (N * math.log2(N))})
+            del plan, tp, tq, F
+            torch.cuda.empty_cache()
+        except Exception as e:  # report, do not lose the headline line
+            res.append({"N": N, "M": M, "error": str(e)[:200]})
+    return res
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -462,6 +490,7 @@ def main():
         # the larger systems of the method's workloads (k-space E+F, mixed)
         if args.workload == "rpm_1e4" and not args.no_large:
             extra["large_systems"] = large_systems(P, dev, timed, kspace)
+            extra["n_sweep"] = n_sweep(P, dev, timed, kspace)
         extra["rms_force_err_vs_exact"] = {"rpm_1e-4": "7.9e-5", "rpm": "4.1e-4"}.get(d["name"])
         dom = max(acc, key=acc.get)
         peak, src = measured_peaks()
