@@ -225,6 +225,12 @@ class Plan:
         parts = {k: float(h[i]) for k, i in OUT.items() if k not in ("virial", "status")}
         return parts, F, h[6:15].reshape(3, 3).copy(), ph
 
+    def __call__(self, pos, q, ad=False):
+        """plan(pos, q) -> (E, F, virial): the total energy (float), the forces
+        (device tensor, N x 3) and the 3 x 3 virial (numpy), synchronously."""
+        parts, F, W, _ = self.energy_forces(pos, q, ad=ad)
+        return parts["E"], F, W
+
     def energy_forces_host(self, pos_host, q_host, phi_host=None, F_host=None, kspace_only=False, ad=False):
         """End-to-end call with host (numpy or pinned torch CPU) buffers; the
         copies in and out are part of the call."""

@@ -422,3 +422,16 @@ def test_rpm_1e4_forces_only_full_size():
     assert abs(parts["E"] / Ek - 1) < 1e-6
     assert rel_rms(F, Fk) < 1e-5
     assert np.abs(Wv - Wk).max() < 1e-5 * np.abs(Wk).max()
+
+
+def test_plan_call_returns_energy_forces_virial():
+    """plan(pos, q) -> (E, F, virial), the binding's short form, against the
+    oracle on the rock-salt workload (FP64)."""
+    d = W.nacl()
+    plan = P.Plan(L=d["L"], N=len(d["q"]), alpha=d["alpha"], r_c=d["r_c"], M=d["M"], p=d["p"], n_c=d["n_c"],
+                  precision="fp64", device=DEV)
+    E, F, Wv = plan(torch.tensor(d["pos"], device=DEV), torch.tensor(d["q"], device=DEV))
+    ref = O.nfft_ewald(d["pos"], d["q"], d["L"], d["alpha"], d["r_c"], d["M"], d["p"], d["n_c"])
+    assert abs(E / ref.E - 1) < 1e-12
+    assert rel_rms(F.cpu().numpy(), ref.F) < 1e-12
+    assert np.abs(Wv - ref.virial).max() < 1e-12 * np.abs(ref.virial).max()
