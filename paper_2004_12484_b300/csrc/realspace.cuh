@@ -30,18 +30,16 @@ template <typename R> struct RealParams {
 
 // ENUF-DPD factors of Slater-type charges (Eq. 57-58) at x = r / lambda_e:
 // B_U = 1 - (1 + x) e^{-2x}, B_F = 1 - (1 + 2x (1 + x)) e^{-2x}, written with
-// expm1 so that B_U keeps its relative accuracy for close pairs (its leading
-// term is x).
+// em = 1 - e^{-2x} from expm1 so that B_U keeps its relative accuracy for
+// close pairs (its leading term is x); e^{-2x} = 1 - em then costs no second
+// exponential (for large x its relative error grows, but it only enters
+// multiplied by terms that B_U and B_F approach 1 against).
 template <typename R> __device__ __forceinline__ void slater_factors(R x, R& bu, R& bf)
 {
-    R e, em;
-    if constexpr (sizeof(R) == 4) {
-        e = expf(-2.0f * x);
-        em = -expm1f(-2.0f * x);  // 1 - e^{-2x}
-    } else {
-        e = exp(-2.0 * x);
-        em = -expm1(-2.0 * x);
-    }
+    R em;
+    if constexpr (sizeof(R) == 4) em = -expm1f(-2.0f * x);
+    else em = -expm1(-2.0 * x);
+    const R e = R(1) - em;
     bu = em - x * e;
     bf = em - R(2) * x * (R(1) + x) * e;
 }
