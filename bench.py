@@ -98,7 +98,7 @@ def measured_peaks():
 
 # Sources that make up each profiled kernel: the files it is compiled from
 # and, in enuf.cu, the function that sets its launch geometry.
-KERNEL_SOURCES = {"gather": (("common.cuh", "spread_gather.cuh", "sort.cuh"), "int launch_gather_t(")}
+KERNEL_SOURCES = {"gather": (("common.cuh", "spread_gather.cuh"), "int launch_gather_t(")}
 
 
 def csrc_hash(kernel=None):

@@ -106,25 +106,29 @@ __device__ __forceinline__ void scan_bins_block(const ScanArgs& a, int* status, 
 #pragma unroll
         for (int e = 0; e < 3; e++) base[e] = base0[e];
     }
+    // the thread's counts of a segment, all loads in flight at once; the next
+    // segment's are loaded while this one is scanned
+    uint32_t t[PER];
+    auto load_segment = [&](int s0) {
+        const int ns = min(SEG, hi - s0);
+#pragma unroll
+        for (int k = 0; k < PER; k++) {
+            const int i = tid + k * NT;
+            t[k] = i < ns ? __ldcg(a.count + (size_t)(s0 + i) * a.cs) : 0u;
+        }
+    };
+    if (lo < hi) load_segment(lo);
     for (int s0 = lo; s0 < hi; s0 += SEG) {
         const int ns = min(SEG, hi - s0);
-        {
-            // all of the thread's loads in flight at once
-            uint32_t t[PER];
 #pragma unroll
-            for (int k = 0; k < PER; k++) {
-                const int i = tid + k * NT;
-                t[k] = i < ns ? __ldcg(a.count + (size_t)(s0 + i) * a.cs) : 0u;
-            }
-#pragma unroll
-            for (int k = 0; k < PER; k++) {
-                const int i = tid + k * NT;
-                if (i < ns) {
-                    s_a[i] = t[k];
-                    a.count[(size_t)(s0 + i) * a.cs] = 0u;
-                }
+        for (int k = 0; k < PER; k++) {
+            const int i = tid + k * NT;
+            if (i < ns) {
+                s_a[i] = t[k];
+                a.count[(size_t)(s0 + i) * a.cs] = 0u;
             }
         }
+        if (s0 + SEG < hi) load_segment(s0 + SEG);
         __syncthreads();
         const int b0 = tid * PER;
         uint32_t n[PER];
