@@ -163,6 +163,13 @@ int enuf_energy_forces_host(enuf_plan* plan, const void* pos_host, const void* q
  * state.  dpos: N x 3, dq: N (device; either may be NULL).  Asynchronous. */
 int enuf_backward(enuf_plan* plan, const void* pos, const void* q, const double* gE, void* dpos, void* dq);
 
+/* enuf_backward with flags: ENUF_AD_FORCES takes -F by analytic
+ * differentiation, which is the exact gradient of the energy the forward
+ * call returns (the ik forces of enuf_backward are that gradient only within
+ * the method's accuracy).  Any other flag bit is ENUF_EINVAL. */
+int enuf_backward_flags(enuf_plan* plan, const void* pos, const void* q, const double* gE, void* dpos, void* dq,
+                        int flags);
+
 /* Time stepping driven by the plan: nsteps velocity-Verlet steps
  *   v += (dt/2) F/m;  r += dt v (wrapped into the box);  F = F(r);  v += (dt/2) F/m
  * with the forces of enuf_compute under `flags` (ENUF_AD_FORCES,

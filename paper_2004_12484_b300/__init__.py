@@ -71,6 +71,7 @@ def lib():
         L.enuf_plan_workspace_bytes.argtypes = [ctypes.POINTER(EnufParams), ctypes.POINTER(ctypes.c_size_t)]
         L.enuf_md_run.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                   ctypes.c_int, _vp]
+        L.enuf_backward_flags.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int]
         L.enuf_plan_create.argtypes = [ctypes.POINTER(EnufParams), _vp, ctypes.c_int, ctypes.POINTER(_vp)]
         L.enuf_plan_set_workspace.argtypes = [_vp, _vp, ctypes.c_size_t]
         L.enuf_plan_set_stream.argtypes = [_vp, _vp]
@@ -275,9 +276,10 @@ class Plan:
                                  int(nsteps), fl, _vp(energies.data_ptr())))
         return energies[:nsteps], F
 
-    def backward(self, pos, q, gE=None, dpos=None, dq=None):
+    def backward(self, pos, q, gE=None, dpos=None, dq=None, ad=False):
         """dpos = -gE F, dq = gE phi (recomputed; gE a 1-element float64
-        device tensor or None for 1)."""
+        device tensor or None for 1).  ad=True: F by analytic differentiation,
+        the exact gradient of the returned energy."""
         torch = self.torch
         self._dev(pos, (self.N, 3), "pos")
         self._dev(q, (self.N,), "q")
@@ -290,8 +292,8 @@ class Plan:
             gE = gE.detach().to(device=self.device, dtype=torch.float64).reshape(1).contiguous()
             g = gE.data_ptr()
         self._sync_stream()
-        _check(lib().enuf_backward(self._h, _vp(pos.data_ptr()), _vp(q.data_ptr()), _vp(g),
-                                   _vp(dpos.data_ptr()), _vp(dq.data_ptr())))
+        _check(lib().enuf_backward_flags(self._h, _vp(pos.data_ptr()), _vp(q.data_ptr()), _vp(g),
+                                         _vp(dpos.data_ptr()), _vp(dq.data_ptr()), AD_FORCES if ad else 0))
         self._keep = gE  # keep the scalar alive until the stream consumes it
         return dpos, dq
 
@@ -343,23 +345,25 @@ def _autograd():
         """E(pos, q) as a differentiable torch function.  forward returns the
         total energy (0-dim float64); backward returns dE/dpos = -F and
         dE/dq = phi, recomputing the grids through the library (no grid is
-        stored between the two passes)."""
+        stored between the two passes).  apply(pos, q, plan, True) takes F by
+        analytic differentiation: the exact gradient of the returned energy."""
 
         @staticmethod
-        def forward(ctx, pos, q, plan):
+        def forward(ctx, pos, q, plan, ad=False):
             if getattr(plan, "_eout", None) is None:
                 plan._eout = torch.empty((NOUT,), dtype=torch.float64, device=plan.device)
             out, _, _ = plan.compute(pos.detach(), q.detach(), forces=False, phi=False, virial=False,
                                      out=plan._eout)
             ctx.plan = plan
+            ctx.ad = bool(ad)
             ctx.save_for_backward(pos, q)
             return out[0].clone()
 
         @staticmethod
         def backward(ctx, gE):
             pos, q = ctx.saved_tensors
-            dpos, dq = ctx.plan.backward(pos.detach().contiguous(), q.detach().contiguous(), gE)
-            return dpos, dq, None
+            dpos, dq = ctx.plan.backward(pos.detach().contiguous(), q.detach().contiguous(), gE, ad=ctx.ad)
+            return dpos, dq, None, None
 
     return EnufEnergy
 

@@ -1421,13 +1421,15 @@ int enuf_energy_forces_host(enuf_plan* pl, const void* pos_host, const void* q_h
     return check_status(h);
 }
 
-int enuf_backward(enuf_plan* pl, const void* pos, const void* q, const double* gE, void* dpos, void* dq)
+int enuf_backward_flags(enuf_plan* pl, const void* pos, const void* q, const double* gE, void* dpos, void* dq,
+                        int flags)
 {
     if (!pl || !pl->ws) return fail(ENUF_EINVAL, "plan is NULL or has no workspace");
+    if (flags & ~ENUF_AD_FORCES) return fail(ENUF_EINVAL, "only ENUF_AD_FORCES is accepted");
     const Layout& y = pl->lay;
     void* F = pl->ws + y.s_F;
     void* phi = pl->ws + y.s_phi;
-    LCHK(compute_impl(pl, pos, q, F, phi, at<double>(pl, y.out), ENUF_WANT_PHI));
+    LCHK(compute_impl(pl, pos, q, F, phi, at<double>(pl, y.out), ENUF_WANT_PHI | flags));
     const int N = (int)pl->r.prm.N, nb = (N + 255) / 256;
     if (pl->r.fp64)
         k_backward_scale<double><<<nb, 256, 0, pl->stream>>>(N, (const double*)F, (const double*)phi, gE, (double*)dpos,
@@ -1437,6 +1439,11 @@ int enuf_backward(enuf_plan* pl, const void* pos, const void* q, const double* g
                                                            (float*)dq);
     CK(cudaGetLastError());
     return ENUF_OK;
+}
+
+int enuf_backward(enuf_plan* pl, const void* pos, const void* q, const double* gE, void* dpos, void* dq)
+{
+    return enuf_backward_flags(pl, pos, q, gE, dpos, dq, 0);
 }
 
 int enuf_last_timings(enuf_plan* pl, const char** names, float* times_ms, int cap)
