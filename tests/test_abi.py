@@ -57,7 +57,8 @@ def test_workspace_bytes_scales_with_grid():
 
 @pytest.mark.parametrize("bad", [dict(M=48), dict(M=4), dict(M=1024), dict(p=5), dict(p=14), dict(p=0),
                                  dict(n_c=16), dict(n_c=-1), dict(r_c=11.0), dict(r_c=0.0), dict(alpha=0.0),
-                                 dict(N=0), dict(L=(20.0, -1.0, 20.0)), dict(precision=7)])
+                                 dict(N=0), dict(L=(20.0, -1.0, 20.0)), dict(precision=7),
+                                 dict(slater_lambda=-1.0), dict(slater_lambda=float("inf"))])
 def test_invalid_parameters_are_rejected(bad):
     with pytest.raises(P.EnufError):
         P.workspace_bytes(**base(**bad))
@@ -66,3 +67,18 @@ def test_invalid_parameters_are_rejected(bad):
 def test_error_message_is_reported():
     with pytest.raises(P.EnufError, match="power of two"):
         P.workspace_bytes(**base(M=48))
+
+
+def test_entry_points_reject_a_missing_plan():
+    """Every call that takes a plan reports ENUF_EINVAL for NULL instead of
+    touching the device."""
+    L = P.lib()
+    v = ctypes.c_void_p
+    assert L.enuf_compute(None, v(1), v(1), None, None, None, 0) == -1
+    assert L.enuf_backward_flags(None, v(1), v(1), None, v(1), v(1), 0) == -1
+    assert L.enuf_md_run(None, v(1), v(1), v(1), v(1), v(1), 0, 0.1, 1, 0, v(1)) == -1
+
+
+def test_slater_decay_length_is_accepted():
+    assert P.workspace_bytes(**base(slater_lambda=0.889)) == P.workspace_bytes(**base())
+
