@@ -435,3 +435,26 @@ def test_plan_call_returns_energy_forces_virial():
     assert abs(E / ref.E - 1) < 1e-12
     assert rel_rms(F.cpu().numpy(), ref.F) < 1e-12
     assert np.abs(Wv - ref.virial).max() < 1e-12 * np.abs(ref.virial).max()
+
+
+@pytest.mark.parametrize("env", [{"ENUF_TILE": "16", "ENUF_GATHER_FULL_TILE": "1"}, {"ENUF_FZ_W": "16"},
+                                 {"ENUF_NO_PDL": "1"}, {"ENUF_NO_GRAPH": "1"}])
+def test_alternative_launch_configurations(env, monkeypatch):
+    """The plan-creation switches that select other launch configurations
+    (whole 16-cell interpolation tiles, another z-pass width, no
+    programmatic dependent launch, direct launches instead of graphs) give
+    the same results: forces only and with the potential, against the
+    oracle."""
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    g = np.random.default_rng(70)
+    L = np.array([22.0, 25.0, 27.0])
+    pos = g.uniform(-1.0, 2.0, size=(2500, 3)) * L
+    q = g.normal(size=2500)
+    q -= q.mean()
+    check_kspace(pos, q, L, 0.4, 32, 8, 8)
+    pos32, q32 = W.as_fp32(pos, q)
+    parts, F, _, _ = run(pos32, q32, L, 0.4, 0.45 * min(L), 32, 8, 8, "mixed", phi=False, kspace_only=True)
+    Ek, Fk, _, _ = O.kspace_nfft(pos32, q32, L, 0.4, 32, 8, 8)
+    assert abs(parts["E"] / Ek - 1) < 1e-6
+    assert rel_rms(F, Fk) < 1e-5
