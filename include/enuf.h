@@ -17,6 +17,12 @@
  * spread (Gaussian window) -> 3D FFT -> scale -> energy (Eq. 38); subdivide ->
  * inverse FFT (the three force components packed in one pass) -> interpolate.
  *
+ * Variants: forces by analytic differentiation of the approximated energy
+ * (flag ENUF_AD_FORCES: the potential alone is transformed back and the
+ * window's gradient interpolated); smeared Slater-type charges of ENUF-DPD
+ * (enuf_params.slater_lambda, Eq. 51-60: real-space pair terms scaled by
+ * B_U and B_F); velocity-Verlet time stepping driven by a plan (enuf_md_run).
+ *
  * Conventions
  *   - Every array argument of the compute calls is a DEVICE pointer unless
  *     its name ends in _host.  Positions are N x 3 row-major (x, y, z per
