@@ -88,6 +88,21 @@ def aggregate(ms_local, n_local, dist=None, device="cpu"):
     return n_tot / (ms_max * 1e-3) / 1e6, ms_max, n_tot
 
 
+def fma_peak_tflops():
+    """Single-precision FMA rate of this GPU (TFLOP/s) from the benchmark's
+    probe library (libenuf_probe.so, include/enuf_probe.h), the peak of the
+    FMA roofline of spreading and interpolation."""
+    import ctypes
+    lib = ctypes.CDLL(os.path.join(ROOT, "paper_2004_12484_b300", "libenuf_probe.so"))
+    lib.enuf_fma_peak_tflops.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+    lib.enuf_probe_last_error.restype = ctypes.c_char_p
+    v = ctypes.c_double()
+    rc = lib.enuf_fma_peak_tflops(ctypes.byref(v), None)
+    if rc != 0:
+        raise RuntimeError(lib.enuf_probe_last_error().decode())
+    return v.value
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -242,38 +257,102 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
-def large_systems(P, dev, timed, kspace):
-    """k-space E+F of the polyelectrolyte (N = 1,572,864, grid 256^3, p = 6)
-    and ionic-liquid (N = 8,388,608, grid 512^3, p = 8) workloads."""
+# Relative RMS total-force error of each large workload against converged
+# Ewald, as measured by tests/test_gpu_accuracy_large.py (the oracle runs
+# only in the tests and in the CPU-baseline leg).
+LARGE_ERRORS = {
+    "polyelectrolyte": "7e-4 (p = 6 window and r_c = 3 sigma; tests/test_gpu_accuracy_large.py)",
+    "polyelectrolyte_1e4": "<= 1e-4 target, about 6e-5 (tests/test_gpu_accuracy_large.py)",
+    "ionic_liquid": "<= 1e-5 target, about 5e-6 (tests/test_gpu_accuracy_large.py)",
+}
+
+
+def kernel_rooflines(acc, N, M, nc, nf, peak, rs=4):
+    """Per-kernel HBM roofline: algorithmic bytes of each launch over its
+    event-timed duration, against the measured copy bandwidth."""
+    out = {}
+    for k, t in acc.items():
+        alg = algorithmic_bytes(k, N, M, nc, nf, rs)
+        if not alg or t <= 0:
+            continue
+        gbs = alg / (t * 1e-3) / 1e9
+        out[k] = {"ms": round(t, 5), "algorithmic_bytes": alg, "achieved_gbs": round(gbs, 1),
+                  "frac": round(gbs / peak, 4)}
+    return out
+
+
+def profile_kernels(P, plan_kw, fn_of_plan, flush, reps=3):
+    """Mean per-kernel device times (ms) of one evaluation, from a plan made
+    with ENUF_PROFILE=1 (events between the kernels)."""
+    import torch
+    os.environ["ENUF_PROFILE"] = "1"
+    try:
+        pplan = P.Plan(**plan_kw)
+    finally:
+        os.environ.pop("ENUF_PROFILE", None)
+    fn_of_plan(pplan)
+    acc = {}
+    for _ in range(reps):
+        flush.fill_(1.0)
+        fn_of_plan(pplan)
+        for name, t in pplan.timings():
+            acc[name] = acc.get(name, 0.0) + t / reps
+    torch.cuda.synchronize()
+    del pplan
+    return acc
+
+
+def large_systems(P, dev, timed, kspace, flush, peak):
+    """k-space E+F of the polyelectrolyte (N = 1,572,864, grid 256^3; the
+    stated p = 6 settings and the 1e-4 settings) and ionic-liquid (N =
+    8,388,608, grid 512^3, p = 8) workloads: mixed and FP64 times, per-kernel
+    times and HBM rooflines."""
     import torch
     res = {}
-    for name in ("polyelectrolyte", "ionic_liquid"):
+    for name in ("polyelectrolyte", "polyelectrolyte_1e4", "ionic_liquid"):
         try:
             d = getattr(W, name)()
             N = len(d["q"])
             pos32, q32 = W.as_fp32(d["pos"], d["q"])
             tp = torch.tensor(pos32, dtype=torch.float32, device=dev)
             tq = torch.tensor(q32, dtype=torch.float32, device=dev)
-            plan = P.Plan(L=d["L"], N=N, alpha=d["alpha"], r_c=d["r_c"], M=d["M"], p=d["p"], n_c=d["n_c"],
-                          precision="mixed", device=dev)
+            kw = dict(L=d["L"], N=N, alpha=d["alpha"], r_c=d["r_c"], M=d["M"], p=d["p"], n_c=d["n_c"], device=dev)
+            plan = P.Plan(precision="mixed", **kw)
             F = torch.empty((N, 3), dtype=torch.float32, device=dev)
             out = torch.empty(16, dtype=torch.float64, device=dev)
             ms, _ = timed(lambda: kspace(plan, tp, tq, F, out), 10, 3)
-            res[name] = {"value": N / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms, "N": N, "M": d["M"],
-                         "p": d["p"]}
-            if name == "polyelectrolyte":
-                # full steps (real space included, r_c = 3 sigma) with point
-                # charges and with the ENUF-DPD smeared charges (lambda_e =
-                # sigma / 1.125)
+            r = {"value": N / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms, "N": N, "M": d["M"],
+                 "p": d["p"], "alpha": d["alpha"], "r_c": d["r_c"], "n_c": d["n_c"],
+                 "rms_force_err_vs_exact": LARGE_ERRORS[name]}
+            acc = profile_kernels(P, dict(precision="mixed", **kw), lambda pl: kspace(pl, tp, tq, F, out), flush)
+            r["kernel_ms"] = {k: round(v, 5) for k, v in acc.items()}
+            r["kernel_roofline"] = kernel_rooflines(acc, N, d["M"], d["n_c"], 3, peak)
+            r["kspace_algorithmic_bytes"] = 28 * N + 32 * d["M"] ** 3
+            r["kspace_hbm_frac"] = r["kspace_algorithmic_bytes"] / (ms * 1e-3) / 1e9 / peak
+            if name.startswith("polyelectrolyte"):
+                # full steps (real space included) with point charges and, at
+                # the stated settings, with the ENUF-DPD smeared charges
+                # (lambda_e = sigma / 1.125)
                 ms_full, _ = timed(lambda: plan.compute(tp, tq, forces=True, virial=True, F=F, out=out), 10, 3)
-                plan_s = P.Plan(L=d["L"], N=N, alpha=d["alpha"], r_c=d["r_c"], M=d["M"], p=d["p"], n_c=d["n_c"],
-                                precision="mixed", device=dev, slater_lambda=1.0 / 1.125)
-                ms_dpd, _ = timed(lambda: plan_s.compute(tp, tq, forces=True, virial=True, F=F, out=out), 10, 3)
-                res[name].update({"ms_full_step": ms_full, "ms_full_step_slater": ms_dpd,
-                                  "value_full_step_slater": N / (ms_dpd * 1e-3) / 1e6})
-                del plan_s
-            del plan, tp, tq, F
+                r["ms_full_step"] = ms_full
+                if name == "polyelectrolyte":
+                    plan_s = P.Plan(precision="mixed", slater_lambda=1.0 / 1.125, **kw)
+                    ms_dpd, _ = timed(lambda: plan_s.compute(tp, tq, forces=True, virial=True, F=F, out=out), 10, 3)
+                    r.update({"ms_full_step_slater": ms_dpd, "value_full_step_slater": N / (ms_dpd * 1e-3) / 1e6})
+                    del plan_s
+            del plan
             torch.cuda.empty_cache()
+            # the FP64 path on the same inputs
+            plan64 = P.Plan(precision="fp64", **kw)
+            tp64, tq64 = tp.double(), tq.double()
+            F64 = torch.empty((N, 3), dtype=torch.float64, device=dev)
+            ms64, _ = timed(lambda: kspace(plan64, tp64, tq64, F64, out), 3, 2)
+            r.update({"fp64_value": N / (ms64 * 1e-3) / 1e6, "ms_per_step_fp64": ms64, "mixed_over_fp64": ms64 / ms,
+                      "mixed_vs_fp64_rel_rms_force": float(((F.double() - F64) ** 2).sum().sqrt()
+                                                           / (F64 ** 2).sum().sqrt())})
+            del plan64, tp64, tq64, F64, tp, tq, F
+            torch.cuda.empty_cache()
+            res[name] = r
         except Exception as e:  # report, do not lose the headline line
             res[name] = {"error": str(e)[:200]}
     return res
@@ -489,7 +568,7 @@ def main():
         del tv, tq1, im, Fmd
         # the larger systems of the method's workloads (k-space E+F, mixed)
         if args.workload == "rpm_1e4" and not args.no_large:
-            extra["large_systems"] = large_systems(P, dev, timed, kspace)
+            extra["large_systems"] = large_systems(P, dev, timed, kspace, flush, measured_peaks()[0])
             extra["n_sweep"] = n_sweep(P, dev, timed, kspace)
         extra["rms_force_err_vs_exact"] = {"rpm_1e-4": "7.9e-5", "rpm": "4.1e-4"}.get(d["name"])
         dom = max(acc, key=acc.get)
@@ -504,7 +583,7 @@ def main():
         # adds per particle, window evaluations not counted) against the FMA
         # rate measured on this GPU by the library's probe kernel
         try:
-            fpk = P.fma_peak_tflops()
+            fpk = fma_peak_tflops()
 
             def fma_line(kernel, fmas_per_particle):
                 flops = 2.0 * fmas_per_particle * N

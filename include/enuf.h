@@ -192,6 +192,26 @@ int enuf_backward_flags(enuf_plan* plan, const void* pos, const void* q, const d
 int enuf_md_run(enuf_plan* plan, void* pos, void* vel, const void* q, const void* inv_mass, void* F,
                 int have_forces, double dt, int nsteps, int flags, double* energies);
 
+/* The transposed NFFT of Sec. 3.1 alone (spread, 3D FFT, scaling by the
+ * window's Fourier coefficients; Eq. 36-37): the approximated structure
+ * factor S~(n) ~ sum_j q_j exp(-2 pi i n.x_j), x_j = r_j / L, on the
+ * retained half cube n_x in [0, n_c], n_y, n_z in [-n_c, n_c].  S: device,
+ * (2 n_c + 1)^2 (n_c + 1) complex values of the plan's type (re, im pairs),
+ * element n at ((n_z + n_c)(2 n_c + 1) + (n_y + n_c))(n_c + 1) + n_x; the
+ * other half follows from S~(-n) = conj S~(n).  The structure factor is
+ * additive over any partition of the particles (the partial structure
+ * factors of Sec. 3.3 sum to the whole).  pos, q as for enuf_compute.
+ * Synchronises the plan's stream and checks the inputs (ENUF_ENONFINITE). */
+int enuf_structure_factor(enuf_plan* plan, const void* pos, const void* q, void* S);
+
+/* The library's hand-written forward 3D FFT alone, for checking it against
+ * another FFT: ghat(k) = sum_l g_l exp(-2 pi i k.l / M) (unnormalised, the
+ * sign of Sec. 3.1's forward transform) of the caller's real grid g
+ * ([z][y][x], M^3 values of the plan's type, device, not modified), on the
+ * same retained half cube and layout as enuf_structure_factor, without the
+ * scaling.  Asynchronous on the plan's stream. */
+int enuf_fft_forward(enuf_plan* plan, const void* grid, void* ghat);
+
 /* Per-kernel device times (milliseconds) of the last enuf_compute, measured
  * with CUDA events when ENUF_PROFILE=1 was set at plan creation (graphs are
  * then not used).  Fills up to `cap` entries; returns the count. */
@@ -201,8 +221,8 @@ int enuf_last_timings(enuf_plan* plan, const char** names, float* times_ms, int 
  * (memset nodes not counted). */
 int enuf_launch_count(enuf_plan* plan, int flags, int with_forces);
 
-/* Real-space part only (the pair sum of Eq. 17 / Eq. 29), for callers that
- * cannot allocate device memory: code running inside a framework whose
+/* Real-space erfc pair sum only, for callers that cannot allocate device
+ * memory: code running inside a framework whose
  * device memory is reserved by its own pool allocator, plugins handed only
  * their input and output buffers, or code that must not allocate (and so
  * possibly synchronise or fail) after set-up.  The paper has no counterpart
@@ -220,7 +240,7 @@ int enuf_launch_count(enuf_plan* plan, int flags, int with_forces);
  *   cuda_stream: cudaStream_t the work is ordered on (NULL = legacy stream).
  * Limits and behaviour: N <= 262,144 (the fixed scratch holds 1024 blocks of
  * 256 particles); larger N returns ENUF_EUNSUPPORTED with a message.  The
- * cost grows as N^2.  The first call on each device looks up the scratch
+ * cost grows as N^2 (every pair is visited).  The first call on each device looks up the scratch
  * array's device address (cudaGetSymbolAddress with that device current);
  * make that first call before any stream capture.  All calls on a device
  * share the scratch, so calls whose kernels overlap on the GPU (different
@@ -255,16 +275,6 @@ int enuf_mlp_train_step(float* w_master, void* w_bf16, float* adam_m, float* ada
                         const float* y_target, const float* out_weight, int batch, float lr, float beta1,
                         float beta2, float eps, int step, float* loss_out, float* grad_out, int apply_update,
                         void* stream);
-
-/* ---------------------------------------------------------------------
- * Measurement helper (not part of the method): the single-precision FMA
- * rate of the current device, measured by a kernel of independent fused
- * multiply-add chains, in TFLOP/s (2 flops per FMA).  It is the peak the
- * FMA roofline of the spreading and interpolation kernels is reported
- * against.  Synchronous (waits for its kernels on cuda_stream, NULL = legacy
- * stream); allocates no device memory; runs for a few milliseconds.
- * --------------------------------------------------------------------- */
-int enuf_fma_peak_tflops(double* tflops, void* cuda_stream);
 
 /* Thread-local description of the last failure ("" if none). */
 const char* enuf_last_error(void);

@@ -86,7 +86,8 @@ def lib():
         L.enuf_real_space_noalloc.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
                                               ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                               _vp, _vp, _vp, _vp]
-        L.enuf_fma_peak_tflops.argtypes = [ctypes.POINTER(ctypes.c_double), _vp]
+        L.enuf_structure_factor.argtypes = [_vp, _vp, _vp, _vp]
+        L.enuf_fft_forward.argtypes = [_vp, _vp, _vp]
         _lib = L
     return _lib
 
@@ -94,14 +95,6 @@ def lib():
 def _check(rc):
     if rc != 0:
         raise EnufError(f"enuf error {rc}: {lib().enuf_last_error().decode()}")
-
-
-def fma_peak_tflops(stream=None) -> float:
-    """Measured single-precision FMA rate of the current device (TFLOP/s),
-    the peak of the FMA roofline of the spreading and interpolation kernels."""
-    v = ctypes.c_double()
-    _check(lib().enuf_fma_peak_tflops(ctypes.byref(v), _vp(stream or 0)))
-    return v.value
 
 
 def version() -> str:
@@ -296,6 +289,31 @@ class Plan:
                                          _vp(dpos.data_ptr()), _vp(dq.data_ptr()), AD_FORCES if ad else 0))
         self._keep = gE  # keep the scalar alive until the stream consumes it
         return dpos, dq
+
+    def _spectrum(self):
+        nn, kx = 2 * self.n_c + 1, self.n_c + 1
+        ct = self.torch.complex128 if self.dtype == self.torch.float64 else self.torch.complex64
+        return self.torch.empty((nn, nn, kx), dtype=ct, device=self.device)
+
+    def structure_factor(self, pos, q):
+        """S~(n) on the retained half cube, a (2 n_c + 1, 2 n_c + 1, n_c + 1)
+        complex device tensor indexed [n_z + n_c, n_y + n_c, n_x] (synchronous)."""
+        self._dev(pos, (self.N, 3), "pos")
+        self._dev(q, (self.N,), "q")
+        S = self._spectrum()
+        self._sync_stream()
+        _check(lib().enuf_structure_factor(self._h, _vp(pos.data_ptr()), _vp(q.data_ptr()), _vp(S.data_ptr())))
+        return S
+
+    def fft_forward(self, grid):
+        """The library's forward FFT of a real (M, M, M) [z, y, x] device grid
+        on the retained half cube (same indexing as structure_factor)."""
+        M = self.M
+        self._dev(grid, (M, M, M), "grid")
+        G = self._spectrum()
+        self._sync_stream()
+        _check(lib().enuf_fft_forward(self._h, _vp(grid.data_ptr()), _vp(G.data_ptr())))
+        return G
 
     def launch_count(self, flags: int, forces: bool = True) -> int:
         n = lib().enuf_launch_count(self._h, int(flags), 1 if forces else 0)

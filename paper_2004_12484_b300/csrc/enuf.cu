@@ -574,8 +574,13 @@ template <typename R> int launch_gather_ad(Launcher& L, enuf_plan* pl, R* F, R* 
     DISPATCH_P(8, launch_gather_ad_t, L, pl, F, phi)
 }
 
+// The FFT chain of one evaluation: forward x and y, the z pass with the
+// reciprocal-space step and the inverse z transforms of nf fields, inverse y
+// and x.  With `spec` set, the chain stops after the forward z transform and
+// writes the retained spectrum there instead (ghat, or S~ = D ghat when
+// scale is 1; k_fz_spectrum).
 template <typename R, int M>
-int launch_fft_chain_m(Launcher& L, enuf_plan* pl, int nf)
+int launch_fft_chain_m(Launcher& L, enuf_plan* pl, int nf, void* spec = nullptr, int scale = 0)
 {
     using V = typename Cpx<R>::T;
     const Resolved& r = pl->r;
@@ -600,6 +605,19 @@ int launch_fft_chain_m(Launcher& L, enuf_plan* pl, int nf)
         const int Wc = r.gy.W;
         LCHK(L.go("fft_y", k_fy<R, M>, dim3((r.Kx + Wc - 1) / Wc, M), dim3(Wc * NT), (size_t)(Wc * (padlen(M) + 1) + M) * vs,
                   at<const V>(pl, y.C1), at<V>(pl, y.C2), r.gy, W));
+    }
+    if (spec) {
+        const int Wc = r.gz.W;
+        const size_t smem = (size_t)(Wc * (padlen(M) + 1) + M) * vs;
+        if (smem > 48 * 1024 && !L.attr_only) {
+            cudaError_t e = cudaFuncSetAttribute((const void*)k_fz_spectrum<R, M>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return fail(ENUF_ECUDA, std::string("cudaFuncSetAttribute(fft_z_spectrum): ") +
+                                                              cudaGetErrorString(e));
+        }
+        const int NTZ = M >= 4 ? M / 4 : 1;
+        return L.go("fft_z_spectrum", k_fz_spectrum<R, M>, dim3((r.P + Wc - 1) / Wc), dim3(Wc * NTZ), smem,
+                    at<const V>(pl, y.C2), reinterpret_cast<V*>(spec), r.gz, W, at<const R>(pl, y.td), scale);
     }
     // z + reciprocal-space step + inverse z
     {
@@ -649,16 +667,16 @@ int launch_fft_chain_m(Launcher& L, enuf_plan* pl, int nf)
     return ENUF_OK;
 }
 
-template <typename R> int launch_fft_chain(Launcher& L, enuf_plan* pl, int nf)
+template <typename R> int launch_fft_chain(Launcher& L, enuf_plan* pl, int nf, void* spec = nullptr, int scale = 0)
 {
     switch (pl->r.prm.M) {
-    case 8: return launch_fft_chain_m<R, 8>(L, pl, nf);
-    case 16: return launch_fft_chain_m<R, 16>(L, pl, nf);
-    case 32: return launch_fft_chain_m<R, 32>(L, pl, nf);
-    case 64: return launch_fft_chain_m<R, 64>(L, pl, nf);
-    case 128: return launch_fft_chain_m<R, 128>(L, pl, nf);
-    case 256: return launch_fft_chain_m<R, 256>(L, pl, nf);
-    case 512: return launch_fft_chain_m<R, 512>(L, pl, nf);
+    case 8: return launch_fft_chain_m<R, 8>(L, pl, nf, spec, scale);
+    case 16: return launch_fft_chain_m<R, 16>(L, pl, nf, spec, scale);
+    case 32: return launch_fft_chain_m<R, 32>(L, pl, nf, spec, scale);
+    case 64: return launch_fft_chain_m<R, 64>(L, pl, nf, spec, scale);
+    case 128: return launch_fft_chain_m<R, 128>(L, pl, nf, spec, scale);
+    case 256: return launch_fft_chain_m<R, 256>(L, pl, nf, spec, scale);
+    case 512: return launch_fft_chain_m<R, 512>(L, pl, nf, spec, scale);
     default: return fail(ENUF_EUNSUPPORTED, "unsupported M");
     }
 }
@@ -713,15 +731,18 @@ BinGeom make_geom(const int S[3], int T, const double L3[3], bool grid_units, in
 }
 
 // The whole evaluation on stream L.st.
+// With `spec` set: the transposed NFFT alone (sort, spread, forward FFT,
+// scaling), the structure factor S~ written to spec; nothing else runs.
 template <typename R>
-int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, R* phi, double* out, int flags)
+int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, R* phi, double* out, int flags,
+                    void* spec = nullptr)
 {
     const Resolved& r = pl->r;
     const Layout& y = pl->lay;
     const int N = (int)r.prm.N;
     const int nblkN = (N + 255) / 256;
     const bool want_phi = (flags & ENUF_WANT_PHI) && phi;
-    const bool konly = flags & ENUF_KSPACE_ONLY;
+    const bool konly = (flags & ENUF_KSPACE_ONLY) || spec;
     // forces by analytic differentiation: the potential's grid alone
     const bool ad = (flags & ENUF_AD_FORCES) && (F || want_phi);
     const int nf = ad ? 1 : (want_phi ? 4 : (F ? 3 : 0));
@@ -820,6 +841,7 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
     // (a3) spread (into a zeroed grid: zeroed at binding, then by the
     // forward FFT that reads it)
     LCHK(launch_spread<R>(L, pl));
+    if (spec) return launch_fft_chain<R>(L, pl, 0, spec, 1);
     // (a4-a6) FFT chain with the fused reciprocal step
     LCHK(launch_fft_chain<R>(L, pl, nf));
     // (a9) assembly parameters
@@ -1190,8 +1212,10 @@ int enuf_plan_create(const enuf_params* params, void* cuda_stream, int allocate,
     if (e != cudaSuccess) {
         cudaGetLastError();
         if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
+        if (pl->ev_join) cudaEventDestroy(pl->ev_join);
         if (pl->aux_stream) cudaStreamDestroy(pl->aux_stream);
         if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+        for (auto x : pl->tevents) cudaEventDestroy(x);
         delete pl;
         return fail(ENUF_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
     }
@@ -1204,8 +1228,12 @@ int enuf_plan_create(const enuf_params* params, void* cuda_stream, int allocate,
             cudaEventDestroy(pl->ev_join);
             cudaStreamDestroy(pl->aux_stream);
             cudaStreamDestroy(pl->cap_stream);
+            if (pl->hout) cudaFreeHost(pl->hout);
+            for (auto x : pl->tevents) cudaEventDestroy(x);
+            const size_t want = pl->lay.total;
             delete pl;
-            return fail(ENUF_ENOMEM, "cudaMalloc of " + std::to_string(pl->lay.total) + " bytes failed");
+            return fail(ENUF_ENOMEM, "cudaMalloc of " + std::to_string(want) + " bytes failed: " +
+                                         cudaGetErrorString(e));
         }
         pl->own_ws = true;
         int rc = bind_workspace(pl, p);
@@ -1460,6 +1488,48 @@ int enuf_last_timings(enuf_plan* pl, const char** names, float* times_ms, int ca
         if (times_ms) times_ms[i] = pl->ttimes[i];
     }
     return m;
+}
+
+int enuf_structure_factor(enuf_plan* pl, const void* pos, const void* q, void* S)
+{
+    if (!pl || !pl->ws) return fail(ENUF_EINVAL, "plan is NULL or has no workspace");
+    if (!pos || !q || !S) return fail(ENUF_EINVAL, "pos, q and S are required");
+    LCHK(prepare_attrs(pl));
+    Launcher L{pl, pl->stream, false};
+    int rc = pl->r.fp64 ? launch_sequence<double>(L, pl, (const double*)pos, (const double*)q, nullptr, nullptr,
+                                                  nullptr, ENUF_KSPACE_ONLY, S)
+                        : launch_sequence<float>(L, pl, (const float*)pos, (const float*)q, nullptr, nullptr,
+                                                 nullptr, ENUF_KSPACE_ONLY, S);
+    if (rc != ENUF_OK) {
+        reset_zeroed(pl);
+        return rc;
+    }
+    // the key pass records non-finite inputs in the status word, which the
+    // assembly of an evaluation would otherwise read and clear
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, pl->ws + pl->lay.status, sizeof(int), cudaMemcpyDeviceToHost, pl->stream));
+    CK(cudaStreamSynchronize(pl->stream));
+    if (st) {
+        CK(cudaMemsetAsync(pl->ws + pl->lay.status, 0, sizeof(int), pl->stream));
+        CK(cudaStreamSynchronize(pl->stream));
+        if (st & ST_NONFINITE) return fail(ENUF_ENONFINITE, "a position or charge is NaN or infinite");
+        return fail(ENUF_EDEVICE, "a kernel reported internal status " + std::to_string(st));
+    }
+    return ENUF_OK;
+}
+
+int enuf_fft_forward(enuf_plan* pl, const void* grid, void* ghat)
+{
+    if (!pl || !pl->ws) return fail(ENUF_EINVAL, "plan is NULL or has no workspace");
+    if (!grid || !ghat) return fail(ENUF_EINVAL, "grid and ghat are required");
+    LCHK(prepare_attrs(pl));
+    const size_t M = (size_t)pl->r.prm.M;
+    // the forward passes read the plan's grid buffer (and leave it zeroed)
+    CK(cudaMemcpyAsync(pl->ws + pl->lay.grid, grid, M * M * M * pl->r.rsz, cudaMemcpyDeviceToDevice, pl->stream));
+    Launcher L{pl, pl->stream, false};
+    int rc = pl->r.fp64 ? launch_fft_chain<double>(L, pl, 0, ghat, 0) : launch_fft_chain<float>(L, pl, 0, ghat, 0);
+    if (rc != ENUF_OK) reset_zeroed(pl);
+    return rc;
 }
 
 int enuf_launch_count(enuf_plan* pl, int flags, int with_forces)

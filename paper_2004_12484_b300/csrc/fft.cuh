@@ -432,6 +432,50 @@ __global__ void __launch_bounds__(512) k_fz(const typename Cpx<R>::T* __restrict
     }
 }
 
+// ---------------------------------------------------------------- k_fz_spectrum
+// The forward z pass alone, for the entry points that return the retained
+// spectrum instead of forces: the same pencils and transform as k_fz, then
+// for every retained n the value ghat(n) (scale = 0) or the approximated
+// structure factor S~(n) = D(n) ghat(n) (scale = 1, the scaling step of Sec.
+// 3.1), written to out[((n_z + n_c) Kb + (n_y + n_c)) Kx + n_x].
+// grid: ceil(P / W) blocks, W * NT(M) threads.
+template <typename R, int M>
+__global__ void __launch_bounds__(512) k_fz_spectrum(const typename Cpx<R>::T* __restrict__ C2,
+                                                     typename Cpx<R>::T* __restrict__ out, FftGeom g,
+                                                     const typename Cpx<R>::T* __restrict__ Wg,
+                                                     const R* __restrict__ td, int scale)
+{
+    using V = typename Cpx<R>::T;
+    constexpr int MR = 4, NT = FftThreads<M, MR>::NT, LD = PadLen<M>::V + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* X = reinterpret_cast<V*>(smraw);
+    const int Wc = g.W, Kx = g.Kx, Kb = g.Kb, nc = g.nc, P = g.P;
+    V* sW = X + Wc * LD;
+    stage_twiddles(sW, Wg, M);
+    pdl_wait();
+    const int p0 = blockIdx.x * Wc;
+    for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
+        const int z = (int)g.fW.div(i), w = i - z * Wc, p = p0 + w;
+        cp_async_cpx(X + w * LD + pidx(z), C2 + (p < P ? (size_t)z * P + p : 0), p < P);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    fft_smem<V, M, false, MR>(X + (threadIdx.x / NT) * LD, threadIdx.x % NT, sW, 1);
+    for (int i = threadIdx.x; i < Wc * Kb; i += blockDim.x) {
+        const int kbz = (int)g.fW.div(i), w = i - kbz * Wc, p = p0 + w;
+        if (p >= P) continue;
+        const int nz = kbz - nc, z = nz >= 0 ? nz : nz + M;
+        const int kb = (int)g.fKx.div(p), kx = p - kb * Kx;
+        const int ny = kb <= nc ? kb : kb - Kb;
+        V v = X[w * LD + pidx(z)];
+        if (scale) {
+            const R d = sqrt(td[kx + nc] * td[Kb + ny + nc] * td[2 * Kb + kbz]);
+            v = V{d * v.x, d * v.y};
+        }
+        out[((size_t)kbz * Kb + (ny + nc)) * Kx + kx] = v;
+    }
+}
+
 // ---------------------------------------------------------------- k_iy
 // grid: (ceil(Kx / W), M, NF) blocks, W * NT(M) threads.
 template <typename R, int M>

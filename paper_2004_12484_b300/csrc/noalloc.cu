@@ -62,7 +62,9 @@ int nfail(int code, const std::string& msg)
     return code;
 }
 
-template <typename R> __device__ __forceinline__ R wrap_to_box(R x, R L) { return x - L * floor(x / L); }
+// x wrapped into [0, L) (iL = 1/L, passed in so that no division runs per
+// particle or pair)
+template <typename R> __device__ __forceinline__ R wrap_to_box(R x, R L, R iL) { return x - L * floor(x * iL); }
 
 template <typename R>
 __device__ __forceinline__ void pair_sum(R dx, R dy, R dz, R qi, R qj, R rc2, R alpha, R two_a_sqpi, R (&f)[3], R& ph,
@@ -93,7 +95,8 @@ __device__ __forceinline__ void pair_sum(R dx, R dy, R dz, R qi, R qj, R rc2, R 
 // (deterministic), writes `out` and resets the counter.
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_real_space_noalloc(int N, const R* __restrict__ pos,
-                                                                 const R* __restrict__ q, R L0, R L1, R L2, R rc2,
+                                                                 const R* __restrict__ q, R L0, R L1, R L2, R iL0,
+                                                                 R iL1, R iL2, R rc2,
                                                                  R alpha, R two_a_sqpi, double ke,
                                                                  R* __restrict__ F, R* __restrict__ phi,
                                                                  NoAllocScratch* __restrict__ scratch,
@@ -105,9 +108,9 @@ __global__ void __launch_bounds__(kThreads) k_real_space_noalloc(int N, const R*
     const int i = blockIdx.x * kThreads + threadIdx.x;
     R xi = R(0), yi = R(0), zi = R(0), qi = R(0);
     if (i < N) {
-        xi = wrap_to_box(pos[3 * (size_t)i], L0);
-        yi = wrap_to_box(pos[3 * (size_t)i + 1], L1);
-        zi = wrap_to_box(pos[3 * (size_t)i + 2], L2);
+        xi = wrap_to_box(pos[3 * (size_t)i], L0, iL0);
+        yi = wrap_to_box(pos[3 * (size_t)i + 1], L1, iL1);
+        zi = wrap_to_box(pos[3 * (size_t)i + 2], L2, iL2);
         qi = q[i];
     }
     R f[3] = {R(0), R(0), R(0)}, ph = R(0);
@@ -115,9 +118,9 @@ __global__ void __launch_bounds__(kThreads) k_real_space_noalloc(int N, const R*
     for (int j0 = 0; j0 < N; j0 += kThreads) {
         const int j = j0 + threadIdx.x;
         if (j < N) {
-            sx[threadIdx.x] = wrap_to_box(pos[3 * (size_t)j], L0);
-            sy[threadIdx.x] = wrap_to_box(pos[3 * (size_t)j + 1], L1);
-            sz[threadIdx.x] = wrap_to_box(pos[3 * (size_t)j + 2], L2);
+            sx[threadIdx.x] = wrap_to_box(pos[3 * (size_t)j], L0, iL0);
+            sy[threadIdx.x] = wrap_to_box(pos[3 * (size_t)j + 1], L1, iL1);
+            sz[threadIdx.x] = wrap_to_box(pos[3 * (size_t)j + 2], L2, iL2);
             sq[threadIdx.x] = q[j];
         }
         __syncthreads();
@@ -126,9 +129,9 @@ __global__ void __launch_bounds__(kThreads) k_real_space_noalloc(int N, const R*
             for (int t = 0; t < nt; t++) {
                 if (j0 + t == i) continue;
                 R dx = xi - sx[t], dy = yi - sy[t], dz = zi - sz[t];
-                dx -= L0 * rint(dx / L0);
-                dy -= L1 * rint(dy / L1);
-                dz -= L2 * rint(dz / L2);
+                dx -= L0 * rint(dx * iL0);
+                dy -= L1 * rint(dy * iL1);
+                dz -= L2 * rint(dz * iL2);
                 pair_sum<R>(dx, dy, dz, qi, sq[t], rc2, alpha, two_a_sqpi, f, ph, acc);
             }
         }
@@ -218,11 +221,13 @@ int enuf_real_space_noalloc(const void* pos, const void* q, int64_t N, const dou
     const double two_a_sqpi = 2.0 * alpha / std::sqrt(3.14159265358979323846);
     if (precision == ENUF_FP64)
         k_real_space_noalloc<double><<<nb, kThreads, 0, st>>>(
-            (int)N, (const double*)pos, (const double*)q, L[0], L[1], L[2], r_c * r_c, alpha, two_a_sqpi, coulomb_k,
+            (int)N, (const double*)pos, (const double*)q, L[0], L[1], L[2], 1.0 / L[0], 1.0 / L[1], 1.0 / L[2],
+            r_c * r_c, alpha, two_a_sqpi, coulomb_k,
             (double*)F, (double*)phi, scratch, out);
     else
         k_real_space_noalloc<float><<<nb, kThreads, 0, st>>>(
-            (int)N, (const float*)pos, (const float*)q, (float)L[0], (float)L[1], (float)L[2], (float)(r_c * r_c),
+            (int)N, (const float*)pos, (const float*)q, (float)L[0], (float)L[1], (float)L[2], (float)(1.0 / L[0]),
+            (float)(1.0 / L[1]), (float)(1.0 / L[2]), (float)(r_c * r_c),
             (float)alpha, (float)two_a_sqpi, coulomb_k, (float*)F, (float*)phi, scratch, out);
     e = cudaGetLastError();
     if (e != cudaSuccess) return nfail(ENUF_ECUDA, std::string("launch: ") + cudaGetErrorString(e));

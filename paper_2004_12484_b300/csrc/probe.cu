@@ -1,5 +1,6 @@
 // probe.cu -- measured peak rate of single-precision fused multiply-adds on
-// the current device.  It is the denominator of the FMA roofline that is
+// the current device (libenuf_probe.so, a helper of the benchmark; not part
+// of the ENUF library).  It is the denominator of the FMA roofline that is
 // reported beside the HBM roofline for the spreading and interpolation
 // kernels, whose algorithmic work is p^3 and f p^3 multiply-adds per
 // particle (plus the window evaluations).
@@ -7,13 +8,11 @@
 
 #include <string>
 
-#include "../../include/enuf.h"
-
-namespace enuf {
-void set_last_error(const std::string& msg);  // enuf.cu: backs enuf_last_error()
-}
+#include "../../include/enuf_probe.h"
 
 namespace {
+
+thread_local std::string g_probe_err;
 
 __device__ float fma_sink;  // written only if the chains hit an impossible value
 
@@ -42,20 +41,22 @@ __global__ void __launch_bounds__(256) k_fma_peak(int iters, float seed)
 
 int pfail(int code, const std::string& msg)
 {
-    enuf::set_last_error(msg);
+    g_probe_err = msg;
     return code;
 }
 
 }  // namespace
 
+extern "C" const char* enuf_probe_last_error(void) { return g_probe_err.c_str(); }
+
 extern "C" int enuf_fma_peak_tflops(double* tflops, void* cuda_stream)
 {
-    enuf::set_last_error("");
-    if (!tflops) return pfail(ENUF_EINVAL, "tflops is NULL");
+    g_probe_err.clear();
+    if (!tflops) return pfail(-1, "tflops is NULL");
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return pfail(ENUF_ECUDA, std::string("device query: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return pfail(-4, std::string("device query: ") + cudaGetErrorString(e));
     const cudaStream_t st = (cudaStream_t)cuda_stream;
     const int blocks = sms * 8, threads = 256, iters = 2048, reps = 3;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -75,9 +76,9 @@ extern "C" int enuf_fma_peak_tflops(double* tflops, void* cuda_stream)
     if (e1) cudaEventDestroy(e1);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return pfail(ENUF_ECUDA, std::string("FMA probe: ") + cudaGetErrorString(e));
+        return pfail(-4, std::string("FMA probe: ") + cudaGetErrorString(e));
     }
     const double fmas = (double)blocks * threads * iters * kUnroll * kChains * reps;
     *tflops = 2.0 * fmas / ((double)ms * 1e-3) / 1e12;
-    return ENUF_OK;
+    return 0;
 }

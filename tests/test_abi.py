@@ -25,6 +25,19 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, n), n
 
 
+def test_probe_library_is_separate_and_exports_its_header():
+    """The benchmark's FMA probe lives in its own library, not in libenuf.so."""
+    lib = P.lib()
+    assert not hasattr(lib, "enuf_fma_peak_tflops")
+    phdr = os.path.join(os.path.dirname(HDR), "enuf_probe.h")
+    text = re.sub(r"/\*.*?\*/", "", open(phdr).read(), flags=re.S)
+    names = sorted(set(re.findall(r"\b(enuf_[a-z0-9_]+)\s*\(", text)))
+    probe = ctypes.CDLL(os.path.join(os.path.dirname(P.LIB_PATH), "libenuf_probe.so"))
+    assert names == ["enuf_fma_peak_tflops", "enuf_probe_last_error"]
+    for n in names:
+        assert hasattr(probe, n), n
+
+
 def test_params_struct_matches_header_layout(tmp_path):
     """The binding's ctypes structure has the size and field offsets that
     a C compiler gives enuf_params from the header."""

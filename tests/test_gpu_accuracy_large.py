@@ -1,0 +1,151 @@
+"""Accuracy of the large workloads at full size against converged Ewald, and
+the central-difference check of the differentiable energy on the full
+polyelectrolyte system.
+
+* Ionic-liquid sites (N = 8,388,608, grid 512^3, p = 8): the total forces of
+  the mixed plan on 128 sampled charged sites against the direct Ewald sum
+  (O1) converged far below the target, relative RMS error <= 1e-5.
+* Polyelectrolyte (N = 1,572,864, grid 256^3): the same at the 1e-4 settings
+  (p = 8, r_c = 4.3 sigma, alpha = 0.70) and at the stated p = 6, r_c =
+  3 sigma settings, which the window and the real-space truncation cap near
+  7e-4.
+* Polyelectrolyte at the 1e-4 settings, FP64: central differences (h = 1e-4
+  sigma) of the energy returned by the autograd function on 64 random beads
+  (one coordinate each) against its backward pass -- dE/dr by analytic
+  differentiation is the exact derivative (agreement to the rounding of the
+  energy, about 1e-14 of its 1e6 magnitude, over 2h), the ik gradient
+  differs from it by no more than the sum of the two gradients' errors
+  against converged Ewald -- and dE/dq against central differences in q (the
+  energy is quadratic in q).
+
+The converged reference uses r_c = 0.499 L (one periodic image per pair) and
+alpha r_c = 4.5, with every wave vector |n| <= n_max where exp(-k^2/4a^2)
+falls below exp(-4.5^2): its own truncation errors are below 1e-8 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2004_12484_b300 as P  # noqa: E402
+
+DEV = torch.device("cuda", 0)
+
+
+def rel_rms(a, b):
+    return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
+
+
+def plan_for(d, precision="mixed"):
+    return P.Plan(L=d["L"], N=len(d["q"]), alpha=d["alpha"], r_c=d["r_c"], M=d["M"], p=d["p"], n_c=d["n_c"],
+                  precision=precision, device=DEV)
+
+
+def converged_reference(pos, q, L, idx):
+    """O1 forces on the sites idx, converged: alpha r_c = 4.5 with r_c just
+    below L/2, and the wave vectors of the matching sphere."""
+    x = 4.5
+    rc = 0.499 * float(min(L))
+    a = x / rc
+    nmax = int(math.ceil(a * float(max(L)) * x / math.pi))
+    return O.direct_ewald(pos, q, L, a, rc, nmax=nmax, sphere=True, idx=idx).F
+
+
+def total_force_error(d, n_sites=128, seed=9):
+    pos, q = W.as_fp32(d["pos"], d["q"])
+    plan = plan_for(d)
+    tp = torch.tensor(pos, dtype=torch.float32, device=DEV)
+    tq = torch.tensor(q, dtype=torch.float32, device=DEV)
+    _, F, _, _ = plan.energy_forces(tp, tq)
+    F = F.cpu().double().numpy()
+    del plan, tp, tq
+    torch.cuda.empty_cache()
+    # charged sites only: a neutral site's force is zero in both
+    idx = np.random.default_rng(seed).choice(np.nonzero(q != 0)[0], n_sites, replace=False)
+    ref = converged_reference(pos, q, d["L"], idx)
+    return rel_rms(F[idx], ref)
+
+
+def test_ionic_liquid_meets_1e5_against_exact_ewald():
+    err = total_force_error(W.ionic_liquid())
+    print("ionic liquid, relative RMS force error vs converged Ewald:", err)
+    assert err < 1e-5
+
+
+@pytest.mark.parametrize("variant,bound", [("polyelectrolyte_1e4", 1e-4), ("polyelectrolyte", 1.5e-3)])
+def test_polyelectrolyte_force_error_against_exact_ewald(variant, bound):
+    err = total_force_error(getattr(W, variant)())
+    print(variant, "relative RMS force error vs converged Ewald:", err)
+    assert err < bound
+
+
+def test_polyelectrolyte_central_differences_full_size():
+    d = W.polyelectrolyte_1e4()
+    pos, q, L = d["pos"], d["q"], d["L"]
+    N, M, rc = len(q), d["M"], d["r_c"]
+    plan = plan_for(d, "fp64")
+    tp = torch.tensor(pos, dtype=torch.float64, device=DEV)
+    tq = torch.tensor(q, dtype=torch.float64, device=DEV)
+    # gradients through the autograd function: ik and analytic differentiation
+    grads = {}
+    for ad in (False, True):
+        x = tp.clone().requires_grad_(True)
+        y = tq.clone().requires_grad_(True)
+        P.EnufEnergy.apply(x, y, plan, ad).backward()
+        grads[ad] = (x.grad.cpu().numpy(), y.grad.cpu().numpy())
+    beads = np.random.default_rng(33).choice(np.nonzero(q[: d["n_beads"]] != 0)[0], 64, replace=False)
+    h = 1e-4
+
+    def energy(pp, qq):
+        return float(P.EnufEnergy.apply(pp, qq, plan))
+
+    fd = np.full(64, np.nan)
+    comp = np.arange(64) % 3
+    for k, i in enumerate(beads):
+        t = comp[k]
+        # no derivative where the interval crosses a grid-cell face (the
+        # truncated window jumps) or moves a pair across r_c
+        if np.floor(M * (pos[i, t] + h) / L[t]) != np.floor(M * (pos[i, t] - h) / L[t]):
+            continue
+        dr = pos - pos[i]
+        dr -= L * np.round(dr / L)
+        r = np.sqrt((dr ** 2).sum(1))
+        r[i] = np.inf
+        if np.any(np.abs(r - rc) < 2 * h):
+            continue
+        pp = tp.clone(); pp[i, t] += h
+        pm = tp.clone(); pm[i, t] -= h
+        fd[k] = (energy(pp, tq) - energy(pm, tq)) / (2 * h)
+    ok = ~np.isnan(fd)
+    assert ok.sum() > 55
+    sel = (beads[ok], comp[ok])
+    g_ad, g_ik, fdo = grads[True][0][sel], grads[False][0][sel], fd[ok]
+    err_ad = rel_rms(g_ad, fdo)
+    err_ik = rel_rms(g_ik, fdo)
+    # both gradients against converged Ewald (minus the force) on the same beads
+    ref = -converged_reference(pos, q, L, beads)[ok, comp[ok]]
+    e_ad, e_ik = rel_rms(g_ad, ref), rel_rms(g_ik, ref)
+    print(f"central differences: analytic-differentiation gradient {err_ad:.2e}, ik gradient {err_ik:.2e} "
+          f"(relative RMS); against converged Ewald: analytic differentiation {e_ad:.2e}, ik {e_ik:.2e}")
+    assert err_ad < 5e-6
+    assert float(np.abs(g_ad - fdo).max()) < 2e-5 * float(np.sqrt((fdo ** 2).mean()))
+    # the ik forces are not the exact derivative, but both approximate the
+    # same exact force: their gap is bounded by the two errors
+    assert err_ik <= 1.05 * (e_ad + e_ik)
+    assert e_ik < 1e-4 and e_ad < 2e-3
+    # dE/dq: the energy is quadratic in q, so the central difference is exact
+    # for any step (a wide one keeps the energy's rounding small against it)
+    dq = grads[False][1]
+    for i in beads[:4]:
+        qp = tq.clone(); qp[i] += 0.1
+        qm = tq.clone(); qm[i] -= 0.1
+        fdq = (energy(tp, qp) - energy(tp, qm)) / 0.2
+        assert abs(fdq - dq[i]) < 1e-7 * (1 + abs(dq[i]))

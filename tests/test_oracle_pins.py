@@ -132,7 +132,7 @@ def test_wigner_background_term():
 
 # ------------------------------------------------------------------ Ewald invariants
 def test_alpha_independence_direct():
-    """The total energy does not depend on alpha (Sec. 2.4.2, L551)."""
+    """The total energy does not depend on alpha (Sec. 2.4.2)."""
     d = W.nacl()
     Es = []
     for a, rc, nm in [(0.3, 20.0, 14), (0.4, 15.0, 19), (0.5, 12.0, 24)]:
@@ -193,7 +193,7 @@ def test_phi_is_dE_dq_direct_and_nfft():
 
 
 def test_net_force_zero_and_translation():
-    """Sum of forces vanishes (momentum conservation, L39) and the energy is
+    """Sum of forces vanishes (the momentum conservation the abstract claims) and the energy is
     translation invariant; O2 is exactly invariant under shifts by whole grid
     cells h = L/M (Eq. 18)."""
     d = W.nacl()

@@ -23,7 +23,10 @@ Sec. 4) are not public data, so these generators stand in for their shapes:
 The Ewald parameter alpha recorded for the polyelectrolyte and ionic-liquid
 workloads is the value that balances the two truncation errors for the given
 r_c and n_c, r_c = pi n_c / (alpha^2 L) (Eq. 32), rounded to four digits; the
-RPM values are stated at ``rpm`` and ``rpm_1e4``.
+RPM values are stated at ``rpm`` and ``rpm_1e4``.  ``rpm_1e4`` and
+``polyelectrolyte_1e4`` are the same systems with the smallest parameter
+changes that meet a 1e-4 relative RMS force error; the ionic-liquid settings
+meet their 1e-5 target as they are.
 """
 from __future__ import annotations
 
@@ -129,6 +132,22 @@ def polyelectrolyte(n_beads=1048576, chain=50, density=0.85, bond=0.97, seed=3, 
     pos = np.mod(pos, L)
     return dict(name="polyelectrolyte", pos=pos, q=q, L=np.full(3, L), alpha=alpha, r_c=r_c, M=M, p=p,
                 n_c=M // 4, precision="mixed", seed=seed, n_beads=n_beads)
+
+
+def polyelectrolyte_1e4(**kw):
+    """The polyelectrolyte system with the smallest changes that meet a 1e-4
+    relative RMS force error against converged Ewald (grid 256^3 unchanged):
+    the stated p = 6 window and r_c = 3 sigma give about 7e-4 (the window and
+    the real-space truncation both exceed the target), p = 8 with r_c = 4.3
+    sigma and alpha = 0.70 give about 6e-5 (measured with the oracle on
+    1/8- and 1/64-volume copies of the system at the same density and grid
+    spacing)."""
+    kw.setdefault("p", 8)
+    kw.setdefault("r_c", 4.3)
+    kw.setdefault("alpha", 0.70)
+    d = polyelectrolyte(**kw)
+    d["name"] = "polyelectrolyte_1e-4"
+    return d
 
 
 def ionic_liquid(N=8388608, density=0.1, n_centres=1_000_000, blob=2.0, seed=4, M=512, p=8,
