@@ -302,6 +302,43 @@ def profile_kernels(P, plan_kw, fn_of_plan, flush, reps=3):
     return acc
 
 
+FFT_KERNELS = ("fft_xy", "fft_x", "fft_y", "fft_z_kspace", "ifft_yx", "ifft_y", "ifft_x")
+
+
+def cufft_chain_ms(M, dev, timed):
+    """cuFFT (through torch.fft) doing the transforms an unpruned ENUF step
+    needs -- one real-to-complex 3D FFT of the M^3 grid and three
+    complex-to-real inverse FFTs of the force-field spectra -- timed the same
+    way as the library's chain.  A comparison only: the library never calls
+    cuFFT."""
+    import torch
+    g = torch.randn((M, M, M), device=dev, dtype=torch.float32)
+    out = [torch.empty((M, M, M), device=dev, dtype=torch.float32) for _ in range(3)]
+
+    def run():
+        S = torch.fft.rfftn(g)
+        for f in range(3):
+            out[f].copy_(torch.fft.irfftn(S, s=(M, M, M)))
+
+    ms, _ = timed(run, 10, 3)
+    del g, out
+    torch.cuda.empty_cache()
+    return ms
+
+
+def fft_comparison(acc, M, dev, timed):
+    """The library's pruned FFT chain (forward x-y, the z pass with the fused
+    reciprocal-space step and inverse z, inverse y-x; per-kernel event times)
+    beside cuFFT's R2C + 3 C2R of the same grid."""
+    hand = sum(v for k, v in acc.items() if k in FFT_KERNELS)
+    try:
+        cu = cufft_chain_ms(M, dev, timed)
+    except Exception as e:  # report, do not lose the headline line
+        return {"hand_fft_chain_ms": hand, "error": str(e)[:200]}
+    return {"hand_fft_chain_ms": round(hand, 5), "cufft_r2c_3c2r_ms": round(cu, 5),
+            "cufft_over_hand": round(cu / hand, 3) if hand > 0 else None}
+
+
 def large_systems(P, dev, timed, kspace, flush, peak):
     """k-space E+F of the polyelectrolyte (N = 1,572,864, grid 256^3; the
     stated p = 6 settings and the 1e-4 settings) and ionic-liquid (N =
@@ -327,6 +364,8 @@ def large_systems(P, dev, timed, kspace, flush, peak):
             acc = profile_kernels(P, dict(precision="mixed", **kw), lambda pl: kspace(pl, tp, tq, F, out), flush)
             r["kernel_ms"] = {k: round(v, 5) for k, v in acc.items()}
             r["kernel_roofline"] = kernel_rooflines(acc, N, d["M"], d["n_c"], 3, peak)
+            if name != "polyelectrolyte_1e4":  # same grid as the stated settings
+                r["fft_vs_cufft"] = fft_comparison(acc, d["M"], dev, timed)
             r["kspace_algorithmic_bytes"] = 28 * N + 32 * d["M"] ** 3
             r["kspace_hbm_frac"] = r["kspace_algorithmic_bytes"] / (ms * 1e-3) / 1e9 / peak
             if name.startswith("polyelectrolyte"):
@@ -495,6 +534,8 @@ def main():
         torch.cuda.synchronize()
         del pplan
         extra["kernel_ms"] = {k: round(v, 5) for k, v in acc.items()}
+        extra["kernel_roofline"] = kernel_rooflines(acc, N, M, nc, 3, measured_peaks()[0])
+        extra["fft_vs_cufft"] = fft_comparison(acc, M, dev, timed)
         # the named p = 6 settings of the same system, for reference
         if args.workload == "rpm_1e4":
             d6 = workload("rpm", seed_offset=rank)

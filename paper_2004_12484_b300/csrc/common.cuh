@@ -106,7 +106,69 @@ template <typename R> __device__ __forceinline__ R warp_sum(R v)
 enum : int {
     ST_NONFINITE = 1,  // a non-finite position or charge was seen
     ST_WORKLIST = 2,   // the bin work list overflowed its bound (internal error)
+    ST_TIMEOUT = 4,    // a bounded wait for asynchronous copies gave up (internal error)
 };
+
+// ------------------------------------------------------------------ bulk copies
+// Copies by the TMA engine from global to shared memory, completed on an
+// mbarrier in the CTA's shared memory: non-tensor ("bulk") copies of a
+// multiple of 16 bytes between 16-byte aligned addresses, and boxes of a
+// tensor described by a tensor map.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    // make the initialised barrier visible to the asynchronous proxy
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One arrival that also announces `bytes` of transactions still to come.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// One box of a 4-dimensional tensor (tile mode) from global to shared memory
+// through the tensor map at `tmap` (a __grid_constant__ kernel parameter);
+// coordinates are element indices, innermost first, and may lie outside the
+// tensor (those elements are filled with zeros).  The destination must be
+// 128-byte aligned.
+__device__ __forceinline__ void tma_load_4d(void* dst, const void* tmap, int c0, int c1, int c2, int c3, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Waits for the barrier's phase `parity` to complete, giving up after
+// `limit` polls (each poll may suspend the thread for a while); returns
+// whether the phase completed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit)
+{
+    const uint32_t a = smem_addr(bar);
+    for (int i = 0; i < limit; i++) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
 
 // Block reduction of NV values per thread.  Each warp sums in type R, the
 // warp totals are added in double; threads 0..NV-1 write out[0..NV).

@@ -12,7 +12,9 @@
 //   gather                             interpolation, F = q E (a7)
 //   real-space sort + pair kernel      erfc sum (a8)
 //   finalize                           FP64 assembly of E and the virial (a9)
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -339,6 +341,9 @@ struct enuf_plan {
     bool use_graph = true;
     bool profile = false;
     bool pdl = true;  // programmatic dependent launch along the chain (ENUF_NO_PDL=1 turns it off)
+    bool legacy_gather = false;  // ENUF_LEGACY_GATHER=1: the generic interpolation kernel for p = 8 as well
+    bool gather_p8 = false;      // k_gather_p8 serves the interpolation (its tensor map is set)
+    CUtensorMap fld_tmap;        // the field planes, for the TMA boxes of k_gather_p8
     bool attrs_done = false;
     std::vector<GraphEntry> graphs;
     // one time step of the harness (enuf_md_run) as a graph, for one set of
@@ -470,6 +475,22 @@ int launch_gather_t(Launcher& L, enuf_plan* pl, int nf, R* F, R* phi)
                     at<const R>(pl, y.fld), F, phi);
     }
     using RecT = typename Rec<R>::T;
+    if constexpr (T == 16 && P == 8 && sizeof(R) == 4) {
+        if (pl->gather_p8) {
+            // p = 8 in single precision: boxes staged by the TMA engine,
+            // z-accumulated window rows
+            int* st = at<int>(pl, y.status);
+            if (nf == 4)
+                return L.go("gather", k_gather_p8<4>, dim3(r.max_work), dim3(512), GatherP8<4>::SMEM,
+                            at<const int4>(pl, y.work), at<const int>(pl, y.nwork), at<const f4>(pl, y.rec),
+                            at<const uint32_t>(pl, y.perm), r.prm.M, pl->lnb, winc<float>(pl), (float)pl->cnorm3,
+                            at<const float>(pl, y.fld), pl->fld_tmap, (float*)F, (float*)phi, st);
+            return L.go("gather", k_gather_p8<3>, dim3(r.max_work), dim3(512), GatherP8<3>::SMEM,
+                        at<const int4>(pl, y.work), at<const int>(pl, y.nwork), at<const f4>(pl, y.rec),
+                        at<const uint32_t>(pl, y.perm), r.prm.M, pl->lnb, winc<float>(pl), (float)pl->cnorm3,
+                        at<const float>(pl, y.fld), pl->fld_tmap, (float*)F, (float*)phi, st);
+        }
+    }
     if constexpr (T == 16) {
         if (r.zhalf) {
             // z-halves of the tiles, 512 threads: two CTAs (three-field boxes
@@ -973,10 +994,44 @@ void drop_graphs(enuf_plan* pl)
     pl->md.exec = nullptr;
 }
 
+// Tensor map of the four field planes (x, y, z, field) for the TMA boxes of
+// k_gather_p8: boxes of BX x PT x PZ x 1 cells, no swizzle, zeros outside.
+int encode_field_map(enuf_plan* pl)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            return fail(ENUF_ECUDA, "the driver does not provide cuTensorMapEncodeTiled");
+        }
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    using B = Box<8, 16, 8>;
+    const cuuint64_t M = (cuuint64_t)pl->r.prm.M;
+    const cuuint64_t dims[4] = {M, M, M, 4};
+    const cuuint64_t strides[3] = {M * 4, M * M * 4, M * M * M * 4};
+    const cuuint32_t box[4] = {(cuuint32_t)B::BX, (cuuint32_t)B::PT, (cuuint32_t)B::PZ, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult rc = encode(&pl->fld_tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, pl->ws + pl->lay.fld, dims, strides,
+                               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (rc != CUDA_SUCCESS) return fail(ENUF_ECUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string((int)rc));
+    return ENUF_OK;
+}
+
 int bind_workspace(enuf_plan* pl, void* ptr)
 {
     drop_graphs(pl);
     pl->ws = (char*)ptr;
+    // the p = 8 single-precision interpolation on z-halves of 16-cell tiles
+    // stages its boxes through a tensor map of this workspace's field planes
+    const Resolved& r = pl->r;
+    pl->gather_p8 = !r.fp64 && r.T == 16 && r.zhalf && r.prm.p == 8 && r.prm.M >= 32 && r.gcap == 256 &&
+                    !r.gather_direct && !pl->legacy_gather;
+    if (pl->gather_p8) LCHK(encode_field_map(pl));
     // the status word and the bin counts start (and are kept) zeroed
     CK(cudaMemset(pl->ws, 0, pl->lay.total));
     LCHK(upload_tables(pl));
@@ -1197,6 +1252,8 @@ int enuf_plan_create(const enuf_params* params, void* cuda_stream, int allocate,
     pl->profile = ev && ev[0] == '1';
     ev = std::getenv("ENUF_NO_PDL");
     pl->pdl = !(ev && ev[0] == '1');
+    ev = std::getenv("ENUF_LEGACY_GATHER");
+    pl->legacy_gather = ev && ev[0] == '1';
     if (pl->profile) {
         pl->tevents.resize(48);
         for (auto& x : pl->tevents) cudaEventCreate(&x);

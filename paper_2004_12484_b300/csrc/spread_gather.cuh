@@ -21,6 +21,8 @@
 // or writes p consecutive cells of one grid row per step; the partial sums
 // are combined with shuffles.
 #pragma once
+#include <cuda.h>  // CUtensorMap
+
 #include "common.cuh"
 
 namespace enuf {
@@ -449,6 +451,124 @@ __global__ void __launch_bounds__(NTH) k_gather(const int4* __restrict__ work, c
 
     interp_unit<R, P, T, NF, ZS>(s, s + NF * C + (threadIdx.x >> 5) * WyzTable<P>::N, srec, w.z - w.y, z0, wc,
                                  cnorm3, F, phi, [&](int k) { return sperm[k]; });
+}
+
+// Interpolation for windows of p = 8 on 16-cell tiles in z-halves, single
+// precision (the configuration of the large workloads and the benchmark).
+// Staging: one thread has the TMA engine copy the unit's box of each field
+// plane (a tensor-map box of BX x PT x PZ cells) and the unit's particle
+// records into shared memory, completing on an mbarrier; cells of a box that
+// crosses the edge of the periodic grid arrive as zeros and are then filled
+// from their periodic images by the threads (16-byte loads of whole aligned
+// groups of four cells).  Compute: one warp per particle, lane (g, a) =
+// (lane / 8, lane % 8) takes x offset a of rows g and g + 4 and all eight
+// planes, and sums each of its two rows along z with the z weights before
+// applying the x and y weights, so a window point costs one shared load and
+// one FMA per field.  Needs M >= 32 (a box crosses each edge at most once).
+template <int NF> struct GatherP8 {
+    using B = Box<8, 16, 8>;
+    static constexpr int CP = (B::CELLS + 31) / 32 * 32;  // field stride in shared memory, 128-byte aligned
+    static constexpr int CAP = 256;                        // particles per work item
+    static constexpr size_t SMEM = (size_t)NF * CP * 4 + CAP * sizeof(f4) + 16;
+};
+
+template <int NF>
+__global__ void __launch_bounds__(512, 2) k_gather_p8(const int4* __restrict__ work, const int* __restrict__ nwork,
+                                                      const f4* __restrict__ rec, const uint32_t* __restrict__ perm,
+                                                      int M, int lnb, WinC<float> wc, float cnorm3,
+                                                      const float* __restrict__ fld,
+                                                      const __grid_constant__ CUtensorMap tmap, float* __restrict__ F,
+                                                      float* __restrict__ phi, int* __restrict__ status)
+{
+    using G8 = GatherP8<NF>;
+    using B = typename G8::B;
+    constexpr int PT = B::PT, PZ = B::PZ, BX = B::BX, C = G8::CP, XOFF = B::XOFF;
+    extern __shared__ __align__(128) unsigned char smraw_g8[];
+    float* s = reinterpret_cast<float*>(smraw_g8);
+    f4* srec = reinterpret_cast<f4*>(s + NF * C);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(srec + G8::CAP);
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    pdl_wait();
+    if ((int)blockIdx.x >= *nwork) return;  // uniform for the whole CTA
+    const int4 w = work[blockIdx.x];
+    const int n = w.z - w.y;                 // 1..CAP (the scan splits larger units)
+    const int tile = w.x >> 1, z0 = (w.x & 1) * 8;
+    const int nbm = (1 << lnb) - 1;
+    const int tx = tile & nbm, ty = (tile >> lnb) & nbm, tz = tile >> (2 * lnb);
+    const int ox = tx * 16 - B::XA, oy = ty * 16 - 3, oz = tz * 16 + z0 - 3;
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(bar, (uint32_t)(NF * B::CELLS * 4 + n * 16));
+#pragma unroll
+        for (int f = 0; f < NF; f++) tma_load_4d(s + f * C, &tmap, ox, oy, oz, f, bar);
+        bulk_g2s(srec, rec + w.y, (uint32_t)n * 16u, bar);
+    }
+    if (!mbar_wait(bar, 0, 1 << 22)) {
+        // should not happen: report, and wait (bounded) for the copies still
+        // writing this CTA's shared memory before leaving
+        if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+        mbar_wait(bar, 0, 1 << 22);
+        return;
+    }
+    if (ox < 0 || ox + BX > M || oy < 0 || oy + PT > M || oz < 0 || oz + PZ > M) {
+        // the box crosses the grid's edge: its outside cells came as zeros
+        const int mask = M - 1;
+        const size_t M3 = (size_t)M * M * M;
+        constexpr int NV = BX / 4;
+        for (int i = threadIdx.x; i < NV * PT * PZ; i += 512) {
+            const int vx = i % NV, ly = (i / NV) % PT, lz = i / (NV * PT);
+            const int gx = ox + 4 * vx, gy = oy + ly, gz = oz + lz;
+            if (gx >= 0 && gx < M && gy >= 0 && gy < M && gz >= 0 && gz < M) continue;
+            const size_t gi = ((size_t)(gz & mask) * M + (gy & mask)) * M + (gx & mask);
+            const int si = (lz * PT + ly) * BX + 4 * vx;
+#pragma unroll
+            for (int f = 0; f < NF; f++)
+                *reinterpret_cast<float4*>(s + f * C + si) = __ldg(reinterpret_cast<const float4*>(fld + f * M3 + gi));
+        }
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 3, a = lane & 7;
+    for (int k = warp; k < n; k += 16) {
+        const f4 r = srec[k];
+        int ix, iy, iz;
+        float dx, dy, dz;
+        split_offset<float, 16>(r.x, ix, dx);
+        split_offset<float, 16>(r.y, iy, dy);
+        split_offset<float, 16>(r.z, iz, dz);
+        iz -= z0;
+        const float ux = dx + (float)(3 - a), uy = dy + (float)(3 - a);
+        const float wx = win_exp(ux * ux, wc), wya = win_exp(uy * uy, wc);
+        float wz[8];
+        window_weights<float, 8>(dz, wc, wz);
+        const float wy0 = __shfl_sync(0xffffffffu, wya, g), wy1 = __shfl_sync(0xffffffffu, wya, g + 4);
+        const float* base = s + (iz * PT + iy + g) * BX + ix + XOFF + a;
+        float s0[NF], s1[NF];
+#pragma unroll
+        for (int f = 0; f < NF; f++) s0[f] = s1[f] = 0.f;
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+#pragma unroll
+            for (int f = 0; f < NF; f++) {
+                s0[f] = fmaf(wz[c], base[f * C + c * PT * BX], s0[f]);
+                s1[f] = fmaf(wz[c], base[f * C + c * PT * BX + 4 * BX], s1[f]);
+            }
+        }
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int f = 0; f < NF; f++) acc[f] = wx * fmaf(wy0, s0[f], wy1 * s1[f]);
+        // lane 8 f holds the total of field f
+        const float tot = warp_sum4(acc, lane);
+        if ((lane & 7) == 0) {
+            const int f = lane >> 3;
+            const uint32_t oi = perm[w.y + k];
+            if (f < 3) {
+                if (F) F[3 * (size_t)oi + f] = r.w * cnorm3 * tot;
+            } else if (NF == 4 && phi) {
+                phi[oi] = cnorm3 * tot;
+            }
+        }
+    }
 }
 
 // Interpolation for the analytic-differentiation forces: one real potential

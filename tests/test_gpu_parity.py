@@ -394,10 +394,10 @@ def test_positions_on_cell_and_box_boundaries(precision):
 
 @pytest.mark.parametrize("p", [2, 4, 6, 8])
 def test_persistent_interpolation_forces_only(p, monkeypatch):
-    """Forces without the potential take the persistent double-buffered
-    interpolation kernel when the tiles have 16 cells: a random system and a
-    heavy tile on a 32^3 grid, and the benchmark's workload at full size
-    (the launch configuration the benchmark times), against the oracle."""
+    """Forces without the potential on 16-cell tiles (for p = 8 the
+    interpolation with z-accumulated window rows): a random system
+    with wrapping and a heavy tile cut into several work items on a 32^3
+    grid, against the oracle."""
     monkeypatch.setenv("ENUF_TILE", "16")
     g = np.random.default_rng(60 + p)
     L = np.array([22.0, 25.0, 27.0])
@@ -438,11 +438,13 @@ def test_plan_call_returns_energy_forces_virial():
 
 
 @pytest.mark.parametrize("env", [{"ENUF_TILE": "16", "ENUF_GATHER_FULL_TILE": "1"}, {"ENUF_FZ_W": "16"},
-                                 {"ENUF_NO_PDL": "1"}, {"ENUF_NO_GRAPH": "1"}])
+                                 {"ENUF_NO_PDL": "1"}, {"ENUF_NO_GRAPH": "1"},
+                                 {"ENUF_TILE": "16", "ENUF_LEGACY_GATHER": "1"}])
 def test_alternative_launch_configurations(env, monkeypatch):
     """The plan-creation switches that select other launch configurations
     (whole 16-cell interpolation tiles, another z-pass width, no
-    programmatic dependent launch, direct launches instead of graphs) give
+    programmatic dependent launch, direct launches instead of graphs, the
+    generic interpolation kernel for p = 8 instead of its own) give
     the same results: forces only and with the potential, against the
     oracle."""
     for k, v in env.items():
