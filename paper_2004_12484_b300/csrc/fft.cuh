@@ -172,6 +172,87 @@ __device__ __forceinline__ void fft_smem_multi(V* x, int trs, int t, const V* __
     FftPasses<V, N, 1, INV, NTR, MR>::run(x, trs, t, W, ws);
 }
 
+// ---------------------------------------------------------------- register passes
+// The same Stockham passes with the data of the first pass taken from, and
+// the results of the last pass left in, registers: thread t of the NT
+// threads serving a transform holds v[m] = x[t + NT m] (m < E = N / NT) on
+// entry and v[m] = X[t + NT m] on exit, so a transform loaded from and
+// stored to global memory directly touches shared memory only between
+// passes (passes - 1 exchanges through the transform's buffer at x, PadLen
+// slots).  NTR transforms (buffers x + q trs) per thread, as in
+// stockham_pass.  All threads of the CTA must call it (it contains
+// barriers).
+template <typename V, int N, int Ns, bool INV, int NTR, int MR> struct RegPasses {
+    static constexpr int R = (MR >= 8 && Ns * 8 <= N) ? 8 : ((Ns * 4 <= N) ? 4 : 2);
+    static constexpr int NT = FftThreads<N, MR>::NT;
+    static constexpr int NB = N / R, PER = NB / NT, E = N / NT;
+    // v[q][m]: element m of transform q (m = b + PER r for butterfly b, leg r)
+    static __device__ __forceinline__ void run(V (&v)[NTR][E], V* x, int trs, int t, const V* __restrict__ W, int ws)
+    {
+#pragma unroll
+        for (int b = 0; b < PER; b++) {
+            const int j = t + b * NT;
+            const int k = j & (Ns - 1);
+            V tw[R];
+            if (Ns > 1) {
+#pragma unroll
+                for (int r = 1; r < R; r++) {
+                    tw[r] = W[(r * k * (N / (Ns * R))) * ws];
+                    if (INV) tw[r].y = -tw[r].y;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < NTR; q++) {
+                V u[R];
+#pragma unroll
+                for (int r = 0; r < R; r++) u[r] = v[q][b + PER * r];
+                if (Ns > 1) {
+#pragma unroll
+                    for (int r = 1; r < R; r++) u[r] = cmul(u[r], tw[r]);
+                }
+                dftR<V, R, INV>(u);
+#pragma unroll
+                for (int r = 0; r < R; r++) v[q][b + PER * r] = u[r];
+            }
+        }
+        if constexpr (Ns * R < N) {
+            // exchange: results to their autosort positions, then the next
+            // pass's inputs x[j + r N / R'] into the same register slots
+            using Next = RegPasses<V, N, Ns * R, INV, NTR, MR>;
+#pragma unroll
+            for (int b = 0; b < PER; b++) {
+                const int j = t + b * NT;
+                const int k = j & (Ns - 1);
+                const int d = (j - k) * R + k;
+#pragma unroll
+                for (int q = 0; q < NTR; q++) {
+#pragma unroll
+                    for (int r = 0; r < R; r++) x[q * trs + pidx(d + r * Ns)] = v[q][b + PER * r];
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int b = 0; b < Next::PER; b++) {
+                const int j = t + b * NT;
+#pragma unroll
+                for (int q = 0; q < NTR; q++) {
+#pragma unroll
+                    for (int r = 0; r < Next::R; r++) v[q][b + Next::PER * r] = x[q * trs + pidx(j + r * Next::NB)];
+                }
+            }
+            __syncthreads();
+            Next::run(v, x, trs, t, W, ws);
+        }
+    }
+};
+
+template <typename V, int N, bool INV, int MR = 8>
+__device__ __forceinline__ void fft_reg(V (&v)[1][N / FftThreads<N, MR>::NT], V* x, int t, const V* __restrict__ W,
+                                        int ws)
+{
+    RegPasses<V, N, 1, INV, 1, MR>::run(v, x, 0, t, W, ws);
+}
+
 // Copies the twiddle table exp(-2 pi i k / M), k < M, into shared memory
 // (asynchronously: complete after the kernel's next cp_async_wait_all and
 // barrier).
@@ -195,37 +276,47 @@ struct FftGeom {
 
 // ---------------------------------------------------------------- k_fx
 // grid: ceil(M*M / rows) blocks, rows * NT(M/2) threads.  Clears the grid
-// rows it reads (the spreading accumulates into a zeroed grid).
+// rows it reads (the spreading accumulates into a zeroed grid).  Thread t of
+// a row loads the packed pairs z_j = x_{2j} + i x_{2j+1}, j = t + NT m,
+// straight from the grid row, transforms with register passes, and the
+// even/odd split X_k = (Z_k + conj Z_{M/2-k})/2 - i/2 e^{-2 pi i k/M}
+// (Z_k - conj Z_{M/2-k}) of the kept kx <= n_c reads the partners from
+// shared memory.
 template <typename R, int M>
 __global__ void __launch_bounds__(256) k_fx(R* __restrict__ grid, typename Cpx<R>::T* __restrict__ C1, FftGeom g,
                      const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
-    constexpr int MH = M / 2, NT = FftThreads<MH>::NT, RS = PadLen<MH>::V;
+    constexpr int MH = M / 2, NT = FftThreads<MH>::NT, RS = PadLen<MH>::V, E = MH / NT;
     extern __shared__ __align__(16) unsigned char smraw[];
     V* s = reinterpret_cast<V*>(smraw);
     const int rows = g.rows, row0 = blockIdx.x * rows, nrows = M * M;
     const V* sW = stage_twiddles(s + rows * RS, Wg, M);
-    V* gin = reinterpret_cast<V*>(grid);
-    for (int i = threadIdx.x; i < rows * MH; i += blockDim.x) {
-        const int r = i / MH, j = i % MH, row = row0 + r;
-        cp_async_cpx(s + r * RS + pidx(j), gin + (row < nrows ? (size_t)row * MH + j : 0), row < nrows);
-    }
+    const int r = threadIdx.x / NT, t = threadIdx.x % NT, row = row0 + r;
+    const bool live = row < nrows;
+    V* gin = reinterpret_cast<V*>(grid) + (size_t)(live ? row : 0) * MH;
+    V v[1][E];
+#pragma unroll
+    for (int m = 0; m < E; m++) v[0][m] = live ? gin[t + NT * m] : V{R(0), R(0)};
     cp_async_wait_all();
-    // the grid is left zeroed for the next spreading (each element was read
-    // by the thread that clears it)
-    for (int i = threadIdx.x; i < rows * MH; i += blockDim.x) {
-        const int r = i / MH, j = i % MH, row = row0 + r;
-        if (row < nrows) gin[(size_t)row * MH + j] = V{R(0), R(0)};
-    }
     __syncthreads();
-    fft_smem<V, MH, false>(s + (threadIdx.x / NT) * RS, threadIdx.x % NT, sW, 2);
+    V* x = s + r * RS;
+    fft_reg<V, MH, false>(v, x, t, sW, 2);
+    // the grid is left zeroed for the next spreading (each element is
+    // cleared by the thread that read it, once its value is in use: a
+    // store right behind the load of the same address waits for it)
+    if (live) {
+#pragma unroll
+        for (int m = 0; m < E; m++) gin[t + NT * m] = V{R(0), R(0)};
+    }
+#pragma unroll
+    for (int m = 0; m < E; m++) x[pidx(t + NT * m)] = v[0][m];
+    __syncthreads();
+    if (!live) return;
     const int Kx = g.Kx;
-    for (int i = threadIdx.x; i < rows * Kx; i += blockDim.x) {
-        const int r = (int)g.fKx.div(i), k = i - r * Kx, row = row0 + r;
-        if (row >= nrows) continue;
-        const V zk = s[r * RS + pidx(k % MH)];
-        const V zc = cconj(s[r * RS + pidx((MH - k) % MH)]);
+    for (int k = t; k < Kx; k += NT) {
+        const V zk = x[pidx(k % MH)];
+        const V zc = cconj(x[pidx((MH - k) % MH)]);
         const V fe = V{R(0.5) * (zk.x + zc.x), R(0.5) * (zk.y + zc.y)};
         const V d = csub(zk, zc);
         const V fo = V{R(0.5) * d.y, R(-0.5) * d.x};  // -i/2 (zk - zc)
@@ -295,30 +386,36 @@ __global__ void __launch_bounds__(1024) k_fxy(R* __restrict__ grid, typename Cpx
 }
 
 // ---------------------------------------------------------------- k_fy
-// grid: (ceil(Kx / W), M) blocks, W * NT(M) threads.
+// grid: (ceil(Kx / W), M) blocks, W * NT(M) threads.  Thread (w, t) = (tid %
+// W, tid / W) serves column kx0 + w: loads y = t + NT m straight from C1,
+// register passes, stores the band rows to C2.
 template <typename R, int M>
 __global__ void __launch_bounds__(1024) k_fy(const typename Cpx<R>::T* __restrict__ C1, typename Cpx<R>::T* __restrict__ C2, FftGeom g,
                      const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
-    constexpr int NT = FftThreads<M>::NT, LD = PadLen<M>::V + 1;
+    constexpr int NT = FftThreads<M>::NT, LD = PadLen<M>::V + 1, E = M / NT;
     extern __shared__ __align__(16) unsigned char smraw[];
     V* s = reinterpret_cast<V*>(smraw);
     const int Wc = g.W, Kx = g.Kx, Kb = g.Kb, nc = g.nc;
     const int kx0 = blockIdx.x * Wc, z = blockIdx.y;
     const V* sW = stage_twiddles(s + Wc * LD, Wg, M);
-    for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
-        const int y = (int)g.fW.div(i), w = i - y * Wc, kx = kx0 + w;
-        cp_async_cpx(s + w * LD + pidx(y), C1 + (kx < Kx ? ((size_t)z * M + y) * Kx + kx : 0), kx < Kx);
-    }
+    const int t = (int)g.fW.div(threadIdx.x), w = threadIdx.x - t * Wc, kx = kx0 + w;
+    V v[1][E];
+#pragma unroll
+    for (int m = 0; m < E; m++)
+        v[0][m] = kx < Kx ? C1[((size_t)z * M + t + NT * m) * Kx + kx] : V{R(0), R(0)};
     cp_async_wait_all();
     __syncthreads();
-    fft_smem<V, M, false>(s + (threadIdx.x / NT) * LD, threadIdx.x % NT, sW, 1);
-    for (int i = threadIdx.x; i < Wc * Kb; i += blockDim.x) {
-        const int kb = (int)g.fW.div(i), w = i - kb * Wc, kx = kx0 + w;
-        if (kx >= Kx) continue;
-        const int ky = kb <= nc ? kb : M - Kb + kb;
-        C2[((size_t)z * Kb + kb) * Kx + kx] = s[w * LD + pidx(ky)];
+    fft_reg<V, M, false>(v, s + w * LD, t, sW, 1);
+    if (kx >= Kx) return;
+#pragma unroll
+    for (int m = 0; m < E; m++) {
+        const int ky = t + NT * m;
+        int kb = -1;
+        if (ky <= nc) kb = ky;
+        else if (ky >= M - nc) kb = ky - (M - Kb);
+        if (kb >= 0) C2[((size_t)z * Kb + kb) * Kx + kx] = v[0][m];
     }
 }
 
@@ -350,7 +447,7 @@ __global__ void __launch_bounds__(512) k_fz(const typename Cpx<R>::T* __restrict
     using V = typename Cpx<R>::T;
     // radix-4 passes: twice the threads of the radix-8 kernels, for more
     // parallelism in this small kernel
-    constexpr int MR = 4, NT = FftThreads<M, MR>::NT, LD = PadLen<M>::V + 1, NB = NF > 0 ? NF : 1;
+    constexpr int MR = 4, NT = FftThreads<M, MR>::NT, LD = PadLen<M>::V + 1, NB = NF > 0 ? NF : 1, E = M / NT;
     extern __shared__ __align__(16) unsigned char smraw[];
     V* X = reinterpret_cast<V*>(smraw);
     const int Wc = g.W, Kx = g.Kx, Kb = g.Kb, nc = g.nc, P = g.P;
@@ -368,66 +465,74 @@ __global__ void __launch_bounds__(512) k_fz(const typename Cpx<R>::T* __restrict
     const R* te = stab + 3 * Kb;
     const R* td = stab + 6 * Kb;
     pdl_wait();
+    // thread (w, t) = (tid % W, tid / W) serves pencil p0 + w, elements
+    // z = t + NT m (neighbouring threads read neighbouring pencils)
     const int p0 = blockIdx.x * Wc;
-    for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
-        const int z = (int)g.fW.div(i), w = i - z * Wc, p = p0 + w;
-        cp_async_cpx(X + w * LD + pidx(z), C2 + (p < P ? (size_t)z * P + p : 0), p < P);
-    }
+    const int t = (int)g.fW.div(threadIdx.x), w = threadIdx.x - t * Wc, p = p0 + w;
+    V v[1][E];
+#pragma unroll
+    for (int m = 0; m < E; m++) v[0][m] = p < P ? C2[(size_t)(t + NT * m) * P + p] : V{R(0), R(0)};
     cp_async_wait_all();
     __syncthreads();
-    fft_smem<V, M, false, MR>(X + (threadIdx.x / NT) * LD, threadIdx.x % NT, sW, 1);
+    fft_reg<V, M, false, MR>(v, X + w * LD, t, sW, 1);
 
     // scaling, energy / virial, subdivided field spectra
     R acc[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
-    for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
-        const int w = i / M, z = i % M, p = p0 + w;
-        V val = V{R(0), R(0)};
-        R kxv = R(0), kyv = R(0), kzv = R(0);
+    V fv[NB][E];
+    int nx = 0, ny = 0;
+    bool pv = false;
+    if (p < P) {
+        const int kb = (int)g.fKx.div(p);
+        nx = p - kb * Kx;
+        ny = kb <= nc ? kb : kb - Kb;
+        pv = true;
+    }
+    const R kxv = pv ? tk[nx + nc] : R(0), kyv = pv ? tk[Kb + ny + nc] : R(0);
+    const R exy = pv ? te[nx + nc] * te[Kb + ny + nc] : R(0), dxy = pv ? td[nx + nc] * td[Kb + ny + nc] : R(0);
+#pragma unroll
+    for (int m = 0; m < E; m++) {
+        const int z = t + NT * m;
         const int nz = z <= nc ? z : (z >= M - nc ? z - M : (1 << 20));
-        if (p < P && nz != (1 << 20)) {
-            const int kb = (int)g.fKx.div(p), kx = p - kb * Kx;
-            const int nx = kx, ny = kb <= nc ? kb : kb - Kb;
-            if (nx != 0 || ny != 0 || nz != 0) {
-                kxv = tk[nx + nc];
-                kyv = tk[Kb + ny + nc];
-                kzv = tk[2 * Kb + nz + nc];
-                const R k2 = kxv * kxv + kyv * kyv + kzv * kzv;
-                const R G = te[nx + nc] * te[Kb + ny + nc] * te[2 * Kb + nz + nc] / k2;
-                const R D2 = td[nx + nc] * td[Kb + ny + nc] * td[2 * Kb + nz + nc];
-                const V gh = X[w * LD + pidx(z)];
-                const R s2 = D2 * (gh.x * gh.x + gh.y * gh.y);  // |S(n)|^2
-                const R e = (nx == 0 ? R(1) : R(2)) * ktg.cE * G * s2;
-                const R c = R(2) * (R(1) / k2 + ktg.inv4a2);
-                acc[0] += e;
-                acc[1] += e * (R(1) - c * kxv * kxv);
-                acc[2] += e * (R(1) - c * kyv * kyv);
-                acc[3] += e * (R(1) - c * kzv * kzv);
-                acc[4] -= e * c * kxv * kyv;
-                acc[5] -= e * c * kxv * kzv;
-                acc[6] -= e * c * kyv * kzv;
-                const R f = ktg.cF * G * D2;
-                val = V{f * gh.x, f * gh.y};
-            }
+        V val = V{R(0), R(0)};
+        R kzv = R(0);
+        if (pv && nz != (1 << 20) && (nx != 0 || ny != 0 || nz != 0)) {
+            kzv = tk[2 * Kb + nz + nc];
+            const R k2 = kxv * kxv + kyv * kyv + kzv * kzv;
+            const R G = exy * te[2 * Kb + nz + nc] / k2;
+            const R D2 = dxy * td[2 * Kb + nz + nc];
+            const V gh = v[0][m];
+            const R s2 = D2 * (gh.x * gh.x + gh.y * gh.y);  // |S(n)|^2
+            const R e = (nx == 0 ? R(1) : R(2)) * ktg.cE * G * s2;
+            const R c = R(2) * (R(1) / k2 + ktg.inv4a2);
+            acc[0] += e;
+            acc[1] += e * (R(1) - c * kxv * kxv);
+            acc[2] += e * (R(1) - c * kyv * kyv);
+            acc[3] += e * (R(1) - c * kzv * kzv);
+            acc[4] -= e * c * kxv * kyv;
+            acc[5] -= e * c * kxv * kzv;
+            acc[6] -= e * c * kyv * kzv;
+            const R f = ktg.cF * G * D2;
+            val = V{f * gh.x, f * gh.y};
         }
         if (NF == 1) {
             // the potential alone (forces by analytic differentiation)
-            X[w * LD + pidx(z)] = val;
+            fv[0][m] = val;
         } else if (NF > 0) {
             // -i k_t val for the three field components, val for the potential
-            X[w * LD + pidx(z)] = V{kxv * val.y, -kxv * val.x};
-            if (NF > 1) X[FS + w * LD + pidx(z)] = V{kyv * val.y, -kyv * val.x};
-            if (NF > 2) X[2 * FS + w * LD + pidx(z)] = V{kzv * val.y, -kzv * val.x};
-            if (NF > 3) X[3 * FS + w * LD + pidx(z)] = val;
+            fv[0][m] = V{kxv * val.y, -kxv * val.x};
+            if (NF > 1) fv[1 % NB][m] = V{kyv * val.y, -kyv * val.x};
+            if (NF > 2) fv[2 % NB][m] = V{kzv * val.y, -kzv * val.x};
+            if (NF > 3) fv[3 % NB][m] = val;
         }
     }
     block_reduce_to_double<R, 7>(acc, part + 8 * (size_t)blockIdx.x, red);
     if (NF == 0) return;
-    fft_smem_multi<V, M, true, NB, MR>(X + (threadIdx.x / NT) * LD, FS, threadIdx.x % NT, sW, 1);
-    for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
-        const int z = (int)g.fW.div(i), w = i - z * Wc, p = p0 + w;
-        if (p < P) {
+    RegPasses<V, M, 1, true, NB, MR>::run(fv, X + w * LD, FS, t, sW, 1);
+    if (p < P) {
 #pragma unroll
-            for (int f = 0; f < NB; f++) C3[((size_t)f * M + z) * P + p] = X[f * FS + w * LD + pidx(z)];
+        for (int f = 0; f < NB; f++) {
+#pragma unroll
+            for (int m = 0; m < E; m++) C3[((size_t)f * M + t + NT * m) * P + p] = fv[f][m];
         }
     }
 }
@@ -477,35 +582,41 @@ __global__ void __launch_bounds__(512) k_fz_spectrum(const typename Cpx<R>::T* _
 }
 
 // ---------------------------------------------------------------- k_iy
-// grid: (ceil(Kx / W), M, NF) blocks, W * NT(M) threads.
+// grid: (ceil(Kx / W), M, NF) blocks, W * NT(M) threads.  Thread (w, t) =
+// (tid % W, tid / W) serves column kx0 + w: it loads its band elements
+// y = t + NT m straight from C3 (neighbouring threads read neighbouring
+// columns), transforms with register passes and stores its outputs to C4.
 template <typename R, int M>
 __global__ void __launch_bounds__(1024) k_iy(const typename Cpx<R>::T* __restrict__ C3, typename Cpx<R>::T* __restrict__ C4, FftGeom g,
                      const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
-    constexpr int NT = FftThreads<M>::NT, LD = PadLen<M>::V + 1;
+    constexpr int NT = FftThreads<M>::NT, LD = PadLen<M>::V + 1, E = M / NT;
     extern __shared__ __align__(16) unsigned char smraw[];
     V* s = reinterpret_cast<V*>(smraw);
     const int Wc = g.W, Kx = g.Kx, Kb = g.Kb, nc = g.nc, P = g.P;
     const int kx0 = blockIdx.x * Wc, z = blockIdx.y, f = blockIdx.z;
     const V* W = stage_twiddles(s + Wc * LD, Wg, M);
+    const int t = (int)g.fW.div(threadIdx.x), w = threadIdx.x - t * Wc, kx = kx0 + w;
     const V* src = C3 + ((size_t)f * M + z) * P;
-    for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
-        const int y = (int)g.fW.div(i), w = i - y * Wc, kx = kx0 + w;
+    V v[1][E];
+#pragma unroll
+    for (int m = 0; m < E; m++) {
+        const int y = t + NT * m;
         int kb = -1;
         if (kx < Kx) {
             if (y <= nc) kb = y;
             else if (y >= M - nc) kb = y - (M - Kb);
         }
-        cp_async_cpx(s + w * LD + pidx(y), src + (kb >= 0 ? (size_t)kb * Kx + kx : 0), kb >= 0);
+        v[0][m] = kb >= 0 ? src[(size_t)kb * Kx + kx] : V{R(0), R(0)};
     }
     cp_async_wait_all();
     __syncthreads();
-    fft_smem<V, M, true>(s + (threadIdx.x / NT) * LD, threadIdx.x % NT, W, 1);
-    V* dst = C4 + ((size_t)f * M + z) * M * Kx;
-    for (int i = threadIdx.x; i < Wc * M; i += blockDim.x) {
-        const int y = (int)g.fW.div(i), w = i - y * Wc, kx = kx0 + w;
-        if (kx < Kx) dst[(size_t)y * Kx + kx] = s[w * LD + pidx(y)];
+    fft_reg<V, M, true>(v, s + w * LD, t, W, 1);
+    if (kx < Kx) {
+        V* dst = C4 + ((size_t)f * M + z) * M * Kx + kx;
+#pragma unroll
+        for (int m = 0; m < E; m++) dst[(size_t)(t + NT * m) * Kx] = v[0][m];
     }
 }
 
@@ -582,39 +693,42 @@ __global__ void __launch_bounds__(IyxBounds<R, M>::T, IyxBounds<R, M>::B) k_iyx(
 // ---------------------------------------------------------------- k_ix
 // grid: ceil(NF*M*M / rows) blocks, rows * NT(M/2) threads.  Complex-to-real
 // rows: X_k (k = 0..n_c, zero above) -> x_j = sum_k X_k e^{2 pi i k j/M} over
-// the Hermitian-completed spectrum.
+// the Hermitian-completed spectrum, as a half-length complex transform of
+// z_k = (X_k + conj X_{M/2-k}) + i e^{2 pi i k / M} (X_k - conj X_{M/2-k})
+// whose outputs are the packed pairs (x_{2j}, x_{2j+1}).  Thread t of a row
+// forms its inputs z_{t + NT m} from the row in global memory, transforms
+// with register passes and stores its outputs straight to the field row.
 template <typename R, int M>
 __global__ void __launch_bounds__(256) k_ix(const typename Cpx<R>::T* __restrict__ C4, R* __restrict__ fld, FftGeom g, int nrows,
                      const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
-    constexpr int MH = M / 2, NT = FftThreads<MH>::NT, RS = PadLen<MH>::V;
+    constexpr int MH = M / 2, NT = FftThreads<MH>::NT, RS = PadLen<MH>::V, E = MH / NT;
     extern __shared__ __align__(16) unsigned char smraw[];
     V* s = reinterpret_cast<V*>(smraw);
     const int rows = g.rows, row0 = blockIdx.x * rows, Kx = g.Kx, nc = g.nc;
     const V* W = stage_twiddles(s + rows * RS, Wg, M);
     cp_async_wait_all();
     __syncthreads();
-    for (int i = threadIdx.x; i < rows * MH; i += blockDim.x) {
-        const int r = i / MH, k = i % MH, row = row0 + r;
-        V z = V{R(0), R(0)};
-        if (row < nrows) {
-            const V* src = C4 + (size_t)row * Kx;
-            const V a = k <= nc ? src[k] : V{R(0), R(0)};
-            const int kb = MH - k;
-            const V b = kb <= nc ? cconj(src[kb]) : V{R(0), R(0)};
-            const V fe = cadd(a, b);
-            const V fo = cmul(csub(a, b), cconj(W[k]));  // (a - b) e^{+2 pi i k / M}
-            z = V{fe.x - fo.y, fe.y + fo.x};             // fe + i fo
-        }
-        s[r * RS + pidx(k)] = z;
+    const int r = threadIdx.x / NT, t = threadIdx.x % NT, row = row0 + r;
+    const bool live = row < nrows;
+    const V* src = C4 + (size_t)(live ? row : 0) * Kx;
+    V v[1][E];
+#pragma unroll
+    for (int m = 0; m < E; m++) {
+        const int k = t + NT * m;
+        const V a = (live && k <= nc) ? src[k] : V{R(0), R(0)};
+        const int kb = MH - k;
+        const V b = (live && kb <= nc) ? cconj(src[kb]) : V{R(0), R(0)};
+        const V fe = cadd(a, b);
+        const V fo = cmul(csub(a, b), cconj(W[k]));  // (a - b) e^{+2 pi i k / M}
+        v[0][m] = V{fe.x - fo.y, fe.y + fo.x};       // fe + i fo
     }
-    __syncthreads();
-    fft_smem<V, MH, true>(s + (threadIdx.x / NT) * RS, threadIdx.x % NT, W, 2);
-    V* out = reinterpret_cast<V*>(fld);
-    for (int i = threadIdx.x; i < rows * MH; i += blockDim.x) {
-        const int r = i / MH, j = i % MH, row = row0 + r;
-        if (row < nrows) out[(size_t)row * MH + j] = s[r * RS + pidx(j)];
+    fft_reg<V, MH, true>(v, s + r * RS, t, W, 2);
+    if (live) {
+        V* out = reinterpret_cast<V*>(fld) + (size_t)row * MH;
+#pragma unroll
+        for (int m = 0; m < E; m++) out[t + NT * m] = v[0][m];
     }
 }
 
