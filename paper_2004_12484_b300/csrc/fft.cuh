@@ -326,17 +326,19 @@ __global__ void __launch_bounds__(256) k_fx(R* __restrict__ grid, typename Cpx<R
 
 // ---------------------------------------------------------------- k_fxy
 // Fused forward x and y passes for grids whose pruned plane fits in shared
-// memory: one CTA per z-plane (grid: M blocks, 1024 threads).  Clears the
-// grid plane it reads (the spreading accumulates into a zeroed grid).  The x-rows are
-// transformed in batches, the kept kx columns are stored transposed in a
-// plane buffer, transformed along y, and the band rows written to C2.
+// memory: one CTA per z-plane (grid: M blocks, CB * NT(M) threads, CB
+// columns per batch).  Clears the grid plane it reads (the spreading
+// accumulates into a zeroed grid).  The x-rows are transformed in batches
+// (loaded straight into registers), their kept kx columns stored transposed
+// in a plane buffer, transformed along y (thread (w, t) = (tid % CB, tid /
+// CB) on column k0 + w) and the band rows stored to C2 from registers.
 template <typename R, int M>
 __global__ void __launch_bounds__(1024) k_fxy(R* __restrict__ grid, typename Cpx<R>::T* __restrict__ C2,
                                               FftGeom g, const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
     constexpr int MH = M / 2, NTX = FftThreads<MH>::NT, NTY = FftThreads<M>::NT, LD = PadLen<M>::V + 1;
-    constexpr int RS = PadLen<MH>::V;
+    constexpr int RS = PadLen<MH>::V, EX = MH / NTX, EY = M / NTY;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int Kx = g.Kx, Kb = g.Kb, nc = g.nc;
     const int RB = blockDim.x / NTX;  // rows per batch
@@ -348,40 +350,59 @@ __global__ void __launch_bounds__(1024) k_fxy(R* __restrict__ grid, typename Cpx
     pdl_wait();
     const int z = blockIdx.x;
     V* gin = reinterpret_cast<V*>(grid + (size_t)z * M * M);
+    const int r = threadIdx.x / NTX, tx = threadIdx.x % NTX;
+    cp_async_wait_all();
+    __syncthreads();
     for (int y0 = 0; y0 < M; y0 += RB) {
-        for (int i = threadIdx.x; i < RB * MH; i += blockDim.x) {
-            const int r = i / MH, j = i % MH, y = y0 + r;
-            cp_async_cpx(rowbuf + r * RS + pidx(j), gin + (y < M ? (size_t)y * MH + j : 0), y < M);
+        const int y = y0 + r;
+        const bool live = y < M;
+        V* row = gin + (size_t)(live ? y : 0) * MH;
+        V v[1][EX];
+#pragma unroll
+        for (int m = 0; m < EX; m++) v[0][m] = live ? row[tx + NTX * m] : V{R(0), R(0)};
+        V* x = rowbuf + r * RS;
+        fft_reg<V, MH, false>(v, x, tx, sW, 2);
+        // the grid is left zeroed for the next spreading (each element is
+        // cleared by the thread that read it, once its value is in use)
+        if (live) {
+#pragma unroll
+            for (int m = 0; m < EX; m++) row[tx + NTX * m] = V{R(0), R(0)};
         }
-        cp_async_wait_all();
-        // the grid is left zeroed for the next spreading (each element was
-        // read by the thread that clears it)
-        for (int i = threadIdx.x; i < RB * MH; i += blockDim.x) {
-            const int r = i / MH, j = i % MH, y = y0 + r;
-            if (y < M) gin[(size_t)y * MH + j] = V{R(0), R(0)};
-        }
+#pragma unroll
+        for (int m = 0; m < EX; m++) x[pidx(tx + NTX * m)] = v[0][m];
         __syncthreads();
-        fft_smem<V, MH, false>(rowbuf + (threadIdx.x / NTX) * RS, threadIdx.x % NTX, sW, 2);
-        for (int i = threadIdx.x; i < RB * Kx; i += blockDim.x) {
-            const int r = (int)g.fKx.div(i), k = i - r * Kx, y = y0 + r;
-            if (y >= M) continue;
-            const V zk = rowbuf[r * RS + pidx(k % MH)];
-            const V zc = cconj(rowbuf[r * RS + pidx((MH - k) % MH)]);
-            const V fe = V{R(0.5) * (zk.x + zc.x), R(0.5) * (zk.y + zc.y)};
-            const V d = csub(zk, zc);
-            const V fo = V{R(0.5) * d.y, R(-0.5) * d.x};
-            plane[k * LD + pidx(y)] = cadd(fe, cmul(sW[k], fo));
+        if (live) {
+            for (int k = tx; k < Kx; k += NTX) {
+                const V zk = x[pidx(k % MH)];
+                const V zc = cconj(x[pidx((MH - k) % MH)]);
+                const V fe = V{R(0.5) * (zk.x + zc.x), R(0.5) * (zk.y + zc.y)};
+                const V d = csub(zk, zc);
+                const V fo = V{R(0.5) * d.y, R(-0.5) * d.x};
+                plane[k * LD + pidx(y)] = cadd(fe, cmul(sW[k], fo));
+            }
         }
         __syncthreads();
     }
-    for (int k0 = 0; k0 < Kx; k0 += CB) {
-        fft_smem<V, M, false>(plane + (k0 + threadIdx.x / NTY) * LD, threadIdx.x % NTY, sW, 1);
-    }
+    const int ty = threadIdx.x / CB, w = threadIdx.x - ty * CB;  // ty < NT(M): blockDim = CB NT(M)
     V* dst = C2 + (size_t)z * Kb * Kx;
-    for (int i = threadIdx.x; i < Kb * Kx; i += blockDim.x) {
-        const int kb = (int)g.fKx.div(i), kx = i - kb * Kx;
-        const int ky = kb <= nc ? kb : M - Kb + kb;
-        dst[i] = plane[kx * LD + pidx(ky)];
+    for (int k0 = 0; k0 < Kx; k0 += CB) {
+        const int kx = k0 + w;
+        V* col = plane + kx * LD;
+        V v[1][EY];
+#pragma unroll
+        for (int m = 0; m < EY; m++) v[0][m] = col[pidx(ty + NTY * m)];
+        __syncthreads();
+        fft_reg<V, M, false>(v, col, ty, sW, 1);
+        if (kx < Kx) {
+#pragma unroll
+            for (int m = 0; m < EY; m++) {
+                const int ky = ty + NTY * m;
+                int kb = -1;
+                if (ky <= nc) kb = ky;
+                else if (ky >= M - nc) kb = ky - (M - Kb);
+                if (kb >= 0) dst[(size_t)kb * Kx + kx] = v[0][m];
+            }
+        }
     }
 }
 
@@ -638,7 +659,7 @@ __global__ void __launch_bounds__(IyxBounds<R, M>::T, IyxBounds<R, M>::B) k_iyx(
 {
     using V = typename Cpx<R>::T;
     constexpr int MH = M / 2, NTX = FftThreads<MH>::NT, NTY = FftThreads<M>::NT, LD = PadLen<M>::V + 1;
-    constexpr int RS = PadLen<MH>::V;
+    constexpr int RS = PadLen<MH>::V, EX = MH / NTX, EY = M / NTY;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int Kx = g.Kx, Kb = g.Kb, nc = g.nc, P = g.P;
     const int RB = blockDim.x / NTX;
@@ -651,42 +672,55 @@ __global__ void __launch_bounds__(IyxBounds<R, M>::T, IyxBounds<R, M>::B) k_iyx(
     pdl_wait();
     const int z = blockIdx.x, f = blockIdx.y;
     const V* src = C3 + ((size_t)f * M + z) * P;
-    for (int i = threadIdx.x; i < KxR * M; i += blockDim.x) {
-        const int y = (int)g.fKxR.div(i), kx = i - y * KxR;  // consecutive threads read consecutive kx
-        int kb = -1;
-        if (kx < Kx) {
-            if (y <= nc) kb = y;
-            else if (y >= M - nc) kb = y - (M - Kb);
-        }
-        cp_async_cpx(plane + kx * LD + pidx(y), src + (kb >= 0 ? (size_t)kb * Kx + kx : 0), kb >= 0);
-    }
+    // inverse y: thread (w, t) = (tid % CB, tid / CB) on column k0 + w loads
+    // its band elements y = t + NT m straight from C3 (neighbouring threads
+    // read neighbouring kx)
+    const int ty = threadIdx.x / CB, w = threadIdx.x - ty * CB;  // ty < NT(M): blockDim = CB NT(M)
     cp_async_wait_all();
     __syncthreads();
     for (int k0 = 0; k0 < Kx; k0 += CB) {
-        fft_smem<V, M, true>(plane + (k0 + threadIdx.x / NTY) * LD, threadIdx.x % NTY, sW, 1);
-    }
-    V* out = reinterpret_cast<V*>(fld + ((size_t)f * M + z) * M * M);
-    for (int y0 = 0; y0 < M; y0 += RB) {
-        for (int i = threadIdx.x; i < RB * MH; i += blockDim.x) {
-            const int r = i / MH, k = i % MH, y = y0 + r;
-            V zz = V{R(0), R(0)};
-            if (y < M) {
-                const V a = k <= nc ? plane[k * LD + pidx(y)] : V{R(0), R(0)};
-                const int kb = MH - k;
-                const V b = kb <= nc ? cconj(plane[kb * LD + pidx(y)]) : V{R(0), R(0)};
-                const V fe = cadd(a, b);
-                const V fo = cmul(csub(a, b), cconj(sW[k]));
-                zz = V{fe.x - fo.y, fe.y + fo.x};
+        const int kx = k0 + w;
+        V v[1][EY];
+#pragma unroll
+        for (int m = 0; m < EY; m++) {
+            const int y = ty + NTY * m;
+            int kb = -1;
+            if (kx < Kx) {
+                if (y <= nc) kb = y;
+                else if (y >= M - nc) kb = y - (M - Kb);
             }
-            rowbuf[r * RS + pidx(k)] = zz;
+            v[0][m] = kb >= 0 ? src[(size_t)kb * Kx + kx] : V{R(0), R(0)};
         }
-        __syncthreads();
-        fft_smem<V, MH, true>(rowbuf + (threadIdx.x / NTX) * RS, threadIdx.x % NTX, sW, 2);
-        for (int i = threadIdx.x; i < RB * MH; i += blockDim.x) {
-            const int r = i / MH, j = i % MH, y = y0 + r;
-            if (y < M) out[(size_t)y * MH + j] = rowbuf[r * RS + pidx(j)];
+        V* col = plane + kx * LD;
+        fft_reg<V, M, true>(v, col, ty, sW, 1);
+#pragma unroll
+        for (int m = 0; m < EY; m++) col[pidx(ty + NTY * m)] = v[0][m];
+    }
+    __syncthreads();
+    // complex-to-real x per row: thread t of row r forms its inputs from the
+    // plane and stores its outputs straight to the field row
+    V* out = reinterpret_cast<V*>(fld + ((size_t)f * M + z) * M * M);
+    const int r = threadIdx.x / NTX, tx = threadIdx.x % NTX;
+    for (int y0 = 0; y0 < M; y0 += RB) {
+        const int y = y0 + r;
+        const bool live = y < M;
+        const int yy = live ? y : 0;
+        V v[1][EX];
+#pragma unroll
+        for (int m = 0; m < EX; m++) {
+            const int k = tx + NTX * m;
+            const V a = k <= nc ? plane[k * LD + pidx(yy)] : V{R(0), R(0)};
+            const int kb = MH - k;
+            const V b = kb <= nc ? cconj(plane[kb * LD + pidx(yy)]) : V{R(0), R(0)};
+            const V fe = cadd(a, b);
+            const V fo = cmul(csub(a, b), cconj(sW[k]));
+            v[0][m] = V{fe.x - fo.y, fe.y + fo.x};
         }
-        __syncthreads();
+        fft_reg<V, MH, true>(v, rowbuf + r * RS, tx, sW, 2);
+        if (live) {
+#pragma unroll
+            for (int m = 0; m < EX; m++) out[(size_t)y * MH + tx + NTX * m] = v[0][m];
+        }
     }
 }
 
