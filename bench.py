@@ -263,7 +263,7 @@ def reference_arm(args):
 LARGE_ERRORS = {
     "polyelectrolyte": "7e-4 (p = 6 window and r_c = 3 sigma; tests/test_gpu_accuracy_large.py)",
     "polyelectrolyte_1e4": "<= 1e-4 target, about 6e-5 (tests/test_gpu_accuracy_large.py)",
-    "ionic_liquid": "<= 1e-5 target, about 5e-6 (tests/test_gpu_accuracy_large.py)",
+    "ionic_liquid": "<= 1e-5 target (tests/test_gpu_accuracy_large.py)",
 }
 
 
