@@ -511,7 +511,9 @@ __global__ void __launch_bounds__(512, 2) k_gather_p8(const int4* __restrict__ w
         return;
     }
     if (ox < 0 || ox + BX > M || oy < 0 || oy + PT > M || oz < 0 || oz + PZ > M) {
-        // the box crosses the grid's edge: its outside cells came as zeros
+        // the box crosses the grid's edge: its outside cells came as zeros;
+        // copy them from their periodic images (asynchronous 16-byte copies,
+        // all in flight before the wait)
         const int mask = M - 1;
         const size_t M3 = (size_t)M * M * M;
         constexpr int NV = BX / 4;
@@ -522,9 +524,9 @@ __global__ void __launch_bounds__(512, 2) k_gather_p8(const int4* __restrict__ w
             const size_t gi = ((size_t)(gz & mask) * M + (gy & mask)) * M + (gx & mask);
             const int si = (lz * PT + ly) * BX + 4 * vx;
 #pragma unroll
-            for (int f = 0; f < NF; f++)
-                *reinterpret_cast<float4*>(s + f * C + si) = __ldg(reinterpret_cast<const float4*>(fld + f * M3 + gi));
+            for (int f = 0; f < NF; f++) cp_async_bytes16(s + f * C + si, fld + f * M3 + gi, true);
         }
+        cp_async_wait_all();
         __syncthreads();
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
