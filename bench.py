@@ -651,10 +651,28 @@ def main():
             t0 = time.perf_counter()
             plan.energy_forces_host(ph, qh, F_host=Fh, kspace_only=True)
             t_e2e.append(time.perf_counter() - t0)
+        # the host link alone: the same copies (positions and charges in,
+        # forces and the results out), event-timed on the stream
+        dp, dq_, dF = torch.empty_like(tp), torch.empty_like(tq), torch.empty_like(F)
+        oh = torch.empty(16, dtype=torch.float64).pin_memory()
+        t_link = []
+        for k in range(23):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            dp.copy_(ph, non_blocking=True)
+            dq_.copy_(qh, non_blocking=True)
+            Fh.copy_(dF, non_blocking=True)
+            oh.copy_(out, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k >= 3:
+                t_link.append(e0.elapsed_time(e1))
+        link_ms = float(np.median(t_link))
         e2e = {"value": N / float(np.mean(t_e2e)) / 1e6, "unit": UNIT, "h2d_bytes_per_step": 16 * N,
                "d2h_bytes_per_step": 12 * N + 16 * 8, "ms_per_step": float(np.mean(t_e2e)) * 1e3,
                "ms_median": float(np.median(t_e2e)) * 1e3, "ms_min": float(np.min(t_e2e)) * 1e3,
-               "calls": len(t_e2e)}
+               "calls": len(t_e2e), "link_ms_per_step": link_ms, "device_ms_per_step": ms,
+               "over_device_plus_link": float(np.median(t_e2e)) * 1e3 / (ms + link_ms)}
         # ---- oracle on the host cores
         cv, cores, runs, el = time_oracle(d)
         cpu = {"value": cv, "unit": UNIT, "cores": cores, "kind": "oracle",
