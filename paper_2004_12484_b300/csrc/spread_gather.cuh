@@ -532,6 +532,8 @@ __global__ void __launch_bounds__(512, 2) k_gather_p8(const int4* __restrict__ w
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 3, a = lane & 7;
     for (int k = warp; k < n; k += 16) {
+        // the output index is needed last: its load runs under the window sums
+        const uint32_t oi = perm[w.y + k];
         const f4 r = srec[k];
         int ix, iy, iz;
         float dx, dy, dz;
@@ -563,7 +565,6 @@ __global__ void __launch_bounds__(512, 2) k_gather_p8(const int4* __restrict__ w
         const float tot = warp_sum4(acc, lane);
         if ((lane & 7) == 0) {
             const int f = lane >> 3;
-            const uint32_t oi = perm[w.y + k];
             if (f < 3) {
                 if (F) F[3 * (size_t)oi + f] = r.w * cnorm3 * tot;
             } else if (NF == 4 && phi) {
