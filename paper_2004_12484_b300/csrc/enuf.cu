@@ -343,8 +343,6 @@ struct enuf_plan {
     bool pdl = true;  // programmatic dependent launch along the chain (ENUF_NO_PDL=1 turns it off)
     bool legacy_gather = false;  // ENUF_LEGACY_GATHER=1: the generic interpolation kernel for p = 8 as well
     bool gather_p8 = false;      // k_gather_p8 serves the interpolation (its tensor map is set)
-    bool gather_single = false;  // ENUF_GATHER_SINGLE=1: forces-only p = 8 interpolation without the pipeline
-    int nsm = 148;               // multiprocessors of the plan's device
     CUtensorMap fld_tmap;        // the field planes, for the TMA boxes of k_gather_p8
     bool attrs_done = false;
     std::vector<GraphEntry> graphs;
@@ -482,17 +480,6 @@ int launch_gather_t(Launcher& L, enuf_plan* pl, int nf, R* F, R* phi)
             // p = 8 in single precision: boxes staged by the TMA engine,
             // z-accumulated window rows
             int* st = at<int>(pl, y.status);
-            if (nf == 3 && !pl->gather_single) {
-                // forces only: the persistent two-stage pipeline, one CTA per
-                // multiprocessor
-                constexpr int NWC = 16;
-                const int grid = std::max(1, std::min(pl->nsm, r.max_work));
-                return L.go("gather", k_gather_p8_pipe<NWC>, dim3(grid), dim3(32 * (NWC + 1)),
-                            GatherP8Pipe<NWC>::SMEM, at<const int4>(pl, y.work), at<const int>(pl, y.nwork),
-                            at<const f4>(pl, y.rec), at<const uint32_t>(pl, y.perm), r.prm.M, pl->lnb,
-                            winc<float>(pl), (float)pl->cnorm3, at<const float>(pl, y.fld), pl->fld_tmap, (float*)F,
-                            st);
-            }
             if (nf == 4)
                 return L.go("gather", k_gather_p8<4>, dim3(r.max_work), dim3(512), GatherP8<4>::SMEM,
                             at<const int4>(pl, y.work), at<const int>(pl, y.nwork), at<const f4>(pl, y.rec),
@@ -1267,15 +1254,6 @@ int enuf_plan_create(const enuf_params* params, void* cuda_stream, int allocate,
     pl->pdl = !(ev && ev[0] == '1');
     ev = std::getenv("ENUF_LEGACY_GATHER");
     pl->legacy_gather = ev && ev[0] == '1';
-    ev = std::getenv("ENUF_GATHER_SINGLE");
-    pl->gather_single = ev && ev[0] == '1';
-    {
-        int dev = 0, nsm = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
-            pl->nsm = nsm;
-        cudaGetLastError();
-    }
     if (pl->profile) {
         pl->tevents.resize(48);
         for (auto& x : pl->tevents) cudaEventCreate(&x);

@@ -574,143 +574,6 @@ __global__ void __launch_bounds__(512, 2) k_gather_p8(const int4* __restrict__ w
     }
 }
 
-// The p = 8 interpolation of k_gather_p8 (forces only, three fields) as a
-// persistent kernel with one CTA per multiprocessor: a producer warp has the
-// TMA engine fill two shared-memory stages in turn (box and records of the
-// CTA's next unit, completing on the stage's "full" mbarrier) while NWC
-// consumer warps interpolate the other stage and release it on its "empty"
-// mbarrier (one arrival per warp).  So a unit's copy is hidden behind the
-// previous unit's interpolation, and no warp waits for the others between
-// units (except to share the patching of boxes that cross the grid's edge,
-// on a barrier of the consumer warps only).
-template <int NWC>
-struct GatherP8Pipe {
-    using G = GatherP8<3>;
-    static constexpr int STAGE = 3 * G::CP * 4 + G::CAP * (int)sizeof(f4);  // bytes of a stage (128-byte multiple)
-    static constexpr size_t SMEM = 2 * (size_t)STAGE + 64;
-};
-
-template <int NWC>
-__global__ void __launch_bounds__(32 * (NWC + 1), 1) k_gather_p8_pipe(
-    const int4* __restrict__ work, const int* __restrict__ nwork, const f4* __restrict__ rec,
-    const uint32_t* __restrict__ perm, int M, int lnb, WinC<float> wc, float cnorm3, const float* __restrict__ fld,
-    const __grid_constant__ CUtensorMap tmap, float* __restrict__ F, int* __restrict__ status)
-{
-    using G = GatherP8<3>;
-    using B = typename G::B;
-    using PP = GatherP8Pipe<NWC>;
-    constexpr int NF = 3, PT = B::PT, PZ = B::PZ, BX = B::BX, C = G::CP, XOFF = B::XOFF;
-    constexpr int LIMIT = 1 << 22;
-    extern __shared__ __align__(128) unsigned char smraw_gp[];
-    uint64_t* full = reinterpret_cast<uint64_t*>(smraw_gp + 2 * PP::STAGE);
-    uint64_t* empty = full + 2;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) {
-        mbar_init(&full[0], 1);
-        mbar_init(&full[1], 1);
-        mbar_init(&empty[0], NWC);
-        mbar_init(&empty[1], NWC);
-    }
-    __syncthreads();
-    pdl_wait();
-    const int nw = *nwork;
-    const int nbm = (1 << lnb) - 1;
-    if (warp == NWC) {
-        // producer
-        if (lane != 0) return;
-        for (int it = 0;; it++) {
-            const int u = blockIdx.x + it * gridDim.x;
-            if (u >= nw) break;
-            const int b = it & 1;
-            if (it >= 2 && !mbar_wait(&empty[b], ((it - 2) >> 1) & 1, LIMIT)) {
-                atomicOr(status, ST_TIMEOUT);
-                break;
-            }
-            const int4 w = work[u];
-            const int tile = w.x >> 1, z0 = (w.x & 1) * 8;
-            const int tx = tile & nbm, ty = (tile >> lnb) & nbm, tz = tile >> (2 * lnb);
-            float* s = reinterpret_cast<float*>(smraw_gp + b * PP::STAGE);
-            mbar_arrive_expect_tx(&full[b], (uint32_t)(NF * B::CELLS * 4 + (w.z - w.y) * 16));
-#pragma unroll
-            for (int f = 0; f < NF; f++) tma_load_4d(s + f * C, &tmap, tx * 16 - B::XA, ty * 16 - 3, tz * 16 + z0 - 3, f, &full[b]);
-            bulk_g2s(s + NF * C, rec + w.y, (uint32_t)(w.z - w.y) * 16u, &full[b]);
-        }
-        return;
-    }
-    // consumers
-    const int g = lane >> 3, a = lane & 7;
-    for (int it = 0;; it++) {
-        const int u = blockIdx.x + it * gridDim.x;
-        if (u >= nw) break;
-        const int b = it & 1;
-        if (!mbar_wait(&full[b], (it >> 1) & 1, LIMIT)) {
-            if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
-            mbar_wait(&full[b], (it >> 1) & 1, LIMIT);  // the copy may still be writing this stage
-            return;
-        }
-        float* s = reinterpret_cast<float*>(smraw_gp + b * PP::STAGE);
-        const f4* srec = reinterpret_cast<const f4*>(s + NF * C);
-        const int4 w = work[u];
-        const int n = w.z - w.y;
-        const int tile = w.x >> 1, z0 = (w.x & 1) * 8;
-        const int tx = tile & nbm, ty = (tile >> lnb) & nbm, tz = tile >> (2 * lnb);
-        const int ox = tx * 16 - B::XA, oy = ty * 16 - 3, oz = tz * 16 + z0 - 3;
-        if (ox < 0 || ox + BX > M || oy < 0 || oy + PT > M || oz < 0 || oz + PZ > M) {
-            // cells outside the grid came as zeros: copy their periodic images
-            const int mask = M - 1;
-            const size_t M3 = (size_t)M * M * M;
-            constexpr int NV = BX / 4;
-            for (int i = threadIdx.x; i < NV * PT * PZ; i += 32 * NWC) {
-                const int vx = i % NV, ly = (i / NV) % PT, lz = i / (NV * PT);
-                const int gx = ox + 4 * vx, gy = oy + ly, gz = oz + lz;
-                if (gx >= 0 && gx < M && gy >= 0 && gy < M && gz >= 0 && gz < M) continue;
-                const size_t gi = ((size_t)(gz & mask) * M + (gy & mask)) * M + (gx & mask);
-                const int si = (lz * PT + ly) * BX + 4 * vx;
-#pragma unroll
-                for (int f = 0; f < NF; f++) cp_async_bytes16(s + f * C + si, fld + f * M3 + gi, true);
-            }
-            cp_async_wait_all();
-            // these generic writes precede the stage's next TMA fill
-            fence_proxy_async_smem();
-            asm volatile("bar.sync 1, %0;" ::"r"(32 * NWC) : "memory");
-        }
-        for (int k = warp; k < n; k += NWC) {
-            const uint32_t oi = perm[w.y + k];
-            const f4 r = srec[k];
-            int ix, iy, iz;
-            float dx, dy, dz;
-            split_offset<float, 16>(r.x, ix, dx);
-            split_offset<float, 16>(r.y, iy, dy);
-            split_offset<float, 16>(r.z, iz, dz);
-            iz -= z0;
-            const float ux = dx + (float)(3 - a), uy = dy + (float)(3 - a);
-            const float wx = win_exp(ux * ux, wc), wya = win_exp(uy * uy, wc);
-            float wz[8];
-            window_weights<float, 8>(dz, wc, wz);
-            const float wy0 = __shfl_sync(0xffffffffu, wya, g), wy1 = __shfl_sync(0xffffffffu, wya, g + 4);
-            const float* base = s + (iz * PT + iy + g) * BX + ix + XOFF + a;
-            float s0[NF], s1[NF];
-#pragma unroll
-            for (int f = 0; f < NF; f++) s0[f] = s1[f] = 0.f;
-#pragma unroll
-            for (int c = 0; c < 8; c++) {
-#pragma unroll
-                for (int f = 0; f < NF; f++) {
-                    s0[f] = fmaf(wz[c], base[f * C + c * PT * BX], s0[f]);
-                    s1[f] = fmaf(wz[c], base[f * C + c * PT * BX + 4 * BX], s1[f]);
-                }
-            }
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int f = 0; f < NF; f++) acc[f] = wx * fmaf(wy0, s0[f], wy1 * s1[f]);
-            const float tot = warp_sum4(acc, lane);
-            if ((lane & 7) == 0 && lane < 24 && F) F[3 * (size_t)oi + (lane >> 3)] = r.w * cnorm3 * tot;
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[b]);
-    }
-}
-
 // Interpolation for the analytic-differentiation forces: one real potential
 // grid A (plane of M^3) and, per particle, the window sum of A together with
 // the three sums weighted by the window's derivative, d phi/du = -(2u/b) phi

@@ -439,14 +439,12 @@ def test_plan_call_returns_energy_forces_virial():
 
 @pytest.mark.parametrize("env", [{"ENUF_TILE": "16", "ENUF_GATHER_FULL_TILE": "1"}, {"ENUF_FZ_W": "16"},
                                  {"ENUF_NO_PDL": "1"}, {"ENUF_NO_GRAPH": "1"},
-                                 {"ENUF_TILE": "16", "ENUF_LEGACY_GATHER": "1"},
-                                 {"ENUF_TILE": "16", "ENUF_GATHER_SINGLE": "1"}])
+                                 {"ENUF_TILE": "16", "ENUF_LEGACY_GATHER": "1"}])
 def test_alternative_launch_configurations(env, monkeypatch):
     """The plan-creation switches that select other launch configurations
     (whole 16-cell interpolation tiles, another z-pass width, no
     programmatic dependent launch, direct launches instead of graphs, the
-    generic interpolation kernel for p = 8 instead of its own, the p = 8
-    forces-only interpolation without its copy pipeline) give
+    generic interpolation kernel for p = 8 instead of its own) give
     the same results: forces only and with the potential, against the
     oracle."""
     for k, v in env.items():
