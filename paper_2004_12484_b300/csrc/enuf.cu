@@ -83,9 +83,12 @@ struct Resolved {
     int fxy_threads;  // > 0: fused x-y kernels with this block size
     size_t fxy_smem;
     bool gather_direct;  // interpolate straight from L2-resident field planes
+    bool fz_wide;        // the z pass is k_fzw (M = 512)
 };
 
 int ffthreads(int n) { return n >= 8 ? n / 8 : 1; }
+// threads per row of the x-row kernels k_fx, k_ix (radix RowMR of fft.cuh)
+int rowthreads(int mh) { return mh == 256 ? mh / 16 : ffthreads(mh); }
 // slots of one transform of length n in shared memory (PadLen in fft.cuh)
 int padlen(int n) { return n + n / 16; }
 
@@ -165,7 +168,7 @@ int resolve(const enuf_params* in, Resolved& r)
     const size_t vsz = 2 * r.rsz;
     const int M = p.M;
     // k_fx / k_ix rows per block
-    r.gfx = FftGeom{r.nc, r.Kx, r.Kb, r.P, 0, 256 / ffthreads(M / 2)};
+    r.gfx = FftGeom{r.nc, r.Kx, r.Kb, r.P, 0, 256 / rowthreads(M / 2)};
     const int NT = ffthreads(M), gran = std::max(1, 32 / NT);
     auto round_up = [](int v, int g) { return (v + g - 1) / g * g; };
     // k_fy / k_iy: columns per block, about 16 but balanced over Kx
@@ -176,6 +179,12 @@ int resolve(const enuf_params* in, Resolved& r)
         while ((size_t)(W * (padlen(M) + 1) + M) * vsz > (size_t)kMaxSmem) W -= gran;
         r.gy = FftGeom{r.nc, r.Kx, r.Kb, r.P, W, 0};
     }
+    // k_fzw for M = 512: 16 pencils a CTA of 16 M/8 threads (8 in double
+    // precision), one buffer per pencil
+    r.fz_wide = M >= 512 && !std::getenv("ENUF_FZ_NARROW");
+    if (r.fz_wide) {
+        r.gz = FftGeom{r.nc, r.Kx, r.Kb, r.P, r.fp64 ? 8 : 16, 0};
+    } else
     // k_fz: pencils per block (at most 512 threads: the batched inverse
     // transforms of four fields need up to 128 registers per thread); its
     // passes use radix 4, so M/4 threads serve one pencil
@@ -615,7 +624,7 @@ int launch_fft_chain_m(Launcher& L, enuf_plan* pl, int nf, void* spec = nullptr,
     }
     // forward x
     if (!fused) {
-        const int NT = ffthreads(M / 2), rows = r.gfx.rows;
+        const int NT = rowthreads(M / 2), rows = r.gfx.rows;
         const int nblk = (M * M + rows - 1) / rows;
         LCHK(L.go("fft_x", k_fx<R, M>, dim3(nblk), dim3(rows * NT), (size_t)(rows * padlen(M / 2) + M) * vs, at<R>(pl, y.grid),
                   at<V>(pl, y.C1), r.gfx, W));
@@ -628,7 +637,12 @@ int launch_fft_chain_m(Launcher& L, enuf_plan* pl, int nf, void* spec = nullptr,
                   at<const V>(pl, y.C1), at<V>(pl, y.C2), r.gy, W));
     }
     if (spec) {
-        const int Wc = r.gz.W;
+        // pencils per CTA of the spectrum pass (radix 4: M/4 threads a
+        // pencil, at most 512 threads)
+        FftGeom gs = r.gz;
+        gs.W = std::max(1, std::min(gs.W, 512 / std::max(1, M / 4)));
+        gs.fW = FDiv::make((uint32_t)gs.W);
+        const int Wc = gs.W;
         const size_t smem = (size_t)(Wc * (padlen(M) + 1) + M) * vs;
         if (smem > 48 * 1024 && !L.attr_only) {
             cudaError_t e = cudaFuncSetAttribute((const void*)k_fz_spectrum<R, M>,
@@ -638,10 +652,39 @@ int launch_fft_chain_m(Launcher& L, enuf_plan* pl, int nf, void* spec = nullptr,
         }
         const int NTZ = M >= 4 ? M / 4 : 1;
         return L.go("fft_z_spectrum", k_fz_spectrum<R, M>, dim3((r.P + Wc - 1) / Wc), dim3(Wc * NTZ), smem,
-                    at<const V>(pl, y.C2), reinterpret_cast<V*>(spec), r.gz, W, at<const R>(pl, y.td), scale);
+                    at<const V>(pl, y.C2), reinterpret_cast<V*>(spec), gs, W, at<const R>(pl, y.td), scale);
     }
     // z + reciprocal-space step + inverse z
-    {
+    bool wide_done = false;
+    if constexpr (M >= 512) {
+        if (r.fz_wide) {
+        const int Wc = r.gz.W;
+        const size_t smem = (size_t)(Wc * (padlen(M) + 1) + M) * vs + 32 * 7 * 8 + (size_t)9 * r.Kb * sizeof(R);
+        KTables<R> kt;
+        kt.tk = at<const R>(pl, y.tk);
+        kt.te = at<const R>(pl, y.te);
+        kt.td = at<const R>(pl, y.td);
+        const double V3 = r.prm.L[0] * r.prm.L[1] * r.prm.L[2];
+        kt.cE = (R)(r.prm.coulomb_k * 2.0 * kPi / V3);
+        kt.cF = (R)(r.prm.coulomb_k * 4.0 * kPi / V3);
+        kt.inv4a2 = (R)(1.0 / (4.0 * r.prm.alpha * r.prm.alpha));
+        const dim3 g((r.P + Wc - 1) / Wc), b(Wc * (M / 8));
+        if (nf == 0)
+            LCHK(L.go("fft_z_kspace", k_fzw<R, M, 0>, g, b, smem, at<const V>(pl, y.C2), at<V>(pl, y.C3), r.gz, W, kt,
+                      at<double>(pl, y.kpart)));
+        else if (nf == 1)
+            LCHK(L.go("fft_z_kspace", k_fzw<R, M, 1>, g, b, smem, at<const V>(pl, y.C2), at<V>(pl, y.C3), r.gz, W, kt,
+                      at<double>(pl, y.kpart)));
+        else if (nf == 3)
+            LCHK(L.go("fft_z_kspace", k_fzw<R, M, 3>, g, b, smem, at<const V>(pl, y.C2), at<V>(pl, y.C3), r.gz, W, kt,
+                      at<double>(pl, y.kpart)));
+        else
+            LCHK(L.go("fft_z_kspace", k_fzw<R, M, 4>, g, b, smem, at<const V>(pl, y.C2), at<V>(pl, y.C3), r.gz, W, kt,
+                      at<double>(pl, y.kpart)));
+        wide_done = true;
+        }
+    }
+    if (!wide_done) {
         const int Wc = r.gz.W;
         const size_t smem = (size_t)(std::max(nf, 1) * Wc * (padlen(M) + 1) + M) * vs + 32 * 7 * 8 + (size_t)9 * r.Kb * sizeof(R);
         KTables<R> kt;
@@ -680,7 +723,7 @@ int launch_fft_chain_m(Launcher& L, enuf_plan* pl, int nf, void* spec = nullptr,
     }
     // inverse x (complex to real)
     {
-        const int NTh = ffthreads(M / 2), rows = r.gfx.rows;
+        const int NTh = rowthreads(M / 2), rows = r.gfx.rows;
         const int nrows = nf * M * M;
         LCHK(L.go("ifft_x", k_ix<R, M>, dim3((nrows + rows - 1) / rows), dim3(rows * NTh), (size_t)(rows * padlen(M / 2) + M) * vs,
                   at<const V>(pl, y.C4), at<R>(pl, y.fld), r.gfx, nrows, W));

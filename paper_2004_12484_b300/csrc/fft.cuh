@@ -75,17 +75,60 @@ template <typename V, bool INV> __device__ __forceinline__ void dft8(V* v)
     }
 }
 
+// 16-point DFT in registers as 4 x 4: DFT4 over n1 of x[4 n1 + n2] for each
+// n2, twiddles W16^(n2 k1), DFT4 over n2; outputs in natural order.
+template <typename V, bool INV> __device__ __forceinline__ void dft16(V* v)
+{
+    using R = decltype(v[0].x);
+    V a[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; n2++) {
+        V t[4] = {v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]};
+        dft4<V, INV>(t);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; k1++) a[n2][k1] = t[k1];
+    }
+    // W16^j = exp(-+ 2 pi i j / 16) for the products n2 k1 in {1, 2, 3, 4, 6, 9}
+    const R c1 = (R)0.92387953251128675613, s1 = (R)0.38268343236508977173, h = (R)0.70710678118654752440;
+    const R sg = INV ? R(1) : R(-1);  // sign of the imaginary part of W16^1
+    auto tw = [&](V x, R c, R sn) { return V{x.x * c - x.y * sn, x.x * sn + x.y * c}; };
+    a[1][1] = tw(a[1][1], c1, sg * s1);
+    a[1][2] = tw(a[1][2], h, sg * h);
+    a[1][3] = tw(a[1][3], s1, sg * c1);
+    a[2][1] = tw(a[2][1], h, sg * h);
+    a[2][2] = tw(a[2][2], R(0), sg);
+    a[2][3] = tw(a[2][3], -h, sg * h);
+    a[3][1] = tw(a[3][1], s1, sg * c1);
+    a[3][2] = tw(a[3][2], -h, sg * h);
+    a[3][3] = tw(a[3][3], -c1, -sg * s1);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; k1++) {
+        V t[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+        dft4<V, INV>(t);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; k2++) v[k1 + 4 * k2] = t[k2];
+    }
+}
+
 template <typename V, int R, bool INV> __device__ __forceinline__ void dftR(V* v)
 {
-    if constexpr (R == 8) dft8<V, INV>(v);
+    if constexpr (R == 16) dft16<V, INV>(v);
+    else if constexpr (R == 8) dft8<V, INV>(v);
     else if constexpr (R == 4) dft4<V, INV>(v);
     else dft2<V, INV>(v);
 }
 
-// Threads serving one transform of length N when passes use radix MR (8 or
-// 4) and below: each thread holds MR elements per pass.
+// Threads serving one transform of length N when passes use radix MR (16,
+// 8 or 4) and below: each thread holds MR elements per pass.
 template <int N, int MR = 8> struct FftThreads {
     static constexpr int NT = N >= MR ? N / MR : 1;
+};
+
+// Radix of the register passes of the x-row kernels (k_fx, k_ix): 16 for
+// the half-length 256 of a 512 grid (two radix-16 passes, one exchange),
+// else 8.
+template <int N> struct RowMR {
+    static constexpr int V = N == 256 ? 16 : 8;
 };
 
 // Shared-memory layout of one transform: element e lives at pidx(e) = e +
@@ -183,7 +226,8 @@ __device__ __forceinline__ void fft_smem_multi(V* x, int trs, int t, const V* __
 // stockham_pass.  All threads of the CTA must call it (it contains
 // barriers).
 template <typename V, int N, int Ns, bool INV, int NTR, int MR> struct RegPasses {
-    static constexpr int R = (MR >= 8 && Ns * 8 <= N) ? 8 : ((Ns * 4 <= N) ? 4 : 2);
+    static constexpr int R =
+        (MR >= 16 && Ns * 16 <= N) ? 16 : ((MR >= 8 && Ns * 8 <= N) ? 8 : ((Ns * 4 <= N) ? 4 : 2));
     static constexpr int NT = FftThreads<N, MR>::NT;
     static constexpr int NB = N / R, PER = NB / NT, E = N / NT;
     // v[q][m]: element m of transform q (m = b + PER r for butterfly b, leg r)
@@ -287,7 +331,7 @@ __global__ void __launch_bounds__(256) k_fx(R* __restrict__ grid, typename Cpx<R
                      const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
-    constexpr int MH = M / 2, NT = FftThreads<MH>::NT, RS = PadLen<MH>::V, E = MH / NT;
+    constexpr int MH = M / 2, MRX = RowMR<MH>::V, NT = FftThreads<MH, MRX>::NT, RS = PadLen<MH>::V, E = MH / NT;
     extern __shared__ __align__(16) unsigned char smraw[];
     V* s = reinterpret_cast<V*>(smraw);
     const int rows = g.rows, row0 = blockIdx.x * rows, nrows = M * M;
@@ -301,7 +345,7 @@ __global__ void __launch_bounds__(256) k_fx(R* __restrict__ grid, typename Cpx<R
     cp_async_wait_all();
     __syncthreads();
     V* x = s + r * RS;
-    fft_reg<V, MH, false>(v, x, t, sW, 2);
+    fft_reg<V, MH, false, MRX>(v, x, t, sW, 2);
     // the grid is left zeroed for the next spreading (each element is
     // cleared by the thread that read it, once its value is in use: a
     // store right behind the load of the same address waits for it)
@@ -558,6 +602,107 @@ __global__ void __launch_bounds__(512) k_fz(const typename Cpx<R>::T* __restrict
     }
 }
 
+// The z pass for large grids (M = 512): the same steps as k_fz with radix-8
+// register passes, W pencils per CTA of W * M/8 threads (W = 16 in single
+// precision: the loads and stores of a z row are 128-byte runs of 16
+// neighbouring pencils; 8 in double), and
+// the NF field transforms done one after the other through one buffer per
+// pencil (the spectrum S~ and k_z stay in registers between them).
+template <typename R, int M, int NF>
+__global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512) k_fzw(const typename Cpx<R>::T* __restrict__ C2, typename Cpx<R>::T* __restrict__ C3, FftGeom g,
+                      const typename Cpx<R>::T* __restrict__ Wg, KTables<R> ktg, double* __restrict__ part)
+{
+    using V = typename Cpx<R>::T;
+    constexpr int MR = 8, NT = FftThreads<M, MR>::NT, LD = PadLen<M>::V + 1, E = M / NT;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* X = reinterpret_cast<V*>(smraw);
+    const int Wc = g.W, Kx = g.Kx, Kb = g.Kb, nc = g.nc, P = g.P;
+    double* red = reinterpret_cast<double*>(X + Wc * LD);
+    V* sW = reinterpret_cast<V*>(red + 32 * 7);
+    stage_twiddles(sW, Wg, M);
+    R* stab = reinterpret_cast<R*>(sW + M);
+    for (int i = threadIdx.x; i < 3 * Kb; i += blockDim.x) {
+        stab[i] = ktg.tk[i];
+        stab[3 * Kb + i] = ktg.te[i];
+        stab[6 * Kb + i] = ktg.td[i];
+    }
+    const R* tk = stab;
+    const R* te = stab + 3 * Kb;
+    const R* td = stab + 6 * Kb;
+    pdl_wait();
+    const int p0 = blockIdx.x * Wc;
+    const int t = (int)g.fW.div(threadIdx.x), w = threadIdx.x - t * Wc, p = p0 + w;
+    V v[1][E];
+#pragma unroll
+    for (int m = 0; m < E; m++) v[0][m] = p < P ? C2[(size_t)(t + NT * m) * P + p] : V{R(0), R(0)};
+    cp_async_wait_all();
+    __syncthreads();
+    V* buf = X + w * LD;
+    fft_reg<V, M, false, MR>(v, buf, t, sW, 1);
+
+    // scaling, energy / virial; v becomes val = (ke 4 pi / V) G D S~, zero
+    // outside the retained cube
+    R acc[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+    R kz[E];
+    int nx = 0, ny = 0;
+    bool pv = false;
+    if (p < P) {
+        const int kb = (int)g.fKx.div(p);
+        nx = p - kb * Kx;
+        ny = kb <= nc ? kb : kb - Kb;
+        pv = true;
+    }
+    const R kxv = pv ? tk[nx + nc] : R(0), kyv = pv ? tk[Kb + ny + nc] : R(0);
+    const R exy = pv ? te[nx + nc] * te[Kb + ny + nc] : R(0), dxy = pv ? td[nx + nc] * td[Kb + ny + nc] : R(0);
+#pragma unroll
+    for (int m = 0; m < E; m++) {
+        const int z = t + NT * m;
+        const int nz = z <= nc ? z : (z >= M - nc ? z - M : (1 << 20));
+        V val = V{R(0), R(0)};
+        R kzv = R(0);
+        if (pv && nz != (1 << 20) && (nx != 0 || ny != 0 || nz != 0)) {
+            kzv = tk[2 * Kb + nz + nc];
+            const R k2 = kxv * kxv + kyv * kyv + kzv * kzv;
+            const R G = exy * te[2 * Kb + nz + nc] / k2;
+            const R D2 = dxy * td[2 * Kb + nz + nc];
+            const V gh = v[0][m];
+            const R s2 = D2 * (gh.x * gh.x + gh.y * gh.y);  // |S(n)|^2
+            const R e = (nx == 0 ? R(1) : R(2)) * ktg.cE * G * s2;
+            const R c = R(2) * (R(1) / k2 + ktg.inv4a2);
+            acc[0] += e;
+            acc[1] += e * (R(1) - c * kxv * kxv);
+            acc[2] += e * (R(1) - c * kyv * kyv);
+            acc[3] += e * (R(1) - c * kzv * kzv);
+            acc[4] -= e * c * kxv * kyv;
+            acc[5] -= e * c * kxv * kzv;
+            acc[6] -= e * c * kyv * kzv;
+            const R f = ktg.cF * G * D2;
+            val = V{f * gh.x, f * gh.y};
+        }
+        v[0][m] = val;
+        kz[m] = kzv;
+    }
+    block_reduce_to_double<R, 7>(acc, part + 8 * (size_t)blockIdx.x, red);
+    if (NF == 0) return;
+#pragma unroll 1
+    for (int f = 0; f < (NF > 0 ? NF : 1); f++) {
+        // NF = 1: the potential; else -i k_t val for the three field
+        // components and val for the potential (f = 3)
+        V fv[1][E];
+#pragma unroll
+        for (int m = 0; m < E; m++) {
+            const V val = v[0][m];
+            const R kk = f == 0 ? kxv : (f == 1 ? kyv : kz[m]);
+            fv[0][m] = (NF == 1 || f == 3) ? val : V{kk * val.y, -kk * val.x};
+        }
+        fft_reg<V, M, true, MR>(fv, buf, t, sW, 1);
+        if (p < P) {
+#pragma unroll
+            for (int m = 0; m < E; m++) C3[((size_t)f * M + t + NT * m) * P + p] = fv[0][m];
+        }
+    }
+}
+
 // ---------------------------------------------------------------- k_fz_spectrum
 // The forward z pass alone, for the entry points that return the retained
 // spectrum instead of forces: the same pencils and transform as k_fz, then
@@ -737,7 +882,7 @@ __global__ void __launch_bounds__(256) k_ix(const typename Cpx<R>::T* __restrict
                      const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
-    constexpr int MH = M / 2, NT = FftThreads<MH>::NT, RS = PadLen<MH>::V, E = MH / NT;
+    constexpr int MH = M / 2, MRX = RowMR<MH>::V, NT = FftThreads<MH, MRX>::NT, RS = PadLen<MH>::V, E = MH / NT;
     extern __shared__ __align__(16) unsigned char smraw[];
     V* s = reinterpret_cast<V*>(smraw);
     const int rows = g.rows, row0 = blockIdx.x * rows, Kx = g.Kx, nc = g.nc;
@@ -758,7 +903,7 @@ __global__ void __launch_bounds__(256) k_ix(const typename Cpx<R>::T* __restrict
         const V fo = cmul(csub(a, b), cconj(W[k]));  // (a - b) e^{+2 pi i k / M}
         v[0][m] = V{fe.x - fo.y, fe.y + fo.x};       // fe + i fo
     }
-    fft_reg<V, MH, true>(v, s + r * RS, t, W, 2);
+    fft_reg<V, MH, true, MRX>(v, s + r * RS, t, W, 2);
     if (live) {
         V* out = reinterpret_cast<V*>(fld) + (size_t)row * MH;
 #pragma unroll
