@@ -250,15 +250,35 @@ __global__ void __launch_bounds__(32) k_spread(const int4* __restrict__ work, co
     const int a = lane % G;
     __syncwarp();
 
+    // p = 8: the warp's 32 records go through shared memory (one broadcast
+    // load per particle; shuffles would share the shared-memory pipe that
+    // bounds this kernel, four per particle)
+    __shared__ RecT srecs[P == 8 ? 32 : 1];
     for (int j0 = w.y; j0 < w.z; j0 += 32) {
-        // one record per lane, handed to the warp with shuffles
+        // one record per lane, handed to the warp with shuffles (or, p = 8,
+        // through shared memory)
         RecT mine;
         if (j0 + lane < w.z) mine = rec[j0 + lane];
         else mine.x = mine.y = mine.z = mine.w = R(0);
+        if constexpr (P == 8) {
+            srecs[lane] = mine;
+            __syncwarp();
+        }
         const int nj = min(32, w.z - j0);
         for (int jj = 0; jj < nj; jj++) {
-            const R rx = __shfl_sync(0xffffffffu, mine.x, jj), ry = __shfl_sync(0xffffffffu, mine.y, jj);
-            const R rz = __shfl_sync(0xffffffffu, mine.z, jj), rq = __shfl_sync(0xffffffffu, mine.w, jj);
+            R rx, ry, rz, rq;
+            if constexpr (P == 8) {
+                const RecT rr = srecs[jj];
+                rx = rr.x;
+                ry = rr.y;
+                rz = rr.z;
+                rq = rr.w;
+            } else {
+                rx = __shfl_sync(0xffffffffu, mine.x, jj);
+                ry = __shfl_sync(0xffffffffu, mine.y, jj);
+                rz = __shfl_sync(0xffffffffu, mine.z, jj);
+                rq = __shfl_sync(0xffffffffu, mine.w, jj);
+            }
             int ix, iy, iz;
             R dx, dy, dz;
             split_offset<R, T>(rx, ix, dx);
@@ -273,16 +293,18 @@ __global__ void __launch_bounds__(32) k_spread(const int4* __restrict__ work, co
             constexpr int NV = P == 8 ? 16 : (P == 4 ? 2 : (P * P + RPI - 1) / RPI);
             if constexpr (P == 8) {
                 // lane 8 g + a: x-offset a of rows b0 + 2i and planes c0 + 2k
-                // (b0 = g & 1, c0 = g >> 1); lane a also evaluates the y and z
-                // weights of offset a for the whole warp
+                // (b0 = g & 1, c0 = g >> 1); every lane evaluates the y and z
+                // weights itself (fast Gaussian gridding: three exponentials
+                // a dimension) rather than taking them by shuffles
                 const int g = lane >> 3, b0 = g & 1, c0 = g >> 1;
-                const R uy = dy + (R)(3 - a), uz = dz + (R)(3 - a);
-                const R wya = win_exp(uy * uy, wc), wza = win_exp(uz * uz, wc);
+                R wy8[8], wz8[8];
+                window_weights<R, 8>(dy, wc, wy8);
+                window_weights<R, 8>(dz, wc, wz8);
                 R t[4], wz[4];
 #pragma unroll
                 for (int i = 0; i < 4; i++) {
-                    t[i] = wx * __shfl_sync(0xffffffffu, wya, b0 + 2 * i);
-                    wz[i] = __shfl_sync(0xffffffffu, wza, c0 + 2 * i);
+                    t[i] = wx * (b0 ? wy8[2 * i + 1] : wy8[2 * i]);
+                    wz[i] = c0 ? wz8[2 * i + 1] : wz8[2 * i];
                 }
                 R* base = acc + (iz + c0) * PS + (iy + b0) * BX + ix + B::XOFF + a;
                 R old[16];
