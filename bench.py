@@ -46,7 +46,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="enuf", choices=["enuf", "reference"])
     ap.add_argument("--workload", default="rpm_1e4",
-                    choices=["rpm_1e4", "rpm", "polyelectrolyte", "ionic_liquid", "nacl"])
+                    choices=["rpm_1e4", "rpm", "polyelectrolyte", "polyelectrolyte_1e4", "ionic_liquid",
+                             "ionic_liquid_eighth", "nacl"])
+    ap.add_argument("--evals", type=int, default=0,
+                    help="only run this many k-space evaluations of the workload and exit (a driver for ncu)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the polyelectrolyte and ionic-liquid systems")
     return ap.parse_args()
@@ -56,9 +59,32 @@ def workload(name, seed_offset=0):
     fn = getattr(W, name)
     if name == "nacl":
         return fn()
-    d = fn(seed={"rpm_1e4": 2, "rpm": 2, "polyelectrolyte": 3, "ionic_liquid": 4}[name] + 100 * seed_offset) \
-        if seed_offset else fn()
+    seeds = {"rpm_1e4": 2, "rpm": 2, "polyelectrolyte": 3, "polyelectrolyte_1e4": 3, "ionic_liquid": 4,
+             "ionic_liquid_eighth": 45}
+    d = fn(seed=seeds[name] + 100 * seed_offset) if seed_offset else fn()
     return d
+
+
+def evals_only(args):
+    """Runs args.evals k-space evaluations (energy, forces, virial) of the
+    workload on GPU 0 and exits: the program that the profiles' ncu captures
+    run."""
+    import torch
+    import paper_2004_12484_b300 as P
+    dev = torch.device("cuda", 0)
+    d = workload(args.workload)
+    N = len(d["q"])
+    pos32, q32 = W.as_fp32(d["pos"], d["q"])
+    tp = torch.tensor(pos32, dtype=torch.float32, device=dev)
+    tq = torch.tensor(q32, dtype=torch.float32, device=dev)
+    plan = P.Plan(L=d["L"], N=N, alpha=d["alpha"], r_c=d["r_c"], M=d["M"], p=d["p"], n_c=d["n_c"],
+                  precision="mixed", device=dev)
+    F = torch.empty((N, 3), dtype=torch.float32, device=dev)
+    out = torch.empty(16, dtype=torch.float64, device=dev)
+    for _ in range(args.evals):
+        plan.compute(tp, tq, forces=True, virial=True, kspace_only=True, F=F, out=out)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": d["name"], "N": N, "evals": args.evals, "E_recip": float(out[0])}), flush=True)
 
 
 def config_of(d, args):
@@ -431,6 +457,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.evals > 0:
+        return evals_only(args)
     import torch
     import paper_2004_12484_b300 as P
 

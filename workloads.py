@@ -191,6 +191,16 @@ def ionic_liquid(N=8388608, density=0.1, n_centres=1_000_000, blob=2.0, seed=4, 
                 n_c=M // 4, precision="mixed", seed=seed)
 
 
+def ionic_liquid_eighth(seed=45):
+    """A 1/8-volume copy of the ionic-liquid workload (1,048,576 sites, box
+    218.9 A, 125,000 cluster centres, grid 256^3: the same density,
+    clustering, grid spacing and method parameters), small enough for
+    detailed profiler captures and CPU accuracy studies."""
+    d = ionic_liquid(N=1048576, n_centres=125000, seed=seed, M=256)
+    d["name"] = "ionic_liquid_eighth"
+    return d
+
+
 def random_neutral(N, L, seed, charged_fraction=1.0, anisotropy=1.0):
     """Uniform positions, +-1 charges on a random charged fraction, neutral."""
     g = _rng(seed)
