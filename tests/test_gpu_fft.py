@@ -101,3 +101,33 @@ def test_structure_factor_is_additive_and_checks_inputs():
     # an evaluation after the reported failure is unaffected
     parts, F, _, _ = whole.energy_forces(tp, tq)
     assert np.isfinite(parts["E"]) and torch.isfinite(F).all()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 2e-6)])
+def test_wide_z_pass_matches_narrow_at_512(precision, tol, monkeypatch):
+    """At M = 512 the z pass is k_fzw (16 pencils a CTA, radix 8, fields one
+    after the other); ENUF_FZ_NARROW=1 selects the z pass of the smaller
+    grids, which the oracle checks at M <= 256.  Both give the same energy,
+    forces, potentials and virial (a small system on the 512^3 grid)."""
+    g = np.random.default_rng(90)
+    N, L = 3000, np.array([60.0, 64.0, 68.0])
+    pos = g.uniform(0, 1, size=(N, 3)) * L
+    q = g.normal(size=N)
+    q -= q.mean()
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    tp = torch.tensor(pos, dtype=dt, device=DEV)
+    tq = torch.tensor(q, dtype=dt, device=DEV)
+    res = []
+    for narrow in (False, True):
+        if narrow:
+            monkeypatch.setenv("ENUF_FZ_NARROW", "1")
+        plan = P.Plan(L=L, N=N, alpha=0.5, r_c=10.0, M=512, p=4, precision=precision, device=DEV)
+        parts, F, Wv, ph = plan.energy_forces(tp, tq, phi=True, kspace_only=True)
+        res.append((parts["E"], F.cpu().double(), Wv, ph.cpu().double()))
+        del plan
+        torch.cuda.empty_cache()
+    (E0, F0, W0, p0), (E1, F1, W1, p1) = res
+    assert abs(E0 / E1 - 1) < tol
+    assert rel_rms(F0, F1) < tol
+    assert rel_rms(p0, p1) < tol
+    assert np.abs(W0 - W1).max() < tol * np.abs(W1).max()
