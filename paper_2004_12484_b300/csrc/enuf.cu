@@ -171,9 +171,12 @@ int resolve(const enuf_params* in, Resolved& r)
     r.gfx = FftGeom{r.nc, r.Kx, r.Kb, r.P, 0, 256 / rowthreads(M / 2)};
     const int NT = ffthreads(M), gran = std::max(1, 32 / NT);
     auto round_up = [](int v, int g) { return (v + g - 1) / g * g; };
-    // k_fy / k_iy: columns per block, about 16 but balanced over Kx
+    // k_fy / k_iy: columns per block, about 16 but balanced over Kx (about 8
+    // at M = 512, where 16 columns of 64 threads made one CTA of 960 threads
+    // an SM by registers)
     {
-        int nch = (r.Kx + 15) / 16;
+        const int cw = M >= 512 ? 8 : 16;
+        int nch = (r.Kx + cw - 1) / cw;
         int W = round_up((r.Kx + nch - 1) / nch, gran);
         while (W * NT > 1024) W -= gran;
         while ((size_t)(W * (padlen(M) + 1) + M) * vsz > (size_t)kMaxSmem) W -= gran;
