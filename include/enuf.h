@@ -276,6 +276,31 @@ int enuf_mlp_train_step(float* w_master, void* w_bf16, float* adam_m, float* ada
                         float beta2, float eps, int step, float* loss_out, float* grad_out, int apply_update,
                         void* stream);
 
+/* ---------------------------------------------------------------------
+ * Checked build.  libenuf_check.so is this library compiled with bounds
+ * checks (in place of a memory checker): every index that the kernels derive
+ * from particle data, bin counts, work lists or their thread decomposition is
+ * tested against its extent before the access; a failed test is counted and
+ * the access skipped (a kernel never traps).  Same entry points and results
+ * as libenuf.so while no check fails; slower.
+ * --------------------------------------------------------------------- */
+
+/* 1 in the checked build, 0 in libenuf.so. */
+int enuf_bounds_checked(void);
+
+/* Synchronises the device and returns in *fails the number of failed checks
+ * since the last clear (always 0 in libenuf.so).  If where (host, where_len
+ * bytes) is given it receives the first failure as "file:line index i of n"
+ * ("" if none).  clear != 0 resets the count.  Errors: ENUF_EINVAL (fails
+ * NULL), ENUF_ECUDA. */
+int enuf_bounds_status(unsigned long long* fails, char* where, int where_len, int clear);
+
+/* Checked build: runs a kernel whose last two of n + 2 writes fail their
+ * check (the buffer has room for them) and verifies that exactly those were
+ * refused and recorded; clears the count.  0 on success, ENUF_EDEVICE if the
+ * checks misbehaved, ENUF_EINVAL in libenuf.so. */
+int enuf_bounds_selftest(void);
+
 /* Thread-local description of the last failure ("" if none). */
 const char* enuf_last_error(void);
 

@@ -21,7 +21,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libenuf.so")
+# ENUF_BOUNDS_CHECK=1 in the environment selects the checked build of the
+# library (bounds checks in every kernel; same entry points and results)
+LIB_PATH = os.path.join(_HERE, "libenuf_check.so" if os.environ.get("ENUF_BOUNDS_CHECK") == "1" else "libenuf.so")
 
 FP64 = 0
 MIXED = 1
@@ -67,6 +69,8 @@ def lib():
                               "`python -m paper_2004_12484_b300.build` (or __graft_entry__.build())")
         L = ctypes.CDLL(LIB_PATH)
         L.enuf_last_error.restype = ctypes.c_char_p
+        L.enuf_bounds_status.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_char_p, ctypes.c_int,
+                                         ctypes.c_int]
         L.enuf_version.restype = ctypes.c_char_p
         L.enuf_plan_workspace_bytes.argtypes = [ctypes.POINTER(EnufParams), ctypes.POINTER(ctypes.c_size_t)]
         L.enuf_md_run.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int,

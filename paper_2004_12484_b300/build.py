@@ -16,6 +16,8 @@ SRC_DIR = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libenuf.so")
 # the benchmark's FMA-rate probe, kept out of the library
 PROBE_LIB = os.path.join(HERE, "libenuf_probe.so")
+# the same library with bounds checks in every kernel (tests only)
+CHECK_LIB = os.path.join(HERE, "libenuf_check.so")
 HEADER = os.path.join(ROOT, "include", "enuf.h")
 
 NVCC_FLAGS = [
@@ -33,7 +35,7 @@ def _sources():
 
 
 def needs_build() -> bool:
-    for lib in (LIB, PROBE_LIB):
+    for lib in (LIB, PROBE_LIB, CHECK_LIB):
         if not os.path.exists(lib):
             return True
         t = os.path.getmtime(lib)
@@ -52,23 +54,26 @@ def nvcc() -> str:
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not needs_build():
         return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *NVCC_FLAGS, "-o", tmp, os.path.join(SRC_DIR, "enuf.cu"), os.path.join(SRC_DIR, "noalloc.cu"),
-           os.path.join(SRC_DIR, "mlp.cu")]
-    ptmp = PROBE_LIB + f".tmp{os.getpid()}"
-    pcmd = [nvcc(), *NVCC_FLAGS, "-o", ptmp, os.path.join(SRC_DIR, "probe.cu")]
-    # the two libraries compile side by side
-    procs = []
-    for c in (cmd, pcmd):
+    srcs = [os.path.join(SRC_DIR, "enuf.cu"), os.path.join(SRC_DIR, "noalloc.cu"), os.path.join(SRC_DIR, "mlp.cu")]
+    jobs = [
+        (LIB, [*NVCC_FLAGS, *srcs]),
+        (PROBE_LIB, [*NVCC_FLAGS, os.path.join(SRC_DIR, "probe.cu")]),
+        (CHECK_LIB, [*NVCC_FLAGS, "-DENUF_BOUNDS_CHECK", *srcs]),
+    ]
+    # the libraries compile side by side
+    procs, cmds = [], []
+    for lib, args in jobs:
+        c = [nvcc(), *args, "-o", lib + f".tmp{os.getpid()}"]
         if verbose:
             print(" ".join(c), flush=True)
+        cmds.append(c)
         procs.append(subprocess.Popen(c))
     rcs = [pr.wait() for pr in procs]
-    for c, rc in zip((cmd, pcmd), rcs):
+    for c, rc in zip(cmds, rcs):
         if rc != 0:
             raise subprocess.CalledProcessError(rc, c)
-    os.replace(tmp, LIB)
-    os.replace(ptmp, PROBE_LIB)
+    for lib, _ in jobs:
+        os.replace(lib + f".tmp{os.getpid()}", lib)
     return LIB
 
 

@@ -102,6 +102,57 @@ template <typename R> __device__ __forceinline__ R warp_sum(R v)
     return v;
 }
 
+// Bytes of dynamic shared memory the block was launched with.
+__device__ __forceinline__ unsigned dynamic_smem_bytes()
+{
+    unsigned v;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+    return v;
+}
+
+// ------------------------------------------------------------------ bounds checks
+// The checked build of the library (compiled with ENUF_BOUNDS_CHECK) tests
+// every index derived from the particle data, the bin counts, the work lists
+// and the thread decomposition of the kernels against the extent it must stay
+// within, before the access it guards.  A failed test counts the failure,
+// records the first one (source file, line, index and extent; read by
+// enuf_bounds_status) and skips the access, so that the kernel carries on
+// and never traps.  In the normal build ENUF_IN is the constant true and
+// the checks vanish at compile time.
+#ifdef ENUF_BOUNDS_CHECK
+struct BoundsLog {
+    unsigned long long fails;
+    long long index, extent;
+    int line;
+    char file[44];
+};
+static __device__ BoundsLog g_bounds;
+
+static __device__ __noinline__ bool bounds_fail(long long i, long long n, int line, const char* file)
+{
+    if (atomicAdd(&g_bounds.fails, 1ull) == 0ull) {
+        g_bounds.index = i;
+        g_bounds.extent = n;
+        g_bounds.line = line;
+        const char* base = file;
+        for (const char* c = file; *c; c++)
+            if (*c == '/') base = c + 1;
+        int k = 0;
+        for (; k < (int)sizeof(g_bounds.file) - 1 && base[k]; k++) g_bounds.file[k] = base[k];
+        g_bounds.file[k] = 0;
+    }
+    return false;
+}
+#define ENUF_IN(i, n)                                                                        \
+    ((unsigned long long)(long long)(i) < (unsigned long long)(long long)(n) ||             \
+     ::enuf::bounds_fail((long long)(i), (long long)(n), __LINE__, __FILE__))
+#else
+#define ENUF_IN(i, n) true
+#endif
+// An index of the thread decomposition, checked and, when out of range,
+// replaced by 0 (kernels with block-wide barriers cannot leave early).
+#define ENUF_CLAMP(i, n) (ENUF_IN(i, n) ? (i) : 0)
+
 // Status bits written by kernels into the workspace status word.
 enum : int {
     ST_NONFINITE = 1,  // a non-finite position or charge was seen

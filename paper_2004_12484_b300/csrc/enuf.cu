@@ -464,7 +464,7 @@ int launch_spread_t(Launcher& L, enuf_plan* pl)
     return L.go("spread", k_spread<R, P, T>, dim3(r.max_work2), dim3(32),
                 (size_t)(SBox<P, S>::CELLS + P * P) * sizeof(R), at<const int4>(pl, y.work2),
                 at<const int>(pl, y.nwork2), at<const typename Rec<R>::T>(pl, y.rec), r.prm.M, pl->lnb, r.lr,
-                winc<R>(pl), (R)pl->cnorm3, at<R>(pl, y.grid));
+                winc<R>(pl), (R)pl->cnorm3, at<R>(pl, y.grid), (int)r.prm.N);
 }
 
 template <typename R, int P, int T>
@@ -496,11 +496,11 @@ int launch_gather_t(Launcher& L, enuf_plan* pl, int nf, R* F, R* phi)
                 return L.go("gather", k_gather_p8<4>, dim3(r.max_work), dim3(512), GatherP8<4>::SMEM,
                             at<const int4>(pl, y.work), at<const int>(pl, y.nwork), at<const f4>(pl, y.rec),
                             at<const uint32_t>(pl, y.perm), r.prm.M, pl->lnb, winc<float>(pl), (float)pl->cnorm3,
-                            at<const float>(pl, y.fld), pl->fld_tmap, (float*)F, (float*)phi, st);
+                            at<const float>(pl, y.fld), pl->fld_tmap, (float*)F, (float*)phi, st, (int)r.prm.N);
             return L.go("gather", k_gather_p8<3>, dim3(r.max_work), dim3(512), GatherP8<3>::SMEM,
                         at<const int4>(pl, y.work), at<const int>(pl, y.nwork), at<const f4>(pl, y.rec),
                         at<const uint32_t>(pl, y.perm), r.prm.M, pl->lnb, winc<float>(pl), (float)pl->cnorm3,
-                        at<const float>(pl, y.fld), pl->fld_tmap, (float*)F, (float*)phi, st);
+                        at<const float>(pl, y.fld), pl->fld_tmap, (float*)F, (float*)phi, st, (int)r.prm.N);
         }
     }
     if constexpr (T == 16) {
@@ -514,11 +514,11 @@ int launch_gather_t(Launcher& L, enuf_plan* pl, int nf, R* F, R* phi)
                 return L.go("gather", k_gather<R, P, T, 4, NTH, ZS>, dim3(r.max_work), dim3(NTH), smem,
                             at<const int4>(pl, y.work), at<const int>(pl, y.nwork), at<const RecT>(pl, y.rec),
                             at<const uint32_t>(pl, y.perm), r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), (R)pl->cnorm3,
-                            at<const R>(pl, y.fld), F, phi);
+                            at<const R>(pl, y.fld), F, phi, (int)r.prm.N);
             return L.go("gather", k_gather<R, P, T, 3, NTH, ZS>, dim3(r.max_work), dim3(NTH), smem,
                         at<const int4>(pl, y.work), at<const int>(pl, y.nwork), at<const RecT>(pl, y.rec),
                         at<const uint32_t>(pl, y.perm), r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), (R)pl->cnorm3,
-                        at<const R>(pl, y.fld), F, phi);
+                        at<const R>(pl, y.fld), F, phi, (int)r.prm.N);
         }
     }
     // 1024 threads for whole 16-cell tiles (one CTA per SM holds the box),
@@ -529,10 +529,10 @@ int launch_gather_t(Launcher& L, enuf_plan* pl, int nf, R* F, R* phi)
     if (nf == 4)
         return L.go("gather", k_gather<R, P, T, 4, NTH>, dim3(r.max_work), dim3(NTH), smem, at<const int4>(pl, y.work),
                     at<const int>(pl, y.nwork), at<const typename Rec<R>::T>(pl, y.rec), at<const uint32_t>(pl, y.perm),
-                    r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), (R)pl->cnorm3, at<const R>(pl, y.fld), F, phi);
+                    r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), (R)pl->cnorm3, at<const R>(pl, y.fld), F, phi, (int)r.prm.N);
     return L.go("gather", k_gather<R, P, T, 3, NTH>, dim3(r.max_work), dim3(NTH), smem, at<const int4>(pl, y.work),
                 at<const int>(pl, y.nwork), at<const typename Rec<R>::T>(pl, y.rec), at<const uint32_t>(pl, y.perm),
-                r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), (R)pl->cnorm3, at<const R>(pl, y.fld), F, phi);
+                r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), (R)pl->cnorm3, at<const R>(pl, y.fld), F, phi, (int)r.prm.N);
 }
 
 // Interpolation of the potential grid with the window gradient (forces by
@@ -565,14 +565,14 @@ int launch_gather_ad_t(Launcher& L, enuf_plan* pl, R* F, R* phi)
             return L.go("gather", k_gather_ad<R, P, T, NTH, ZS>, dim3(r.max_work), dim3(NTH), smem,
                         at<const int4>(pl, y.work), at<const int>(pl, y.nwork), at<const RecT>(pl, y.rec),
                         at<const uint32_t>(pl, y.perm), r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), cn, fa[0], fa[1],
-                        fa[2], at<const R>(pl, y.fld), F, phi);
+                        fa[2], at<const R>(pl, y.fld), F, phi, (int)r.prm.N);
         }
     }
     const size_t smem = ((size_t)Box<P, T>::CELLS + (NTH / 32) * WyzTable<P>::N) * sizeof(R) +
                         (size_t)r.gcap * (sizeof(RecT) + 4);
     return L.go("gather", k_gather_ad<R, P, T, NTH>, dim3(r.max_work), dim3(NTH), smem, at<const int4>(pl, y.work),
                 at<const int>(pl, y.nwork), at<const RecT>(pl, y.rec), at<const uint32_t>(pl, y.perm),
-                r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), cn, fa[0], fa[1], fa[2], at<const R>(pl, y.fld), F, phi);
+                r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), cn, fa[0], fa[1], fa[2], at<const R>(pl, y.fld), F, phi, (int)r.prm.N);
 }
 
 #define DISPATCH_P(T_, FN, ...)                                           \
@@ -833,7 +833,7 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
         LCHK(L.go("real_scatter", k_scatter<R>, dim3(nblkN), dim3(256), 0, N, at<const uint32_t>(pl, y.rkey),
                   at<const uint32_t>(pl, y.rrank), at<const uint32_t>(pl, y.roffsets), at<const RecT>(pl, y.rrec_tmp),
                   at<RecT>(pl, y.rrec), at<uint32_t>(pl, y.rperm), at<uint32_t>(pl, y.rcell), (const uint32_t*)nullptr,
-                  kSpreadCap, (int4*)nullptr, 0));
+                  kSpreadCap, (int4*)nullptr, 0, r.nrbins));
         RealParams<R> rp;
         for (int t = 0; t < 3; t++) {
             rp.nc[t] = r.ncell[t];
@@ -904,7 +904,7 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
     LCHK(L.go("scatter", k_scatter<R>, dim3(nblkN), dim3(256), 0, N, at<const uint32_t>(pl, y.key),
               at<const uint32_t>(pl, y.rank), at<const uint32_t>(pl, y.offsets), at<const RecT>(pl, y.rec_tmp),
               at<RecT>(pl, y.rec), at<uint32_t>(pl, y.perm), at<uint32_t>(pl, y.tile_of),
-              at<const uint32_t>(pl, y.item2), kSpreadCap, at<int4>(pl, y.work2), r.max_work2));
+              at<const uint32_t>(pl, y.item2), kSpreadCap, at<int4>(pl, y.work2), r.max_work2, r.nbins));
     // (a3) spread (into a zeroed grid: zeroed at binding, then by the
     // forward FFT that reads it)
     LCHK(launch_spread<R>(L, pl));
@@ -1633,6 +1633,81 @@ int enuf_fft_forward(enuf_plan* pl, const void* grid, void* ghat)
     int rc = pl->r.fp64 ? launch_fft_chain<double>(L, pl, 0, ghat, 0) : launch_fft_chain<float>(L, pl, 0, ghat, 0);
     if (rc != ENUF_OK) reset_zeroed(pl);
     return rc;
+}
+
+int enuf_bounds_checked(void)
+{
+#ifdef ENUF_BOUNDS_CHECK
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int enuf_bounds_status(unsigned long long* fails, char* where, int where_len, int clear)
+{
+    if (!fails) return fail(ENUF_EINVAL, "fails is NULL");
+    *fails = 0;
+    if (where && where_len > 0) where[0] = 0;
+#ifdef ENUF_BOUNDS_CHECK
+    CK(cudaDeviceSynchronize());
+    BoundsLog log;
+    CK(cudaMemcpyFromSymbol(&log, g_bounds, sizeof(log)));
+    *fails = log.fails;
+    if (log.fails && where && where_len > 0) {
+        log.file[sizeof(log.file) - 1] = 0;
+        snprintf(where, (size_t)where_len, "%s:%d index %lld of %lld", log.file, log.line, log.index, log.extent);
+    }
+    if (clear) {
+        const BoundsLog zero{};
+        CK(cudaMemcpyToSymbol(g_bounds, &zero, sizeof(zero)));
+    }
+#else
+    (void)clear;
+#endif
+    return ENUF_OK;
+}
+
+#ifdef ENUF_BOUNDS_CHECK
+// n + 2 threads write a buffer of n + 2 elements through checks against n:
+// the last two writes must be refused and recorded (the buffer has room
+// for them, so the test stays in bounds even if the checks did not work).
+__global__ void k_bounds_selftest(int* buf, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n + 2 && ENUF_IN(i, n)) buf[i] = 1;
+}
+#endif
+
+int enuf_bounds_selftest(void)
+{
+#ifdef ENUF_BOUNDS_CHECK
+    constexpr int n = 1000;
+    int* d = nullptr;
+    CK(cudaMalloc(&d, (n + 2) * sizeof(int)));
+    std::vector<int> h(n + 2, 0);
+    const BoundsLog zero{};
+    cudaError_t e = cudaMemset(d, 0, (n + 2) * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_bounds, &zero, sizeof(zero));
+    if (e == cudaSuccess) {
+        k_bounds_selftest<<<(n + 2 + 255) / 256, 256>>>(d, n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(h.data(), d, (n + 2) * sizeof(int), cudaMemcpyDeviceToHost);
+    BoundsLog log{};
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&log, g_bounds, sizeof(log));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_bounds, &zero, sizeof(zero));
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(ENUF_ECUDA, std::string("bounds self-test: ") + cudaGetErrorString(e));
+    int written = 0;
+    for (int i = 0; i < n; i++) written += h[i];
+    if (written != n || h[n] != 0 || h[n + 1] != 0 || log.fails != 2 || log.extent != n ||
+        (log.index != n && log.index != n + 1))
+        return fail(ENUF_EDEVICE, "bounds self-test: the checks did not refuse and record the two writes");
+    return ENUF_OK;
+#else
+    return fail(ENUF_EINVAL, "the library was built without bounds checks");
+#endif
 }
 
 int enuf_launch_count(enuf_plan* pl, int flags, int with_forces)

@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(256) k_fx(R* __restrict__ grid, typename Cpx<R
     V* s = reinterpret_cast<V*>(smraw);
     const int rows = g.rows, row0 = blockIdx.x * rows, nrows = M * M;
     const V* sW = stage_twiddles(s + rows * RS, Wg, M);
-    const int r = threadIdx.x / NT, t = threadIdx.x % NT, row = row0 + r;
+    const int r0 = threadIdx.x / NT, t = threadIdx.x % NT, r = ENUF_CLAMP(r0, rows), row = row0 + r;
     const bool live = row < nrows;
     V* gin = reinterpret_cast<V*>(grid) + (size_t)(live ? row : 0) * MH;
     V v[1][E];
@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(256) k_fx(R* __restrict__ grid, typename Cpx<R
         const V fe = V{R(0.5) * (zk.x + zc.x), R(0.5) * (zk.y + zc.y)};
         const V d = csub(zk, zc);
         const V fo = V{R(0.5) * d.y, R(-0.5) * d.x};  // -i/2 (zk - zc)
-        C1[(size_t)row * Kx + k] = cadd(fe, cmul(sW[k], fo));
+        if (ENUF_IN((size_t)row * Kx + k, (size_t)nrows * Kx)) C1[(size_t)row * Kx + k] = cadd(fe, cmul(sW[k], fo));
     }
 }
 
@@ -392,9 +392,9 @@ __global__ void __launch_bounds__(1024) k_fxy(R* __restrict__ grid, typename Cpx
     V* sW = plane + ((Kx + CB - 1) / CB) * CB * LD;
     stage_twiddles(sW, Wg, M);
     pdl_wait();
-    const int z = blockIdx.x;
+    const int z0 = blockIdx.x, z = ENUF_CLAMP(z0, M);
     V* gin = reinterpret_cast<V*>(grid + (size_t)z * M * M);
-    const int r = threadIdx.x / NTX, tx = threadIdx.x % NTX;
+    const int r0 = threadIdx.x / NTX, tx = threadIdx.x % NTX, r = ENUF_CLAMP(r0, RB);
     cp_async_wait_all();
     __syncthreads();
     for (int y0 = 0; y0 < M; y0 += RB) {
@@ -427,10 +427,11 @@ __global__ void __launch_bounds__(1024) k_fxy(R* __restrict__ grid, typename Cpx
         }
         __syncthreads();
     }
-    const int ty = threadIdx.x / CB, w = threadIdx.x - ty * CB;  // ty < NT(M): blockDim = CB NT(M)
+    const int ty0 = threadIdx.x / CB, w = threadIdx.x - ty0 * CB;
+    const int ty = ENUF_CLAMP(ty0, NTY);  // ty < NT(M): blockDim = CB NT(M)
     V* dst = C2 + (size_t)z * Kb * Kx;
     for (int k0 = 0; k0 < Kx; k0 += CB) {
-        const int kx = k0 + w;
+        const int kx = ENUF_CLAMP(k0 + w, ((Kx + CB - 1) / CB) * CB);
         V* col = plane + kx * LD;
         V v[1][EY];
 #pragma unroll
@@ -444,7 +445,7 @@ __global__ void __launch_bounds__(1024) k_fxy(R* __restrict__ grid, typename Cpx
                 int kb = -1;
                 if (ky <= nc) kb = ky;
                 else if (ky >= M - nc) kb = ky - (M - Kb);
-                if (kb >= 0) dst[(size_t)kb * Kx + kx] = v[0][m];
+                if (kb >= 0 && ENUF_IN(kb, Kb)) dst[(size_t)kb * Kx + kx] = v[0][m];
             }
         }
     }
@@ -463,9 +464,10 @@ __global__ void __launch_bounds__(1024) k_fy(const typename Cpx<R>::T* __restric
     extern __shared__ __align__(16) unsigned char smraw[];
     V* s = reinterpret_cast<V*>(smraw);
     const int Wc = g.W, Kx = g.Kx, Kb = g.Kb, nc = g.nc;
-    const int kx0 = blockIdx.x * Wc, z = blockIdx.y;
+    const int kx0 = blockIdx.x * Wc, z = ENUF_CLAMP((int)blockIdx.y, M);
     const V* sW = stage_twiddles(s + Wc * LD, Wg, M);
-    const int t = (int)g.fW.div(threadIdx.x), w = threadIdx.x - t * Wc, kx = kx0 + w;
+    const int t0 = (int)g.fW.div(threadIdx.x), w = threadIdx.x - t0 * Wc, kx = kx0 + w;
+    const int t = ENUF_CLAMP(t0, NT);
     V v[1][E];
 #pragma unroll
     for (int m = 0; m < E; m++)
@@ -480,7 +482,7 @@ __global__ void __launch_bounds__(1024) k_fy(const typename Cpx<R>::T* __restric
         int kb = -1;
         if (ky <= nc) kb = ky;
         else if (ky >= M - nc) kb = ky - (M - Kb);
-        if (kb >= 0) C2[((size_t)z * Kb + kb) * Kx + kx] = v[0][m];
+        if (kb >= 0 && ENUF_IN(kb, Kb)) C2[((size_t)z * Kb + kb) * Kx + kx] = v[0][m];
     }
 }
 
@@ -533,7 +535,8 @@ __global__ void __launch_bounds__(512) k_fz(const typename Cpx<R>::T* __restrict
     // thread (w, t) = (tid % W, tid / W) serves pencil p0 + w, elements
     // z = t + NT m (neighbouring threads read neighbouring pencils)
     const int p0 = blockIdx.x * Wc;
-    const int t = (int)g.fW.div(threadIdx.x), w = threadIdx.x - t * Wc, p = p0 + w;
+    const int t0 = (int)g.fW.div(threadIdx.x), w = threadIdx.x - t0 * Wc, p = p0 + w;
+    const int t = ENUF_CLAMP(t0, NT);
     V v[1][E];
 #pragma unroll
     for (int m = 0; m < E; m++) v[0][m] = p < P ? C2[(size_t)(t + NT * m) * P + p] : V{R(0), R(0)};
@@ -550,7 +553,7 @@ __global__ void __launch_bounds__(512) k_fz(const typename Cpx<R>::T* __restrict
         const int kb = (int)g.fKx.div(p);
         nx = p - kb * Kx;
         ny = kb <= nc ? kb : kb - Kb;
-        pv = true;
+        pv = ENUF_IN(nx, Kx) && ENUF_IN(ny + nc, Kb);
     }
     const R kxv = pv ? tk[nx + nc] : R(0), kyv = pv ? tk[Kb + ny + nc] : R(0);
     const R exy = pv ? te[nx + nc] * te[Kb + ny + nc] : R(0), dxy = pv ? td[nx + nc] * td[Kb + ny + nc] : R(0);
@@ -597,7 +600,9 @@ __global__ void __launch_bounds__(512) k_fz(const typename Cpx<R>::T* __restrict
 #pragma unroll
         for (int f = 0; f < NB; f++) {
 #pragma unroll
-            for (int m = 0; m < E; m++) C3[((size_t)f * M + t + NT * m) * P + p] = fv[f][m];
+            for (int m = 0; m < E; m++)
+                if (ENUF_IN(((size_t)f * M + t + NT * m) * P + p, (size_t)NB * M * P))
+                    C3[((size_t)f * M + t + NT * m) * P + p] = fv[f][m];
         }
     }
 }
@@ -631,7 +636,8 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512) k_fzw(const typen
     const R* td = stab + 6 * Kb;
     pdl_wait();
     const int p0 = blockIdx.x * Wc;
-    const int t = (int)g.fW.div(threadIdx.x), w = threadIdx.x - t * Wc, p = p0 + w;
+    const int t0 = (int)g.fW.div(threadIdx.x), w = threadIdx.x - t0 * Wc, p = p0 + w;
+    const int t = ENUF_CLAMP(t0, NT);
     V v[1][E];
 #pragma unroll
     for (int m = 0; m < E; m++) v[0][m] = p < P ? C2[(size_t)(t + NT * m) * P + p] : V{R(0), R(0)};
@@ -650,7 +656,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512) k_fzw(const typen
         const int kb = (int)g.fKx.div(p);
         nx = p - kb * Kx;
         ny = kb <= nc ? kb : kb - Kb;
-        pv = true;
+        pv = ENUF_IN(nx, Kx) && ENUF_IN(ny + nc, Kb);
     }
     const R kxv = pv ? tk[nx + nc] : R(0), kyv = pv ? tk[Kb + ny + nc] : R(0);
     const R exy = pv ? te[nx + nc] * te[Kb + ny + nc] : R(0), dxy = pv ? td[nx + nc] * td[Kb + ny + nc] : R(0);
@@ -698,7 +704,9 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512) k_fzw(const typen
         fft_reg<V, M, true, MR>(fv, buf, t, sW, 1);
         if (p < P) {
 #pragma unroll
-            for (int m = 0; m < E; m++) C3[((size_t)f * M + t + NT * m) * P + p] = fv[0][m];
+            for (int m = 0; m < E; m++)
+                if (ENUF_IN(((size_t)f * M + t + NT * m) * P + p, (size_t)NF * M * P))
+                    C3[((size_t)f * M + t + NT * m) * P + p] = fv[0][m];
         }
     }
 }
@@ -743,7 +751,8 @@ __global__ void __launch_bounds__(512) k_fz_spectrum(const typename Cpx<R>::T* _
             const R d = sqrt(td[kx + nc] * td[Kb + ny + nc] * td[2 * Kb + kbz]);
             v = V{d * v.x, d * v.y};
         }
-        out[((size_t)kbz * Kb + (ny + nc)) * Kx + kx] = v;
+        if (ENUF_IN(((size_t)kbz * Kb + (ny + nc)) * Kx + kx, (size_t)Kb * Kb * Kx))
+            out[((size_t)kbz * Kb + (ny + nc)) * Kx + kx] = v;
     }
 }
 
@@ -761,9 +770,10 @@ __global__ void __launch_bounds__(1024) k_iy(const typename Cpx<R>::T* __restric
     extern __shared__ __align__(16) unsigned char smraw[];
     V* s = reinterpret_cast<V*>(smraw);
     const int Wc = g.W, Kx = g.Kx, Kb = g.Kb, nc = g.nc, P = g.P;
-    const int kx0 = blockIdx.x * Wc, z = blockIdx.y, f = blockIdx.z;
+    const int kx0 = blockIdx.x * Wc, z = ENUF_CLAMP((int)blockIdx.y, M), f = blockIdx.z;
     const V* W = stage_twiddles(s + Wc * LD, Wg, M);
-    const int t = (int)g.fW.div(threadIdx.x), w = threadIdx.x - t * Wc, kx = kx0 + w;
+    const int t0 = (int)g.fW.div(threadIdx.x), w = threadIdx.x - t0 * Wc, kx = kx0 + w;
+    const int t = ENUF_CLAMP(t0, NT);
     const V* src = C3 + ((size_t)f * M + z) * P;
     V v[1][E];
 #pragma unroll
@@ -774,7 +784,7 @@ __global__ void __launch_bounds__(1024) k_iy(const typename Cpx<R>::T* __restric
             if (y <= nc) kb = y;
             else if (y >= M - nc) kb = y - (M - Kb);
         }
-        v[0][m] = kb >= 0 ? src[(size_t)kb * Kx + kx] : V{R(0), R(0)};
+        v[0][m] = (kb >= 0 && ENUF_IN(kb, Kb)) ? src[(size_t)kb * Kx + kx] : V{R(0), R(0)};
     }
     cp_async_wait_all();
     __syncthreads();
@@ -815,16 +825,17 @@ __global__ void __launch_bounds__(IyxBounds<R, M>::T, IyxBounds<R, M>::B) k_iyx(
     V* sW = plane + KxR * LD;
     stage_twiddles(sW, Wg, M);
     pdl_wait();
-    const int z = blockIdx.x, f = blockIdx.y;
+    const int z0 = blockIdx.x, z = ENUF_CLAMP(z0, M), f = blockIdx.y;
     const V* src = C3 + ((size_t)f * M + z) * P;
     // inverse y: thread (w, t) = (tid % CB, tid / CB) on column k0 + w loads
     // its band elements y = t + NT m straight from C3 (neighbouring threads
     // read neighbouring kx)
-    const int ty = threadIdx.x / CB, w = threadIdx.x - ty * CB;  // ty < NT(M): blockDim = CB NT(M)
+    const int ty0 = threadIdx.x / CB, w = threadIdx.x - ty0 * CB;
+    const int ty = ENUF_CLAMP(ty0, NTY);  // ty < NT(M): blockDim = CB NT(M)
     cp_async_wait_all();
     __syncthreads();
     for (int k0 = 0; k0 < Kx; k0 += CB) {
-        const int kx = k0 + w;
+        const int kx = ENUF_CLAMP(k0 + w, KxR);
         V v[1][EY];
 #pragma unroll
         for (int m = 0; m < EY; m++) {
@@ -834,7 +845,7 @@ __global__ void __launch_bounds__(IyxBounds<R, M>::T, IyxBounds<R, M>::B) k_iyx(
                 if (y <= nc) kb = y;
                 else if (y >= M - nc) kb = y - (M - Kb);
             }
-            v[0][m] = kb >= 0 ? src[(size_t)kb * Kx + kx] : V{R(0), R(0)};
+            v[0][m] = (kb >= 0 && ENUF_IN(kb, Kb)) ? src[(size_t)kb * Kx + kx] : V{R(0), R(0)};
         }
         V* col = plane + kx * LD;
         fft_reg<V, M, true>(v, col, ty, sW, 1);
@@ -845,7 +856,7 @@ __global__ void __launch_bounds__(IyxBounds<R, M>::T, IyxBounds<R, M>::B) k_iyx(
     // complex-to-real x per row: thread t of row r forms its inputs from the
     // plane and stores its outputs straight to the field row
     V* out = reinterpret_cast<V*>(fld + ((size_t)f * M + z) * M * M);
-    const int r = threadIdx.x / NTX, tx = threadIdx.x % NTX;
+    const int r0 = threadIdx.x / NTX, tx = threadIdx.x % NTX, r = ENUF_CLAMP(r0, RB);
     for (int y0 = 0; y0 < M; y0 += RB) {
         const int y = y0 + r;
         const bool live = y < M;
@@ -889,7 +900,7 @@ __global__ void __launch_bounds__(256) k_ix(const typename Cpx<R>::T* __restrict
     const V* W = stage_twiddles(s + rows * RS, Wg, M);
     cp_async_wait_all();
     __syncthreads();
-    const int r = threadIdx.x / NT, t = threadIdx.x % NT, row = row0 + r;
+    const int r0 = threadIdx.x / NT, t = threadIdx.x % NT, r = ENUF_CLAMP(r0, rows), row = row0 + r;
     const bool live = row < nrows;
     const V* src = C4 + (size_t)(live ? row : 0) * Kx;
     V v[1][E];

@@ -114,7 +114,8 @@ __global__ void __launch_bounds__(256) k_realspace_cells(int N, const typename R
     R acc[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
     if (i < N) {
         const typename Rec<R>::T ri = rec[i];
-        const uint32_t c = cell_of[i];
+        const uint32_t c0 = cell_of[i];
+        const uint32_t c = ENUF_CLAMP(c0, (uint32_t)(rp.nc[0] * rp.nc[1] * rp.nc[2]));
         const int cx = c % rp.nc[0], cy = (c / rp.nc[0]) % rp.nc[1], cz = c / (rp.nc[0] * rp.nc[1]);
         R f[3] = {R(0), R(0), R(0)}, ph = R(0);
         {
@@ -126,7 +127,8 @@ __global__ void __launch_bounds__(256) k_realspace_cells(int N, const typename R
                     const int nx = (cx + dx + rp.nc[0]) % rp.nc[0];
                     const uint32_t nb = nx + rp.nc[0] * (ny + rp.nc[1] * nz);
                     const R sx = ri.x - (R)dx * rp.h[0], sy = ri.y - (R)dy * rp.h[1], sz = ri.z - (R)dz * rp.h[2];
-                    const uint32_t e = offset[nb + 1];
+                    const uint32_t e0 = offset[nb + 1];
+                    const uint32_t e = ENUF_IN(e0, N + 1) ? e0 : 0u;
                     for (uint32_t j = offset[nb]; j < e; j++) {
                         if ((int)j == i) continue;
                         const typename Rec<R>::T rj = rec[j];
@@ -136,6 +138,10 @@ __global__ void __launch_bounds__(256) k_realspace_cells(int N, const typename R
             }
         }
         const uint32_t oi = perm[i];
+        if (!ENUF_IN(oi, N)) {
+            F = nullptr;
+            phi = nullptr;
+        }
         if (F) {
             atomicAdd(F + 3 * (size_t)oi, rp.ke * f[0]);
             atomicAdd(F + 3 * (size_t)oi + 1, rp.ke * f[1]);
@@ -171,6 +177,10 @@ __global__ void __launch_bounds__(256) k_realspace_allpairs(int N, const typenam
             pair_term<R, SL>(d[0], d[1], d[2], ri.w, rj.w, rp, f, ph, acc);
         }
         const uint32_t oi = perm[i];
+        if (!ENUF_IN(oi, N)) {
+            F = nullptr;
+            phi = nullptr;
+        }
         if (F) {
             F[3 * (size_t)oi] = rp.ke * f[0];
             F[3 * (size_t)oi + 1] = rp.ke * f[1];

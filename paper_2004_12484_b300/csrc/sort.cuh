@@ -207,6 +207,7 @@ __device__ __forceinline__ void scan_bins_block(const ScanArgs& a, int* status, 
         }
         __syncthreads();
         for (int i = tid; i < ns; i += NT) {
+            if (!ENUF_IN(s0 + i, a.nbins)) continue;
             a.offset[s0 + i] = s_a[i];
             if (a.item2) a.item2[s0 + i] = s_b[i];
         }
@@ -283,7 +284,7 @@ __global__ void __launch_bounds__(256) k_bin_keys(int N, const R* __restrict__ p
             b = (b << (3 * g.lr)) | sb;
         }
         key[i] = b;
-        rank[i] = atomicAdd(&count[(size_t)b * cs], 1u);
+        rank[i] = ENUF_IN(b, sa.nbins) ? atomicAdd(&count[(size_t)b * cs], 1u) : 0u;
         typename Rec<R>::T rr;
         rr.x = off[0]; rr.y = off[1]; rr.z = off[2]; rr.w = qq;
         rec[i] = rr;
@@ -440,14 +441,16 @@ __global__ void __launch_bounds__(256) k_scatter(int N, const uint32_t* __restri
                                                  typename Rec<R>::T* __restrict__ rec_out, uint32_t* __restrict__ perm,
                                                  uint32_t* __restrict__ bin_of_sorted,
                                                  const uint32_t* __restrict__ item2, int cap2,
-                                                 int4* __restrict__ work2, int max_work2)
+                                                 int4* __restrict__ work2, int max_work2, int nbins)
 {
     pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const uint32_t b = key[i];
     const uint32_t r = rank[i];
+    if (!ENUF_IN(b, nbins)) return;
     const uint32_t d = offset[b] + r;
+    if (!ENUF_IN(d, N)) return;
     rec_out[d] = rec_in[i];
     perm[d] = (uint32_t)i;
     if (bin_of_sorted) bin_of_sorted[d] = b;

@@ -228,7 +228,7 @@ template <int P, int S> struct SBox {
 template <typename R, int P, int T>
 __global__ void __launch_bounds__(32) k_spread(const int4* __restrict__ work, const int* __restrict__ nwork,
                                                const typename Rec<R>::T* __restrict__ rec, int M, int lnb, int lr,
-                                               WinC<R> wc, R cnorm3, R* __restrict__ grid)
+                                               WinC<R> wc, R cnorm3, R* __restrict__ grid, int N)
 {
     constexpr int S = T < 8 ? T : 8;
     using B = SBox<P, S>;
@@ -248,6 +248,7 @@ __global__ void __launch_bounds__(32) k_spread(const int4* __restrict__ work, co
     const int nbm = (1 << lnb) - 1;
     const int tx = tile & nbm, ty = (tile >> lnb) & nbm, tz = tile >> (2 * lnb);
     const int a = lane % G;
+    if (!(ENUF_IN(tz, nbm + 1) && ENUF_IN(w.y, w.z) && ENUF_IN(w.z - 1, N))) return;
     __syncwarp();
 
     // p = 8: the warp's 32 records go through shared memory (one broadcast
@@ -287,6 +288,10 @@ __global__ void __launch_bounds__(32) k_spread(const int4* __restrict__ work, co
             ix -= sx * S;  // cell inside the sub-tile, 0..S-1 (the bin was
             iy -= sy * S;  // chosen from the same split)
             iz -= sz * S;
+            if (!(ENUF_IN(ix, S) && ENUF_IN(iy, S) && ENUF_IN(iz, S))) {  // uniform for the warp
+                __syncwarp();
+                continue;
+            }
             const R ua = dx + (R)(m - 1 - (a % P));
             const R wx = rq * cnorm3 * win_exp(ua * ua, wc);
             constexpr int RPI = 32 / G;
@@ -357,7 +362,8 @@ __global__ void __launch_bounds__(32) k_spread(const int4* __restrict__ work, co
             const float4 v = *reinterpret_cast<const float4*>(acc + lz * PS + ly * BX + 4 * vx);
             if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) {
                 const int gx = (ox + 4 * vx) & mask, gy = (oy + ly) & mask, gz = (oz + lz) & mask;
-                atomicAdd(reinterpret_cast<float4*>(grid + ((size_t)gz * M + gy) * M + gx), v);
+                const size_t gi = ((size_t)gz * M + gy) * M + gx;
+                if (ENUF_IN(gi + 3, (size_t)M * M * M)) atomicAdd(reinterpret_cast<float4*>(grid + gi), v);
             }
         }
     } else {
@@ -367,7 +373,8 @@ __global__ void __launch_bounds__(32) k_spread(const int4* __restrict__ work, co
             const R v = acc[lz * PS + ly * BX + lx];
             if (v != R(0)) {
                 const int gx = (ox + lx) & mask, gy = (oy + ly) & mask, gz = (oz + lz) & mask;
-                atomicAdd(grid + ((size_t)gz * M + gy) * M + gx, v);
+                const size_t gi = ((size_t)gz * M + gy) * M + gx;
+                if (ENUF_IN(gi, (size_t)M * M * M)) atomicAdd(grid + gi, v);
             }
         }
     }
@@ -382,7 +389,7 @@ __global__ void __launch_bounds__(32) k_spread(const int4* __restrict__ work, co
 template <typename R, int P, int T, int NF, int ZS, typename OIdx>
 __device__ __forceinline__ void interp_unit(const R* s, R* wyz, const typename Rec<R>::T* srec, int n, int z0,
                                             const WinC<R>& wc, R cnorm3, R* __restrict__ F, R* __restrict__ phi,
-                                            OIdx&& oidx)
+                                            OIdx&& oidx, int N)
 {
     using B = Box<P, T, ZS>;
     constexpr int PT = B::PT, BX = B::BX, C = B::CELLS, m = P / 2, G = GroupOf<P>::G;
@@ -396,6 +403,7 @@ __device__ __forceinline__ void interp_unit(const R* s, R* wyz, const typename R
         split_offset<R, T>(r.y, iy, dy);
         split_offset<R, T>(r.z, iz, dz);
         iz -= z0;
+        if (!(ENUF_IN(ix, T) && ENUF_IN(iy, T) && ENUF_IN(iz, ZS))) continue;  // uniform for the warp
         const R ua = dx + (R)(m - 1 - (a % P));
         const R wx = win_exp(ua * ua, wc);
         const R* base = s + (iz * PT + iy) * BX + ix + B::XOFF + a;
@@ -413,7 +421,8 @@ __device__ __forceinline__ void interp_unit(const R* s, R* wyz, const typename R
         if ((lane & 7) == 0) {
             const int f = lane >> 3;
             const uint32_t oi = oidx(k);
-            if (f < 3) {
+            if (!ENUF_IN(oi, N)) {
+            } else if (f < 3) {
                 if (F) F[3 * (size_t)oi + f] = r.w * cnorm3 * tot;
             } else if (NF == 4 && phi) {
                 phi[oi] = cnorm3 * tot;
@@ -435,7 +444,7 @@ __global__ void __launch_bounds__(NTH) k_gather(const int4* __restrict__ work, c
                                                 const typename Rec<R>::T* __restrict__ rec,
                                                 const uint32_t* __restrict__ perm, int M, int lnbx, int lnby,
                                                 WinC<R> wc, R cnorm3, const R* __restrict__ fld, R* __restrict__ F,
-                                                R* __restrict__ phi)
+                                                R* __restrict__ phi, int N)
 {
     using B = Box<P, T, ZS>;
     constexpr int PT = B::PT, PZ = B::PZ, BX = B::BX, C = B::CELLS, m = P / 2, G = GroupOf<P>::G;
@@ -451,6 +460,11 @@ __global__ void __launch_bounds__(NTH) k_gather(const int4* __restrict__ work, c
     const int ox = tx * T - B::XA, oy = ty * T - (m - 1), oz = tz * T + z0 - (m - 1);
     const int mask = M - 1;
     const size_t M3 = (size_t)M * M * M;
+    if (!(ENUF_IN(tz, M / T) && ENUF_IN(w.y, w.z) && ENUF_IN(w.z - 1, N) &&
+          ENUF_IN((NF * C + (blockDim.x >> 5) * WyzTable<P>::N) * sizeof(R) +
+                      (size_t)(w.z - w.y) * (sizeof(typename Rec<R>::T) + 4) - 1,
+                  dynamic_smem_bytes())))
+        return;  // uniform for the CTA
     // stage the box of every field with 16-byte loads
     constexpr int EV = 16 / sizeof(R);  // elements per 16-byte vector
     constexpr int NV = BX / EV;
@@ -472,7 +486,7 @@ __global__ void __launch_bounds__(NTH) k_gather(const int4* __restrict__ work, c
     __syncthreads();
 
     interp_unit<R, P, T, NF, ZS>(s, s + NF * C + (threadIdx.x >> 5) * WyzTable<P>::N, srec, w.z - w.y, z0, wc,
-                                 cnorm3, F, phi, [&](int k) { return sperm[k]; });
+                                 cnorm3, F, phi, [&](int k) { return sperm[k]; }, N);
 }
 
 // Interpolation for windows of p = 8 on 16-cell tiles in z-halves, single
@@ -500,7 +514,7 @@ __global__ void __launch_bounds__(512, 2) k_gather_p8(const int4* __restrict__ w
                                                       int M, int lnb, WinC<float> wc, float cnorm3,
                                                       const float* __restrict__ fld,
                                                       const __grid_constant__ CUtensorMap tmap, float* __restrict__ F,
-                                                      float* __restrict__ phi, int* __restrict__ status)
+                                                      float* __restrict__ phi, int* __restrict__ status, int N)
 {
     using G8 = GatherP8<NF>;
     using B = typename G8::B;
@@ -519,6 +533,7 @@ __global__ void __launch_bounds__(512, 2) k_gather_p8(const int4* __restrict__ w
     const int nbm = (1 << lnb) - 1;
     const int tx = tile & nbm, ty = (tile >> lnb) & nbm, tz = tile >> (2 * lnb);
     const int ox = tx * 16 - B::XA, oy = ty * 16 - 3, oz = tz * 16 + z0 - 3;
+    if (!(ENUF_IN(tz, nbm + 1) && ENUF_IN(n - 1, G8::CAP) && ENUF_IN(w.z - 1, N))) return;  // uniform for the CTA
     if (threadIdx.x == 0) {
         mbar_arrive_expect_tx(bar, (uint32_t)(NF * B::CELLS * 4 + n * 16));
 #pragma unroll
@@ -545,6 +560,7 @@ __global__ void __launch_bounds__(512, 2) k_gather_p8(const int4* __restrict__ w
             if (gx >= 0 && gx < M && gy >= 0 && gy < M && gz >= 0 && gz < M) continue;
             const size_t gi = ((size_t)(gz & mask) * M + (gy & mask)) * M + (gx & mask);
             const int si = (lz * PT + ly) * BX + 4 * vx;
+            if (!ENUF_IN(gi + 3, M3)) continue;
 #pragma unroll
             for (int f = 0; f < NF; f++) cp_async_bytes16(s + f * C + si, fld + f * M3 + gi, true);
         }
@@ -563,6 +579,7 @@ __global__ void __launch_bounds__(512, 2) k_gather_p8(const int4* __restrict__ w
         split_offset<float, 16>(r.y, iy, dy);
         split_offset<float, 16>(r.z, iz, dz);
         iz -= z0;
+        if (!(ENUF_IN(ix, 16) && ENUF_IN(iy, 16) && ENUF_IN(iz, 8))) continue;  // uniform for the warp
         const float ux = dx + (float)(3 - a), uy = dy + (float)(3 - a);
         const float wx = win_exp(ux * ux, wc), wya = win_exp(uy * uy, wc);
         float wz[8];
@@ -585,7 +602,7 @@ __global__ void __launch_bounds__(512, 2) k_gather_p8(const int4* __restrict__ w
         for (int f = 0; f < NF; f++) acc[f] = wx * fmaf(wy0, s0[f], wy1 * s1[f]);
         // lane 8 f holds the total of field f
         const float tot = warp_sum4(acc, lane);
-        if ((lane & 7) == 0) {
+        if ((lane & 7) == 0 && ENUF_IN(oi, N)) {
             const int f = lane >> 3;
             if (f < 3) {
                 if (F) F[3 * (size_t)oi + f] = r.w * cnorm3 * tot;
@@ -611,7 +628,8 @@ __global__ void __launch_bounds__(NTH) k_gather_ad(const int4* __restrict__ work
                                                    const typename Rec<R>::T* __restrict__ rec,
                                                    const uint32_t* __restrict__ perm, int M, int lnbx, int lnby,
                                                    WinC<R> wc, R cnorm3, R fa0, R fa1, R fa2,
-                                                   const R* __restrict__ fld, R* __restrict__ F, R* __restrict__ phi)
+                                                   const R* __restrict__ fld, R* __restrict__ F, R* __restrict__ phi,
+                                                   int N)
 {
     using B = Box<P, T, ZS>;
     constexpr int PT = B::PT, PZ = B::PZ, BX = B::BX, C = B::CELLS, m = P / 2, G = GroupOf<P>::G;
@@ -626,6 +644,11 @@ __global__ void __launch_bounds__(NTH) k_gather_ad(const int4* __restrict__ work
     const int tx = tile & ((1 << lnbx) - 1), ty = (tile >> lnbx) & ((1 << lnby) - 1), tz = tile >> (lnbx + lnby);
     const int ox = tx * T - B::XA, oy = ty * T - (m - 1), oz = tz * T + z0 - (m - 1);
     const int mask = M - 1;
+    if (!(ENUF_IN(tz, M / T) && ENUF_IN(w.y, w.z) && ENUF_IN(w.z - 1, N) &&
+          ENUF_IN((C + (blockDim.x >> 5) * WyzTable<P>::N) * sizeof(R) +
+                      (size_t)(w.z - w.y) * (sizeof(typename Rec<R>::T) + 4) - 1,
+                  dynamic_smem_bytes())))
+        return;  // uniform for the CTA
     constexpr int EV = 16 / sizeof(R);
     constexpr int NV = BX / EV;
     for (int i = threadIdx.x; i < NV * PT * PZ; i += blockDim.x) {
@@ -653,6 +676,7 @@ __global__ void __launch_bounds__(NTH) k_gather_ad(const int4* __restrict__ work
         split_offset<R, T>(r.y, iy, dy);
         split_offset<R, T>(r.z, iz, dz);
         iz -= z0;
+        if (!(ENUF_IN(ix, T) && ENUF_IN(iy, T) && ENUF_IN(iz, ZS))) continue;  // uniform for the warp
         const R ux = dx + (R)(m - 1 - (a % P));
         const R wx = win_exp(ux * ux, wc);
         const R* base = s + (iz * PT + iy) * BX + ix + B::XOFF + a;
@@ -697,7 +721,7 @@ __global__ void __launch_bounds__(NTH) k_gather_ad(const int4* __restrict__ work
             acc[3] = sz;
         }
         const R tot = warp_sum4(acc, lane);
-        if ((lane & 7) == 0) {
+        if ((lane & 7) == 0 && ENUF_IN(sperm[j - w.y], N)) {
             const int f = lane >> 3;
             const uint32_t oi = sperm[j - w.y];
             if (f == 0) {
@@ -738,6 +762,7 @@ __global__ void __launch_bounds__(256) k_gather_direct(int N, const typename Rec
     split_offset<R, T>(r.x, ix, dx);
     split_offset<R, T>(r.y, iy, dy);
     split_offset<R, T>(r.z, iz, dz);
+    if (!(ENUF_IN(tz, M / T) && ENUF_IN(perm[j], N))) return;  // whole groups leave together
     R wy[P], wz[P];
     window_weights<R, P>(dy, wc, wy);
     window_weights<R, P>(dz, wc, wz);
@@ -808,6 +833,7 @@ __global__ void __launch_bounds__(256) k_gather_direct_ad(int N, const typename 
     split_offset<R, T>(r.x, ix, dx);
     split_offset<R, T>(r.y, iy, dy);
     split_offset<R, T>(r.z, iz, dz);
+    if (!(ENUF_IN(tz, M / T) && ENUF_IN(perm[j], N))) return;  // whole groups leave together
     R wy[P], wz[P];
     window_weights<R, P>(dy, wc, wy);
     window_weights<R, P>(dz, wc, wz);

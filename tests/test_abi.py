@@ -25,6 +25,23 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, n), n
 
 
+def test_checked_build_exports_the_same_symbols():
+    """libenuf_check.so (bounds checks in every kernel) has the same entry
+    points as libenuf.so and says that it is the checked build; libenuf.so
+    says that it is not."""
+    chk = ctypes.CDLL(os.path.join(os.path.dirname(P.LIB_PATH), "libenuf_check.so"))
+    for n in declared_functions():
+        assert hasattr(chk, n), n
+    rel = ctypes.CDLL(os.path.join(os.path.dirname(P.LIB_PATH), "libenuf.so"))
+    assert chk.enuf_bounds_checked() == 1
+    assert rel.enuf_bounds_checked() == 0
+    # without a GPU the release library still answers: no checks, no failures
+    fails = ctypes.c_ulonglong(5)
+    assert rel.enuf_bounds_status(ctypes.byref(fails), None, 0, 0) == 0
+    assert fails.value == 0
+    assert rel.enuf_bounds_selftest() == -1  # ENUF_EINVAL: not the checked build
+
+
 def test_probe_library_is_separate_and_exports_its_header():
     """The benchmark's FMA probe lives in its own library, not in libenuf.so."""
     lib = P.lib()
