@@ -396,17 +396,16 @@ def large_systems(P, dev, timed, kspace, flush, peak):
             r["kspace_hbm_frac"] = r["kspace_algorithmic_bytes"] / (ms * 1e-3) / 1e9 / peak
             kspace(plan, tp, tq, F, out)
             Fk = F.double()  # the k-space forces, for the comparison with the FP64 path
-            if name.startswith("polyelectrolyte"):
-                # full steps (real space included) with point charges and, at
-                # the stated settings, with the ENUF-DPD smeared charges
-                # (lambda_e = sigma / 1.125)
-                ms_full, _ = timed(lambda: plan.compute(tp, tq, forces=True, virial=True, F=F, out=out), 10, 3)
-                r["ms_full_step"] = ms_full
-                if name == "polyelectrolyte":
-                    plan_s = P.Plan(precision="mixed", slater_lambda=1.0 / 1.125, **kw)
-                    ms_dpd, _ = timed(lambda: plan_s.compute(tp, tq, forces=True, virial=True, F=F, out=out), 10, 3)
-                    r.update({"ms_full_step_slater": ms_dpd, "value_full_step_slater": N / (ms_dpd * 1e-3) / 1e6})
-                    del plan_s
+            # full steps (real space included) with point charges and, for
+            # the polyelectrolyte at its stated settings, with the ENUF-DPD
+            # smeared charges (lambda_e = sigma / 1.125)
+            ms_full, _ = timed(lambda: plan.compute(tp, tq, forces=True, virial=True, F=F, out=out), 10, 3)
+            r["ms_full_step"] = ms_full
+            if name == "polyelectrolyte":
+                plan_s = P.Plan(precision="mixed", slater_lambda=1.0 / 1.125, **kw)
+                ms_dpd, _ = timed(lambda: plan_s.compute(tp, tq, forces=True, virial=True, F=F, out=out), 10, 3)
+                r.update({"ms_full_step_slater": ms_dpd, "value_full_step_slater": N / (ms_dpd * 1e-3) / 1e6})
+                del plan_s
             del plan
             torch.cuda.empty_cache()
             # the FP64 path on the same inputs
