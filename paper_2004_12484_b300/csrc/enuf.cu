@@ -182,11 +182,17 @@ int resolve(const enuf_params* in, Resolved& r)
         while ((size_t)(W * (padlen(M) + 1) + M) * vsz > (size_t)kMaxSmem) W -= gran;
         r.gy = FftGeom{r.nc, r.Kx, r.Kb, r.P, W, 0};
     }
-    // k_fzw for M = 512: 16 pencils a CTA of 16 M/8 threads (8 in double
-    // precision), one buffer per pencil
+    // k_fzw for M = 512: 8 pencils a CTA of 8 M/8 threads, one buffer per
+    // pencil (two CTAs an SM: 0.293 ms at the ionic-liquid size against
+    // 0.307 with 16 pencils in one CTA of 1024 threads)
     r.fz_wide = M >= 512 && !std::getenv("ENUF_FZ_NARROW");
     if (r.fz_wide) {
-        r.gz = FftGeom{r.nc, r.Kx, r.Kb, r.P, r.fp64 ? 8 : 16, 0};
+        int W = 8;
+        if (const char* wv = std::getenv("ENUF_FZ_W")) {  // tuning knob: 4, 8 or 16 pencils a CTA
+            const int w = std::atoi(wv);
+            if (w == 4 || w == 8 || (w == 16 && !r.fp64)) W = w;
+        }
+        r.gz = FftGeom{r.nc, r.Kx, r.Kb, r.P, W, 0};
     } else
     // k_fz: pencils per block (at most 512 threads: the batched inverse
     // transforms of four fields need up to 128 registers per thread); its
@@ -903,7 +909,8 @@ int launch_sequence(Launcher& L, enuf_plan* pl, const R* pos, const R* q, R* F, 
     }
     LCHK(L.go("scatter", k_scatter<R>, dim3(nblkN), dim3(256), 0, N, at<const uint32_t>(pl, y.key),
               at<const uint32_t>(pl, y.rank), at<const uint32_t>(pl, y.offsets), at<const RecT>(pl, y.rec_tmp),
-              at<RecT>(pl, y.rec), at<uint32_t>(pl, y.perm), at<uint32_t>(pl, y.tile_of),
+              at<RecT>(pl, y.rec), at<uint32_t>(pl, y.perm),
+              r.gather_direct ? at<uint32_t>(pl, y.tile_of) : (uint32_t*)nullptr,  // read only by the direct gathers
               at<const uint32_t>(pl, y.item2), kSpreadCap, at<int4>(pl, y.work2), r.max_work2, r.nbins));
     // (a3) spread (into a zeroed grid: zeroed at binding, then by the
     // forward FFT that reads it)

@@ -105,7 +105,7 @@ def test_structure_factor_is_additive_and_checks_inputs():
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 2e-6)])
 def test_wide_z_pass_matches_narrow_at_512(precision, tol, monkeypatch):
-    """At M = 512 the z pass is k_fzw (16 pencils a CTA, radix 8, fields one
+    """At M = 512 the z pass is k_fzw (8 pencils a CTA, radix 8, fields one
     after the other); ENUF_FZ_NARROW=1 selects the z pass of the smaller
     grids, which the oracle checks at M <= 256.  Both give the same energy,
     forces, potentials and virial (a small system on the 512^3 grid)."""
