@@ -178,7 +178,7 @@ int resolve(const enuf_params* in, Resolved& r)
         const int cw = M >= 512 ? 8 : 16;
         int nch = (r.Kx + cw - 1) / cw;
         int W = round_up((r.Kx + nch - 1) / nch, gran);
-        while (W * NT > 1024) W -= gran;
+        while (W * NT > (M >= 512 ? 512 : 1024)) W -= gran;  // the launch bounds of k_fy / k_iy
         while ((size_t)(W * (padlen(M) + 1) + M) * vsz > (size_t)kMaxSmem) W -= gran;
         r.gy = FftGeom{r.nc, r.Kx, r.Kb, r.P, W, 0};
     }

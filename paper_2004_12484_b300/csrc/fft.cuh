@@ -318,6 +318,17 @@ struct FftGeom {
     FDiv fKx, fW, fKxR;  // division by Kx, W and (k_iyx) Kx rounded up to its column batch
 };
 
+// Launch bounds of the separate passes of the 512 grid in single precision:
+// CTAs of at most 512 threads for the y passes, three of them an SM (at
+// most 40 registers; ionic-liquid inverse y 0.495 -> 0.395 ms, forward y
+// 0.156 -> 0.137 ms against two), and for the 256-thread x-row passes five
+// (forward x, 0.238 -> 0.225 ms) or four (inverse x: with five, 0.608 ->
+// 0.614 ms; with six both spill).
+template <typename R, int M> struct SepBounds {
+    static constexpr bool big = M >= 512 && sizeof(R) == 4;
+    static constexpr int YT = big ? 512 : 1024, YB = big ? 3 : 1, FXB = big ? 5 : 1, IXB = big ? 4 : 1;
+};
+
 // ---------------------------------------------------------------- k_fx
 // grid: ceil(M*M / rows) blocks, rows * NT(M/2) threads.  Clears the grid
 // rows it reads (the spreading accumulates into a zeroed grid).  Thread t of
@@ -327,7 +338,7 @@ struct FftGeom {
 // (Z_k - conj Z_{M/2-k}) of the kept kx <= n_c reads the partners from
 // shared memory.
 template <typename R, int M>
-__global__ void __launch_bounds__(256) k_fx(R* __restrict__ grid, typename Cpx<R>::T* __restrict__ C1, FftGeom g,
+__global__ void __launch_bounds__(256, SepBounds<R, M>::FXB) k_fx(R* __restrict__ grid, typename Cpx<R>::T* __restrict__ C1, FftGeom g,
                      const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
@@ -456,7 +467,7 @@ __global__ void __launch_bounds__(1024) k_fxy(R* __restrict__ grid, typename Cpx
 // W, tid / W) serves column kx0 + w: loads y = t + NT m straight from C1,
 // register passes, stores the band rows to C2.
 template <typename R, int M>
-__global__ void __launch_bounds__(1024) k_fy(const typename Cpx<R>::T* __restrict__ C1, typename Cpx<R>::T* __restrict__ C2, FftGeom g,
+__global__ void __launch_bounds__(SepBounds<R, M>::YT, SepBounds<R, M>::YB) k_fy(const typename Cpx<R>::T* __restrict__ C1, typename Cpx<R>::T* __restrict__ C2, FftGeom g,
                      const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
@@ -762,7 +773,7 @@ __global__ void __launch_bounds__(512) k_fz_spectrum(const typename Cpx<R>::T* _
 // y = t + NT m straight from C3 (neighbouring threads read neighbouring
 // columns), transforms with register passes and stores its outputs to C4.
 template <typename R, int M>
-__global__ void __launch_bounds__(1024) k_iy(const typename Cpx<R>::T* __restrict__ C3, typename Cpx<R>::T* __restrict__ C4, FftGeom g,
+__global__ void __launch_bounds__(SepBounds<R, M>::YT, SepBounds<R, M>::YB) k_iy(const typename Cpx<R>::T* __restrict__ C3, typename Cpx<R>::T* __restrict__ C4, FftGeom g,
                      const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
@@ -889,7 +900,7 @@ __global__ void __launch_bounds__(IyxBounds<R, M>::T, IyxBounds<R, M>::B) k_iyx(
 // forms its inputs z_{t + NT m} from the row in global memory, transforms
 // with register passes and stores its outputs straight to the field row.
 template <typename R, int M>
-__global__ void __launch_bounds__(256) k_ix(const typename Cpx<R>::T* __restrict__ C4, R* __restrict__ fld, FftGeom g, int nrows,
+__global__ void __launch_bounds__(256, SepBounds<R, M>::IXB) k_ix(const typename Cpx<R>::T* __restrict__ C4, R* __restrict__ fld, FftGeom g, int nrows,
                      const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;

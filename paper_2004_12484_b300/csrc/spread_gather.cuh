@@ -134,9 +134,10 @@ __device__ __forceinline__ void window_rows(int a, int g, Fn&& f)
 // Calls f(s, b, c, w) for the window rows this lane serves (see
 // window_rows), with w = wx * wy[b] * wz[c] (wx: the lane's own x weight)
 // and s = 0, 1, ... the lane's step.  For p = 8 and p = 4 the lane's rows
-// fall on fixed y offsets, so the weights stay in registers (two shuffles
-// per particle, wx folded into the y weights); other widths go through the
-// per-warp product table `wyz` in shared memory.
+// fall on fixed y offsets, so the weights stay in registers (p = 8: the
+// lane's two y weights evaluated in the lane; p = 4: one shuffle; wx folded
+// into the y weights); other widths go through the per-warp product table
+// `wyz` in shared memory.
 template <typename R, int P, typename Fn>
 __device__ __forceinline__ void visit_window(R dy, R dz, R wx, const WinC<R>& wc, R* wyz, int lane, Fn&& f)
 {
@@ -145,9 +146,8 @@ __device__ __forceinline__ void visit_window(R dy, R dz, R wx, const WinC<R>& wc
     if constexpr (P == 8) {
         R wz[8];
         window_weights<R, 8>(dz, wc, wz);
-        const R u = dy + (R)(3 - a);
-        const R wya = win_exp(u * u, wc);
-        const R t0 = wx * __shfl_sync(0xffffffffu, wya, g), t1 = wx * __shfl_sync(0xffffffffu, wya, g + 4);
+        const R uy0 = dy + (R)(3 - g), uy1 = dy - (R)(1 + g);
+        const R t0 = wx * win_exp(uy0 * uy0, wc), t1 = wx * win_exp(uy1 * uy1, wc);
 #pragma unroll
         for (int c = 0; c < 8; c++) {
             f(2 * c, g, c, t0 * wz[c]);
@@ -215,8 +215,9 @@ template <int P, int T, int ZS = T> struct Box {
 // sub-tile (lr = log2(T / S)).
 // The spreading box of a sub-tile (S^3 cells): the Box geometry with row
 // stride BX and plane stride PS padded so that the four rows one warp
-// instruction touches start on disjoint groups of 8 banks -- rows (b, c),
-// (b+1, c), (b, c+1), (b+1, c+1) for p = 8, four consecutive rows otherwise.
+// instruction touches start on disjoint groups of 8 banks -- the same row of
+// four consecutive planes for p = 8 (PS = 24 banks mod 32), four consecutive
+// rows otherwise.
 template <int P, int S> struct SBox {
     using B0 = Box<P, S>;
     static constexpr int m = P / 2, XA = B0::XA, XOFF = B0::XOFF, PT = B0::PT;
@@ -297,31 +298,28 @@ __global__ void __launch_bounds__(32) k_spread(const int4* __restrict__ work, co
             constexpr int RPI = 32 / G;
             constexpr int NV = P == 8 ? 16 : (P == 4 ? 2 : (P * P + RPI - 1) / RPI);
             if constexpr (P == 8) {
-                // lane 8 g + a: x-offset a of rows b0 + 2i and planes c0 + 2k
-                // (b0 = g & 1, c0 = g >> 1); every lane evaluates the y and z
-                // weights itself (fast Gaussian gridding: three exponentials
-                // a dimension) rather than taking them by shuffles
-                const int g = lane >> 3, b0 = g & 1, c0 = g >> 1;
-                R wy8[8], wz8[8];
+                // lane 8 g + a: x-offset a of planes g and g + 4 and all eight
+                // rows; every lane evaluates the eight y weights (fast Gaussian
+                // gridding: three exponentials) and its two z weights itself
+                // rather than taking them by shuffles.  The four lane groups
+                // of one access touch planes g + 4 s, PS apart: disjoint
+                // groups of 8 banks.
+                const int g = lane >> 3;
+                R wy8[8];
                 window_weights<R, 8>(dy, wc, wy8);
-                window_weights<R, 8>(dz, wc, wz8);
-                R t[4], wz[4];
-#pragma unroll
-                for (int i = 0; i < 4; i++) {
-                    t[i] = wx * (b0 ? wy8[2 * i + 1] : wy8[2 * i]);
-                    wz[i] = c0 ? wz8[2 * i + 1] : wz8[2 * i];
-                }
-                R* base = acc + (iz + c0) * PS + (iy + b0) * BX + ix + B::XOFF + a;
+                const R uz0 = dz + (R)(3 - g), uz1 = dz - (R)(1 + g);
+                const R t0 = wx * win_exp(uz0 * uz0, wc), t1 = wx * win_exp(uz1 * uz1, wc);
+                R* base = acc + (iz + g) * PS + iy * BX + ix + B::XOFF + a;
                 R old[16];
 #pragma unroll
-                for (int k = 0; k < 4; k++) {
+                for (int s = 0; s < 2; s++) {
 #pragma unroll
-                    for (int i = 0; i < 4; i++) old[4 * k + i] = base[2 * k * PS + 2 * i * BX];
+                    for (int i = 0; i < 8; i++) old[8 * s + i] = base[4 * s * PS + i * BX];
                 }
 #pragma unroll
-                for (int k = 0; k < 4; k++) {
-#pragma unroll
-                    for (int i = 0; i < 4; i++) base[2 * k * PS + 2 * i * BX] = old[4 * k + i] + t[i] * wz[k];
+                for (int i = 0; i < 8; i++) {
+                    base[i * BX] = old[i] + t0 * wy8[i];
+                    base[4 * PS + i * BX] = old[8 + i] + t1 * wy8[i];
                 }
             } else if constexpr (NV <= 16) {
                 R* base = acc + (iz * PS) + iy * BX + ix + B::XOFF + a;
@@ -580,11 +578,13 @@ __global__ void __launch_bounds__(512, 2) k_gather_p8(const int4* __restrict__ w
         split_offset<float, 16>(r.z, iz, dz);
         iz -= z0;
         if (!(ENUF_IN(ix, 16) && ENUF_IN(iy, 16) && ENUF_IN(iz, 8))) continue;  // uniform for the warp
-        const float ux = dx + (float)(3 - a), uy = dy + (float)(3 - a);
-        const float wx = win_exp(ux * ux, wc), wya = win_exp(uy * uy, wc);
+        // the lane's x weight and the y weights of its rows g and g + 4, each
+        // evaluated in the lane (an exponential costs less than a shuffle
+        // through the shared-memory pipe that bounds this kernel)
+        const float ux = dx + (float)(3 - a), uy0 = dy + (float)(3 - g), uy1 = dy - (float)(1 + g);
+        const float wx = win_exp(ux * ux, wc), wy0 = win_exp(uy0 * uy0, wc), wy1 = win_exp(uy1 * uy1, wc);
         float wz[8];
         window_weights<float, 8>(dz, wc, wz);
-        const float wy0 = __shfl_sync(0xffffffffu, wya, g), wy1 = __shfl_sync(0xffffffffu, wya, g + 4);
         const float* base = s + (iz * PT + iy + g) * BX + ix + XOFF + a;
         float s0[NF], s1[NF];
 #pragma unroll
@@ -687,10 +687,8 @@ __global__ void __launch_bounds__(NTH) k_gather_ad(const int4* __restrict__ work
             // with weights wz and u_z wz, then the y weights
             R wz[8];
             window_weights<R, 8>(dz, wc, wz);
-            const R uya = dy + (R)(3 - a);
-            const R wya = win_exp(uya * uya, wc);
-            const R wy0 = __shfl_sync(0xffffffffu, wya, g), wy1 = __shfl_sync(0xffffffffu, wya, g + 4);
             const R uy0 = dy + (R)(3 - g), uy1 = dy - (R)(1 + g);
+            const R wy0 = win_exp(uy0 * uy0, wc), wy1 = win_exp(uy1 * uy1, wc);
             R s0 = R(0), d0 = R(0), s1 = R(0), d1 = R(0);
 #pragma unroll
             for (int c = 0; c < 8; c++) {
