@@ -80,8 +80,9 @@ struct Resolved {
     int sr;        // stencil radius of the linked cells: 2 (edge >= r_c / 2) or 1 (edge >= r_c)
     double h[3];
     FftGeom gfx, gy, gz;
-    int fxy_threads;  // > 0: fused x-y kernels with this block size
-    size_t fxy_smem;
+    int fxy_threads;  // > 0: fused x-y kernels, k_fxy with this block size
+    int iyx_threads;  // and k_iyx with this one
+    size_t fxy_smem, iyx_smem;
     bool gather_direct;  // interpolate straight from L2-resident field planes
     bool fz_wide;        // the z pass is k_fzw (M = 512)
 };
@@ -89,6 +90,19 @@ struct Resolved {
 int ffthreads(int n) { return n >= 8 ? n / 8 : 1; }
 // threads per row of the x-row kernels k_fx, k_ix (radix RowMR of fft.cuh)
 int rowthreads(int mh) { return mh == 256 ? mh / 16 : ffthreads(mh); }
+// threads of one transform of n points in k_fxy / k_iyx of an M grid (the
+// radix of XyMR) and their largest block (XyBounds)
+int xythreads(bool fp64, int n, int M, bool inv)
+{
+    const bool r16 = !fp64 && (n == 256 || (n == 128 && (M == 256 || inv)));
+    return r16 ? n / 16 : ffthreads(n);
+}
+int xy_max_threads(bool fp64, int M, bool inv)
+{
+    if (fp64) return XyBounds<double, 512, false>::T;
+    if (M == 256) return XyBounds<float, 256, false>::T;
+    return (M == 128 && inv) ? XyBounds<float, 128, true>::T : XyBounds<float, 64, false>::T;
+}
 // slots of one transform of length n in shared memory (PadLen in fft.cuh)
 int padlen(int n) { return n + n / 16; }
 
@@ -218,21 +232,25 @@ int resolve(const enuf_params* in, Resolved& r)
     // the kept kx columns are transformed in as few batches as the 1024-thread
     // limit allows, each batch CB columns wide with no idle column slots;
     // the rows then go through in batches of blockDim / NTX
-    r.fxy_threads = 0;
-    r.fxy_smem = 0;
+    r.fxy_threads = r.iyx_threads = 0;
+    r.fxy_smem = r.iyx_smem = 0;
     if (M >= 32 && M <= 256) {
-        const int NTX = ffthreads(M / 2), NTY = ffthreads(M);
-        for (int nbatch = (r.Kx * NTY + 1023) / 1024; nbatch <= r.Kx; nbatch++) {
-            const int CB = (r.Kx + nbatch - 1) / nbatch, t = CB * NTY;
-            if (t > 1024 || t % NTX) continue;
-            const int RB = t / NTX, KxR = (r.Kx + CB - 1) / CB * CB;
-            const size_t sm = ((size_t)RB * padlen(M / 2) + (size_t)KxR * (padlen(M) + 1) + M) * vsz;
-            if (sm <= (size_t)kMaxSmem) {
-                r.fxy_threads = t;
-                r.fxy_smem = sm;
-                break;
+        for (int inv = 0; inv < 2; inv++) {
+            const int NTX = xythreads(r.fp64, M / 2, M, inv), NTY = xythreads(r.fp64, M, M, inv);
+            const int tmax = xy_max_threads(r.fp64, M, inv);
+            for (int nbatch = (r.Kx * NTY + tmax - 1) / tmax; nbatch <= r.Kx; nbatch++) {
+                const int CB = (r.Kx + nbatch - 1) / nbatch, t = CB * NTY;
+                if (t > tmax || t % NTX) continue;
+                const int RB = t / NTX, KxR = (r.Kx + CB - 1) / CB * CB;
+                const size_t sm = ((size_t)RB * padlen(M / 2) + (size_t)KxR * (padlen(M) + 1) + M) * vsz;
+                if (sm <= (size_t)kMaxSmem) {
+                    (inv ? r.iyx_threads : r.fxy_threads) = t;
+                    (inv ? r.iyx_smem : r.fxy_smem) = sm;
+                    break;
+                }
             }
         }
+        if (!r.fxy_threads || !r.iyx_threads) r.fxy_threads = r.iyx_threads = 0;
     }
     // launch-time divisors of the FFT kernels' index arithmetic
     for (FftGeom* gm : {&r.gfx, &r.gy, &r.gz}) {
@@ -240,8 +258,8 @@ int resolve(const enuf_params* in, Resolved& r)
         gm->fW = FDiv::make((uint32_t)std::max(1, gm->W));
         gm->fKxR = FDiv::make(1);
     }
-    if (r.fxy_threads > 0) {
-        const int CB = r.fxy_threads / ffthreads(M);
+    if (r.iyx_threads > 0) {
+        const int CB = r.iyx_threads / xythreads(r.fp64, M, M, true);
         r.gy.fKxR = FDiv::make((uint32_t)((r.Kx + CB - 1) / CB * CB));
     }
     return ENUF_OK;
@@ -721,7 +739,7 @@ int launch_fft_chain_m(Launcher& L, enuf_plan* pl, int nf, void* spec = nullptr,
     }
     if (nf == 0) return ENUF_OK;
     if (fused) {
-        return L.go("ifft_yx", k_iyx<R, M>, dim3(M, nf), dim3(r.fxy_threads), r.fxy_smem, at<const V>(pl, y.C3),
+        return L.go("ifft_yx", k_iyx<R, M>, dim3(M, nf), dim3(r.iyx_threads), r.iyx_smem, at<const V>(pl, y.C3),
                     at<R>(pl, y.fld), r.gy, W);
     }
     // inverse y

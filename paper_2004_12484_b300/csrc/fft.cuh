@@ -131,6 +131,22 @@ template <int N> struct RowMR {
     static constexpr int V = N == 256 ? 16 : 8;
 };
 
+// Radix of the passes of N points in the fused x-y kernels of an M grid
+// (k_fxy, INV = false; k_iyx, INV = true): 16 in single precision for the
+// 256-point columns and 128-point rows of a 256 grid and for the 128-point
+// columns of the inverse kernel of a 128 grid (two passes, one exchange,
+// instead of radix 8, 8 and 2 or 4); else 8.  At 128 the forward kernel
+// keeps radix 8: its 128 CTAs (one per plane) need the threads of the
+// 16-point columns for the row batches (12.3 against 14.3 us).  The block
+// size (the host's xy_threads) stays within XyBounds<R, M, INV>::T, which
+// leaves the radix-16 kernels room for their registers.
+template <typename R, int N, int M, bool INV> struct XyMR {
+    static constexpr int V = (sizeof(R) == 4 && (N == 256 || (N == 128 && (M == 256 || INV)))) ? 16 : 8;
+};
+template <typename R, int M, bool INV> struct XyBounds {
+    static constexpr int T = sizeof(R) != 4 ? 1024 : (M == 256 ? 544 : ((M == 128 && INV) ? 288 : 1024));
+};
+
 // Shared-memory layout of one transform: element e lives at pidx(e) = e +
 // e/16, which spreads the stride-R writes of the first Stockham passes over
 // all banks.  A transform of length N occupies PadLen<N>::V slots.
@@ -388,11 +404,12 @@ __global__ void __launch_bounds__(256, SepBounds<R, M>::FXB) k_fx(R* __restrict_
 // in a plane buffer, transformed along y (thread (w, t) = (tid % CB, tid /
 // CB) on column k0 + w) and the band rows stored to C2 from registers.
 template <typename R, int M>
-__global__ void __launch_bounds__(1024) k_fxy(R* __restrict__ grid, typename Cpx<R>::T* __restrict__ C2,
+__global__ void __launch_bounds__(XyBounds<R, M, false>::T) k_fxy(R* __restrict__ grid, typename Cpx<R>::T* __restrict__ C2,
                                               FftGeom g, const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
-    constexpr int MH = M / 2, NTX = FftThreads<MH>::NT, NTY = FftThreads<M>::NT, LD = PadLen<M>::V + 1;
+    constexpr int MH = M / 2, MRX = XyMR<R, MH, M, false>::V, MRY = XyMR<R, M, M, false>::V;
+    constexpr int NTX = FftThreads<MH, MRX>::NT, NTY = FftThreads<M, MRY>::NT, LD = PadLen<M>::V + 1;
     constexpr int RS = PadLen<MH>::V, EX = MH / NTX, EY = M / NTY;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int Kx = g.Kx, Kb = g.Kb, nc = g.nc;
@@ -416,7 +433,7 @@ __global__ void __launch_bounds__(1024) k_fxy(R* __restrict__ grid, typename Cpx
 #pragma unroll
         for (int m = 0; m < EX; m++) v[0][m] = live ? row[tx + NTX * m] : V{R(0), R(0)};
         V* x = rowbuf + r * RS;
-        fft_reg<V, MH, false>(v, x, tx, sW, 2);
+        fft_reg<V, MH, false, MRX>(v, x, tx, sW, 2);
         // the grid is left zeroed for the next spreading (each element is
         // cleared by the thread that read it, once its value is in use)
         if (live) {
@@ -448,7 +465,7 @@ __global__ void __launch_bounds__(1024) k_fxy(R* __restrict__ grid, typename Cpx
 #pragma unroll
         for (int m = 0; m < EY; m++) v[0][m] = col[pidx(ty + NTY * m)];
         __syncthreads();
-        fft_reg<V, M, false>(v, col, ty, sW, 1);
+        fft_reg<V, M, false, MRY>(v, col, ty, sW, 1);
         if (kx < Kx) {
 #pragma unroll
             for (int m = 0; m < EY; m++) {
@@ -810,13 +827,12 @@ __global__ void __launch_bounds__(SepBounds<R, M>::YT, SepBounds<R, M>::YB) k_iy
 // ---------------------------------------------------------------- k_iyx
 // Fused inverse y and x (complex-to-real) passes: one CTA per (z-plane,
 // field) (grid: (M, NF) blocks, 1024 threads).
-// Launch bounds of k_iyx: in single precision with M = 128 the CTA has 528
-// threads (33 kept kx columns x 16) and three CTAs share an SM (at most 40
-// registers a thread), so that the 3 * 128 CTAs of three fields run in one
-// wave on 148 SMs.
+// Launch bounds of k_iyx: in single precision with M = 128 the CTA has 264
+// threads (33 kept kx columns x 8) and three CTAs share an SM, so that the
+// 3 * 128 CTAs of three fields run in one wave on 148 SMs.
 template <typename R, int M> struct IyxBounds {
     static constexpr bool small = sizeof(R) == 4 && M == 128;
-    static constexpr int T = small ? 544 : 1024, B = small ? 3 : 1;
+    static constexpr int T = XyBounds<R, M, true>::T, B = small ? 3 : 1;
 };
 
 template <typename R, int M>
@@ -824,7 +840,8 @@ __global__ void __launch_bounds__(IyxBounds<R, M>::T, IyxBounds<R, M>::B) k_iyx(
                                               FftGeom g, const typename Cpx<R>::T* __restrict__ Wg)
 {
     using V = typename Cpx<R>::T;
-    constexpr int MH = M / 2, NTX = FftThreads<MH>::NT, NTY = FftThreads<M>::NT, LD = PadLen<M>::V + 1;
+    constexpr int MH = M / 2, MRX = XyMR<R, MH, M, true>::V, MRY = XyMR<R, M, M, true>::V;
+    constexpr int NTX = FftThreads<MH, MRX>::NT, NTY = FftThreads<M, MRY>::NT, LD = PadLen<M>::V + 1;
     constexpr int RS = PadLen<MH>::V, EX = MH / NTX, EY = M / NTY;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int Kx = g.Kx, Kb = g.Kb, nc = g.nc, P = g.P;
@@ -859,7 +876,7 @@ __global__ void __launch_bounds__(IyxBounds<R, M>::T, IyxBounds<R, M>::B) k_iyx(
             v[0][m] = (kb >= 0 && ENUF_IN(kb, Kb)) ? src[(size_t)kb * Kx + kx] : V{R(0), R(0)};
         }
         V* col = plane + kx * LD;
-        fft_reg<V, M, true>(v, col, ty, sW, 1);
+        fft_reg<V, M, true, MRY>(v, col, ty, sW, 1);
 #pragma unroll
         for (int m = 0; m < EY; m++) col[pidx(ty + NTY * m)] = v[0][m];
     }
@@ -883,7 +900,7 @@ __global__ void __launch_bounds__(IyxBounds<R, M>::T, IyxBounds<R, M>::B) k_iyx(
             const V fo = cmul(csub(a, b), cconj(sW[k]));
             v[0][m] = V{fe.x - fo.y, fe.y + fo.x};
         }
-        fft_reg<V, MH, true>(v, rowbuf + r * RS, tx, sW, 2);
+        fft_reg<V, MH, true, MRX>(v, rowbuf + r * RS, tx, sW, 2);
         if (live) {
 #pragma unroll
             for (int m = 0; m < EX; m++) out[(size_t)y * MH + tx + NTX * m] = v[0][m];
