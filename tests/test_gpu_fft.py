@@ -103,12 +103,13 @@ def test_structure_factor_is_additive_and_checks_inputs():
     assert np.isfinite(parts["E"]) and torch.isfinite(F).all()
 
 
+@pytest.mark.parametrize("M", [256, 512])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 2e-6)])
-def test_wide_z_pass_matches_narrow_at_512(precision, tol, monkeypatch):
-    """At M = 512 the z pass is k_fzw (8 pencils a CTA, radix 8, fields one
-    after the other); ENUF_FZ_NARROW=1 selects the z pass of the smaller
-    grids, which the oracle checks at M <= 256.  Both give the same energy,
-    forces, potentials and virial (a small system on the 512^3 grid)."""
+def test_wide_z_pass_matches_narrow(M, precision, tol, monkeypatch):
+    """At M = 512 (and 256 in single precision) the z pass is k_fzw (radix
+    8, fields one after the other); ENUF_FZ_NARROW=1 selects k_fz, the z pass
+    of the smaller grids, which the oracle checks at M <= 256.  Both give
+    the same energy, forces, potentials and virial (a small system)."""
     g = np.random.default_rng(90)
     N, L = 3000, np.array([60.0, 64.0, 68.0])
     pos = g.uniform(0, 1, size=(N, 3)) * L
@@ -121,7 +122,7 @@ def test_wide_z_pass_matches_narrow_at_512(precision, tol, monkeypatch):
     for narrow in (False, True):
         if narrow:
             monkeypatch.setenv("ENUF_FZ_NARROW", "1")
-        plan = P.Plan(L=L, N=N, alpha=0.5, r_c=10.0, M=512, p=4, precision=precision, device=DEV)
+        plan = P.Plan(L=L, N=N, alpha=0.5, r_c=10.0, M=M, p=4, precision=precision, device=DEV)
         parts, F, Wv, ph = plan.energy_forces(tp, tq, phi=True, kspace_only=True)
         res.append((parts["E"], F.cpu().double(), Wv, ph.cpu().double()))
         del plan
