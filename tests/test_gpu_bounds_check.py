@@ -28,9 +28,11 @@ CHECK_LIB = os.path.join(ROOT, "paper_2004_12484_b300", "libenuf_check.so")
 # to 12, tile edges, staged / direct / TMA interpolation, fused and separate
 # FFT passes, heavy tiles, chunked scans, all-pairs and cell real space,
 # analytic-differentiation forces, smeared charges, time stepping, the
-# structure-factor and FFT entry points, and the failure paths
+# structure-factor and FFT entry points, the failure paths, and the
+# benchmark workloads at full size (the 512 grid's passes and the
+# TMA-staged interpolation among them)
 SUITES = ["test_gpu_parity.py", "test_gpu_fft.py", "test_gpu_ad.py", "test_gpu_dpd.py", "test_gpu_md.py",
-          "test_gpu_autograd.py", "test_gpu_failures.py"]
+          "test_gpu_autograd.py", "test_gpu_failures.py", "test_gpu_workloads.py"]
 
 
 def test_selftest_refuses_and_records():
