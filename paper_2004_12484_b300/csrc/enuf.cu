@@ -199,11 +199,12 @@ int resolve(const enuf_params* in, Resolved& r)
     // k_fzw for M = 512: 8 pencils a CTA of 8 M/8 threads, one buffer per
     // pencil (two CTAs an SM: 0.293 ms at the ionic-liquid size against
     // 0.307 with 16 pencils in one CTA of 1024 threads)
-    r.fz_wide = (M >= 512 || (M == 256 && !r.fp64)) && !std::getenv("ENUF_FZ_NARROW");
+    r.fz_wide = (M >= 512 || ((M == 128 || M == 256) && !r.fp64)) && !std::getenv("ENUF_FZ_NARROW");
     if (r.fz_wide) {
-        // at 256 (single precision) 16 pencils, 512 threads: polyelectrolyte
-        // z pass 0.0573 -> 0.0368 ms against k_fz (0.0389 with 8 pencils)
-        int W = M == 256 ? 16 : 8;
+        // at 128 and 256 (single precision) 16 pencils: polyelectrolyte z
+        // pass 0.0573 -> 0.0368 ms against k_fz (0.0389 with 8 pencils); RPM
+        // step 0.1065 -> 0.1048 ms (8 pencils: no change)
+        int W = (M == 128 || M == 256) ? 16 : 8;
         if (const char* wv = std::getenv("ENUF_FZ_W")) {  // tuning knob: 4, 8 or 16 pencils a CTA
             const int w = std::atoi(wv);
             if (w == 4 || w == 8 || (w == 16 && !r.fp64)) W = w;
@@ -685,7 +686,7 @@ int launch_fft_chain_m(Launcher& L, enuf_plan* pl, int nf, void* spec = nullptr,
     }
     // z + reciprocal-space step + inverse z
     bool wide_done = false;
-    if constexpr (M >= 256) {
+    if constexpr (M >= 128) {
         if (r.fz_wide) {
         const int Wc = r.gz.W;
         const size_t smem = (size_t)(Wc * (padlen(M) + 1) + M) * vs + 32 * 7 * 8 + (size_t)9 * r.Kb * sizeof(R);

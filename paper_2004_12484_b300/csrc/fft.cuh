@@ -635,14 +635,16 @@ __global__ void __launch_bounds__(512) k_fz(const typename Cpx<R>::T* __restrict
     }
 }
 
-// The z pass for large grids (M = 512, and 256 in single precision): the
-// same steps as k_fz with radix-8 register passes, W pencils per CTA of
-// W * M/8 threads (8 at 512: two CTAs an SM; 16 at 256: the loads and
-// stores of a z row are 128-byte runs of 16 neighbouring pencils), and the
-// NF field transforms done one after the other through one buffer per
-// pencil (the spectrum S~ and k_z stay in registers between them).
+// The z pass for large grids (M = 512, and 128 and 256 in single
+// precision): the same steps as k_fz with radix-8 register passes, W
+// pencils per CTA of W * M/8 threads (8 at 512: two CTAs an SM; 16 at 128
+// and 256: the loads and stores of a z row are 128-byte runs of 16
+// neighbouring pencils), and the NF field transforms done one after the
+// other through one buffer per pencil (the spectrum S~ and k_z stay in
+// registers between them).  At 128 the CTA has 256 threads and the
+// launch bounds leave it 80 registers.
 template <typename R, int M, int NF>
-__global__ void __launch_bounds__(sizeof(R) == 4 ? 1024 : 512) k_fzw(const typename Cpx<R>::T* __restrict__ C2, typename Cpx<R>::T* __restrict__ C3, FftGeom g,
+__global__ void __launch_bounds__(sizeof(R) == 4 ? (M == 128 ? 256 : 1024) : 512) k_fzw(const typename Cpx<R>::T* __restrict__ C2, typename Cpx<R>::T* __restrict__ C3, FftGeom g,
                       const typename Cpx<R>::T* __restrict__ Wg, KTables<R> ktg, double* __restrict__ part)
 {
     using V = typename Cpx<R>::T;

@@ -103,11 +103,11 @@ def test_structure_factor_is_additive_and_checks_inputs():
     assert np.isfinite(parts["E"]) and torch.isfinite(F).all()
 
 
-@pytest.mark.parametrize("M", [256, 512])
+@pytest.mark.parametrize("M", [128, 256, 512])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 2e-6)])
 def test_wide_z_pass_matches_narrow(M, precision, tol, monkeypatch):
-    """At M = 512 (and 256 in single precision) the z pass is k_fzw (radix
-    8, fields one after the other); ENUF_FZ_NARROW=1 selects k_fz, the z pass
+    """At M = 512 (and 128 and 256 in single precision) the z pass is k_fzw
+    (radix 8, fields one after the other); ENUF_FZ_NARROW=1 selects k_fz, the z pass
     of the smaller grids, which the oracle checks at M <= 256.  Both give
     the same energy, forces, potentials and virial (a small system)."""
     g = np.random.default_rng(90)
