@@ -101,7 +101,8 @@ int xy_max_threads(bool fp64, int M, bool inv)
 {
     if (fp64) return XyBounds<double, 512, false>::T;
     if (M == 256) return XyBounds<float, 256, false>::T;
-    return (M == 128 && inv) ? XyBounds<float, 128, true>::T : XyBounds<float, 64, false>::T;
+    if (M == 128) return inv ? XyBounds<float, 128, true>::T : XyBounds<float, 128, false>::T;
+    return XyBounds<float, 64, false>::T;
 }
 // slots of one transform of length n in shared memory (PadLen in fft.cuh)
 int padlen(int n) { return n + n / 16; }

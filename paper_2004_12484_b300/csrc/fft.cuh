@@ -144,7 +144,7 @@ template <typename R, int N, int M, bool INV> struct XyMR {
     static constexpr int V = (sizeof(R) == 4 && (N == 256 || (N == 128 && (M == 256 || INV)))) ? 16 : 8;
 };
 template <typename R, int M, bool INV> struct XyBounds {
-    static constexpr int T = sizeof(R) != 4 ? 1024 : (M == 256 ? 544 : ((M == 128 && INV) ? 288 : 1024));
+    static constexpr int T = sizeof(R) != 4 ? 1024 : (M == 256 ? 544 : (M == 128 ? (INV ? 288 : 544) : 1024));
 };
 
 // Shared-memory layout of one transform: element e lives at pidx(e) = e +
