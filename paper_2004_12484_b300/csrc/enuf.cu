@@ -489,8 +489,10 @@ int launch_spread_t(Launcher& L, enuf_plan* pl)
     const Resolved& r = pl->r;
     const Layout& y = pl->lay;
     constexpr int S = T < 8 ? T : 8;
+    // the box and (widths without a register path) the weight-product table;
+    // p = 8 needs no table, which lets 14 of its CTAs share an SM instead of 13
     return L.go("spread", k_spread<R, P, T>, dim3(r.max_work2), dim3(32),
-                (size_t)(SBox<P, S>::CELLS + P * P) * sizeof(R), at<const int4>(pl, y.work2),
+                (size_t)(SBox<P, S>::CELLS + WyzTable<P>::N) * sizeof(R), at<const int4>(pl, y.work2),
                 at<const int>(pl, y.nwork2), at<const typename Rec<R>::T>(pl, y.rec), r.prm.M, pl->lnb, r.lr,
                 winc<R>(pl), (R)pl->cnorm3, at<R>(pl, y.grid), (int)r.prm.N);
 }
