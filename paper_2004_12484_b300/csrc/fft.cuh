@@ -5,19 +5,25 @@
 // Forward chain (the spreading, transform and scaling stages of Sec. 3.1):
 //   k_fx  real rows along x -> half spectrum, keep kx = 0..n_c
 //   k_fy  along y for each kx, keep ky in the band (2 n_c + 1 values)
+//         (k_fxy: both in one kernel per z-plane where the kept plane fits
+//         in shared memory, grids 32-256)
 //   k_fz  along z for each (ky, kx) pencil, then for every retained n:
 //         S(n) = D(n) ghat(n) (scaling by the window's Fourier coefficients),
 //         energy and virial (Eq. 38), and the subdivided spectra of the
 //         force field and potential (Eq. 41-42), then the inverse transform
 //         along z of each field (the split into field spectra and the first
-//         inverse pass)
+//         inverse pass); k_fzw does the same with radix-8 passes and the
+//         fields one after the other (512, and 128 and 256 in single
+//         precision)
 // Inverse chain (the inverse transforms ahead of the interpolation):
 //   k_iy  along y (band -> full length) for each field and kx
 //   k_ix  half spectrum kx = 0..n_c -> real rows (complex-to-real)
+//         (k_iyx: both in one kernel per z-plane and field, grids 32-256)
 //
-// Every 1D transform is an in-shared-memory Stockham autosort FFT: each
-// thread holds R (8, 4 or 2) elements in registers per pass, applies the
-// twiddles and a radix-R butterfly, and writes back in autosort order.  The
+// Every 1D transform is a Stockham autosort FFT: each thread holds R (16,
+// 8, 4 or 2) elements in registers per pass, applies the twiddles and a
+// radix-R butterfly; the passes exchange through shared memory, the first
+// loads from and the last stores to global memory directly.  The
 // real-to-complex rows use the half-length complex transform of the packed
 // row (x_{2j} + i x_{2j+1}) and the usual even/odd split.
 // Sign conventions: forward sum_l g_l exp(-2 pi i k l / M), inverse with
