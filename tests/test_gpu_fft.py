@@ -132,3 +132,29 @@ def test_wide_z_pass_matches_narrow(M, precision, tol, monkeypatch):
     assert rel_rms(F0, F1) < tol
     assert rel_rms(p0, p1) < tol
     assert np.abs(W0 - W1).max() < tol * np.abs(W1).max()
+
+
+@pytest.mark.parametrize("M", [128, 256, 512])
+def test_energy_only_evaluation_on_the_wide_z_pass(M):
+    """An evaluation without forces or potentials runs the z pass alone (no
+    field transforms, no interpolation): its energy and virial equal those of
+    a forces evaluation, before and after it (the grid is left cleared
+    either way), and the k-space energy agrees with the oracle."""
+    g = np.random.default_rng(93)
+    N, L = 2000, np.array([60.0, 64.0, 68.0])
+    pos = g.uniform(0, 1, size=(N, 3)) * L
+    q = g.normal(size=N)
+    q -= q.mean()
+    pos32, q32 = W.as_fp32(pos, q)
+    tp = torch.tensor(pos32, dtype=torch.float32, device=DEV)
+    tq = torch.tensor(q32, dtype=torch.float32, device=DEV)
+    plan = P.Plan(L=L, N=N, alpha=0.5, r_c=10.0, M=M, p=4, precision="mixed", device=DEV)
+    e0, _, _ = plan.compute(tp, tq, forces=False, kspace_only=True)
+    parts, F, Wv, _ = plan.energy_forces(tp, tq, kspace_only=True)
+    e1, _, _ = plan.compute(tp, tq, forces=False, kspace_only=True)
+    e0, e1 = e0.cpu().numpy(), e1.cpu().numpy()
+    assert abs(e0[0] / parts["E"] - 1) < 1e-6 and abs(e1[0] / parts["E"] - 1) < 1e-6
+    assert np.abs(e0[6:15] - Wv.reshape(-1)).max() < 1e-6 * np.abs(Wv).max()
+    if M == 128:
+        Ek, _, _, _ = O.kspace_nfft(pos32, q32, L, 0.5, M, 4, M // 4)
+        assert abs(e0[2] / Ek - 1) < 1e-6  # the reciprocal energy
