@@ -35,7 +35,7 @@ template <int P> struct GroupOf {
 // uses for the window widths without a register path (p = 4 and 8 keep the
 // weights in registers).
 template <int P> struct WyzTable {
-    static constexpr int N = (P == 4 || P == 8) ? 0 : P * P;
+    static constexpr int N = (P == 4 || P == 6 || P == 8) ? 0 : P * P;
 };
 
 // Per-plan window constants: 1/b, log2(e)/b and c[a] = exp(-a^2 / b), a < P.
@@ -152,6 +152,21 @@ __device__ __forceinline__ void visit_window(R dy, R dz, R wx, const WinC<R>& wc
         for (int c = 0; c < 8; c++) {
             f(2 * c, g, c, t0 * wz[c]);
             f(2 * c + 1, g + 4, c, t1 * wz[c]);
+        }
+    } else if constexpr (P == 6) {
+        // lane (g, a < 6): planes g and (g < 2) g + 4, all six rows; the six
+        // y weights and the lane's z weights evaluated in the lane (the four
+        // groups of one access touch four consecutive planes)
+        if (a >= P) return;
+        R wy[6];
+        window_weights<R, 6>(dy, wc, wy);
+        const R uz0 = dz + (R)(2 - g), uz1 = dz - (R)(2 + g);
+        const R t0 = wx * win_exp(uz0 * uz0, wc), t1 = wx * win_exp(uz1 * uz1, wc);
+#pragma unroll
+        for (int b = 0; b < 6; b++) f(b, b, g, t0 * wy[b]);
+        if (g < 2) {
+#pragma unroll
+            for (int b = 0; b < 6; b++) f(6 + b, b, g + 4, t1 * wy[b]);
         }
     } else if constexpr (P == 4) {
         R wz[4];
@@ -296,7 +311,7 @@ __global__ void __launch_bounds__(32) k_spread(const int4* __restrict__ work, co
             const R ua = dx + (R)(m - 1 - (a % P));
             const R wx = rq * cnorm3 * win_exp(ua * ua, wc);
             constexpr int RPI = 32 / G;
-            constexpr int NV = P == 8 ? 16 : (P == 4 ? 2 : (P * P + RPI - 1) / RPI);
+            constexpr int NV = P == 8 ? 16 : (P == 6 ? 12 : (P == 4 ? 2 : (P * P + RPI - 1) / RPI));
             if constexpr (P == 8) {
                 // lane 8 g + a: x-offset a of planes g and g + 4 and all eight
                 // rows; every lane evaluates the eight y weights (fast Gaussian
