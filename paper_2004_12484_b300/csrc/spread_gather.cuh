@@ -32,8 +32,8 @@ template <int P> struct GroupOf {
 };
 
 // Entries of the per-warp table of y-z weight products that visit_window
-// uses for the window widths without a register path (p = 4 and 8 keep the
-// weights in registers).
+// uses for the window widths without a register path (p = 4, 6 and 8 keep
+// the weights in registers).
 template <int P> struct WyzTable {
     static constexpr int N = (P == 4 || P == 6 || P == 8) ? 0 : P * P;
 };
