@@ -141,10 +141,11 @@ int resolve(const enuf_params* in, Resolved& r)
         const int m = p.p / 2, XA = (m - 1 + 3) / 4 * 4, BX = (XA + T + m + 3) / 4 * 4, PT = T + p.p - 1;
         return ((size_t)BX * PT * PT * 4 + (size_t)32 * p.p * p.p) * r.rsz + (size_t)kWorkCap * (4 * r.rsz + 4);
     };
-    // windows of p <= 6 interpolate faster straight from L2-resident fields
-    // (8-cell tiles) than from a staged 16-cell box
+    // windows of p <= 4 interpolate faster straight from L2-resident fields
+    // (8-cell tiles) than from a staged 16-cell box; p = 6 and 8 have a
+    // TMA-staged interpolation of their own on 16-cell tiles
     const bool fields_in_l2 = (size_t)4 * p.M * p.M * p.M * r.rsz <= (size_t)64 << 20;
-    r.T = (!r.fp64 && p.M >= 128 && !(p.p <= 6 && fields_in_l2)) ? 16 : 8;
+    r.T = (!r.fp64 && p.M >= 128 && !(p.p <= 4 && fields_in_l2)) ? 16 : 8;
     if (const char* tv = std::getenv("ENUF_TILE")) {  // tuning knob: tile edge 4, 8 or 16
         const int t = std::atoi(tv);
         if ((t == 4 || t == 8 || t == 16) && t <= p.M) r.T = t;
@@ -381,9 +382,9 @@ struct enuf_plan {
     bool use_graph = true;
     bool profile = false;
     bool pdl = true;  // programmatic dependent launch along the chain (ENUF_NO_PDL=1 turns it off)
-    bool legacy_gather = false;  // ENUF_LEGACY_GATHER=1: the generic interpolation kernel for p = 8 as well
-    bool gather_p8 = false;      // k_gather_p8 serves the interpolation (its tensor map is set)
-    CUtensorMap fld_tmap;        // the field planes, for the TMA boxes of k_gather_p8
+    bool legacy_gather = false;  // ENUF_LEGACY_GATHER=1: the generic interpolation kernel for p = 8 and 6 as well
+    bool gather_tma = false;     // k_gather_p8 / k_gather_p6 serve the interpolation (its tensor map is set)
+    CUtensorMap fld_tmap;        // the field planes, for the TMA boxes of k_gather_p8 / k_gather_p6
     bool attrs_done = false;
     std::vector<GraphEntry> graphs;
     // one time step of the harness (enuf_md_run) as a graph, for one set of
@@ -517,20 +518,24 @@ int launch_gather_t(Launcher& L, enuf_plan* pl, int nf, R* F, R* phi)
                     at<const R>(pl, y.fld), F, phi);
     }
     using RecT = typename Rec<R>::T;
-    if constexpr (T == 16 && P == 8 && sizeof(R) == 4) {
-        if (pl->gather_p8) {
-            // p = 8 in single precision: boxes staged by the TMA engine,
-            // z-accumulated window rows
+    if constexpr (T == 16 && (P == 8 || P == 6) && sizeof(R) == 4) {
+        if (pl->gather_tma) {
+            // p = 8 and 6 in single precision: boxes staged by the TMA
+            // engine, z-accumulated window rows
             int* st = at<int>(pl, y.status);
-            if (nf == 4)
-                return L.go("gather", k_gather_p8<4>, dim3(r.max_work), dim3(512), GatherP8<4>::SMEM,
-                            at<const int4>(pl, y.work), at<const int>(pl, y.nwork), at<const f4>(pl, y.rec),
-                            at<const uint32_t>(pl, y.perm), r.prm.M, pl->lnb, winc<float>(pl), (float)pl->cnorm3,
-                            at<const float>(pl, y.fld), pl->fld_tmap, (float*)F, (float*)phi, st, (int)r.prm.N);
-            return L.go("gather", k_gather_p8<3>, dim3(r.max_work), dim3(512), GatherP8<3>::SMEM,
-                        at<const int4>(pl, y.work), at<const int>(pl, y.nwork), at<const f4>(pl, y.rec),
-                        at<const uint32_t>(pl, y.perm), r.prm.M, pl->lnb, winc<float>(pl), (float)pl->cnorm3,
-                        at<const float>(pl, y.fld), pl->fld_tmap, (float*)F, (float*)phi, st, (int)r.prm.N);
+            auto go = [&](auto kern, size_t smem) {
+                return L.go("gather", kern, dim3(r.max_work), dim3(512), smem, at<const int4>(pl, y.work),
+                            at<const int>(pl, y.nwork), at<const f4>(pl, y.rec), at<const uint32_t>(pl, y.perm),
+                            r.prm.M, pl->lnb, winc<float>(pl), (float)pl->cnorm3, at<const float>(pl, y.fld),
+                            pl->fld_tmap, (float*)F, (float*)phi, st, (int)r.prm.N);
+            };
+            if constexpr (P == 8) {
+                if (nf == 4) return go(k_gather_p8<4>, GatherP8<4>::SMEM);
+                return go(k_gather_p8<3>, GatherP8<3>::SMEM);
+            } else {
+                if (nf == 4) return go(k_gather_p6<4>, GatherP6<4>::SMEM);
+                return go(k_gather_p6<3>, GatherP6<3>::SMEM);
+            }
         }
     }
     if constexpr (T == 16) {
@@ -1072,7 +1077,8 @@ void drop_graphs(enuf_plan* pl)
 }
 
 // Tensor map of the four field planes (x, y, z, field) for the TMA boxes of
-// k_gather_p8: boxes of BX x PT x PZ x 1 cells, no swizzle, zeros outside.
+// k_gather_p8 / k_gather_p6: boxes of BX x PY x PZ x 1 cells (the kernel's
+// geometry for the plan's p), no swizzle, zeros outside.
 int encode_field_map(enuf_plan* pl)
 {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -1086,11 +1092,13 @@ int encode_field_map(enuf_plan* pl)
         }
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
-    using B = Box<8, 16, 8>;
+    const bool p8 = pl->r.prm.p == 8;
     const cuuint64_t M = (cuuint64_t)pl->r.prm.M;
     const cuuint64_t dims[4] = {M, M, M, 4};
     const cuuint64_t strides[3] = {M * 4, M * M * 4, M * M * M * 4};
-    const cuuint32_t box[4] = {(cuuint32_t)B::BX, (cuuint32_t)B::PT, (cuuint32_t)B::PZ, 1};
+    const cuuint32_t box[4] = {(cuuint32_t)(p8 ? GatherP8<3>::B::BX : GatherP6<3>::B::BX),
+                               (cuuint32_t)(p8 ? GatherP8<3>::PY : GatherP6<3>::PY),
+                               (cuuint32_t)(p8 ? GatherP8<3>::B::PZ : GatherP6<3>::B::PZ), 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     const CUresult rc = encode(&pl->fld_tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, pl->ws + pl->lay.fld, dims, strides,
                                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -1103,12 +1111,13 @@ int bind_workspace(enuf_plan* pl, void* ptr)
 {
     drop_graphs(pl);
     pl->ws = (char*)ptr;
-    // the p = 8 single-precision interpolation on z-halves of 16-cell tiles
-    // stages its boxes through a tensor map of this workspace's field planes
+    // the p = 8 and 6 single-precision interpolation on z-halves of 16-cell
+    // tiles stages its boxes through a tensor map of this workspace's field
+    // planes
     const Resolved& r = pl->r;
-    pl->gather_p8 = !r.fp64 && r.T == 16 && r.zhalf && r.prm.p == 8 && r.prm.M >= 32 && r.gcap == 256 &&
-                    !r.gather_direct && !pl->legacy_gather;
-    if (pl->gather_p8) LCHK(encode_field_map(pl));
+    pl->gather_tma = !r.fp64 && r.T == 16 && r.zhalf && (r.prm.p == 8 || r.prm.p == 6) && r.prm.M >= 32 &&
+                     r.gcap == 256 && !r.gather_direct && !pl->legacy_gather;
+    if (pl->gather_tma) LCHK(encode_field_map(pl));
     // the status word and the bin counts start (and are kept) zeroed
     CK(cudaMemset(pl->ws, 0, pl->lay.total));
     LCHK(upload_tables(pl));

@@ -231,14 +231,39 @@ template <int P, int T, int ZS = T> struct Box {
 // The spreading box of a sub-tile (S^3 cells): the Box geometry with row
 // stride BX and plane stride PS padded so that the four rows one warp
 // instruction touches start on disjoint groups of 8 banks -- the same row of
-// four consecutive planes for p = 8 (PS = 24 banks mod 32), four consecutive
-// rows otherwise.
+// four consecutive planes for p = 8 (PS = 24 banks mod 32), for p = 6 on
+// 8-cell sub-tiles rows 24 and planes 16 banks apart (see RowsP6), four
+// consecutive rows otherwise.
 template <int P, int S> struct SBox {
     using B0 = Box<P, S>;
     static constexpr int m = P / 2, XA = B0::XA, XOFF = B0::XOFF, PT = B0::PT;
     static constexpr int BX = (P != 8 && B0::BX % 16 == 0) ? B0::BX + 8 : B0::BX;
-    static constexpr int PS = PT * BX + ((P == 8 && (PT * BX) % 16 == 0) ? 8 : 0);
+    static constexpr bool P6 = P == 6 && BX == 24;
+    static constexpr int PS0 = PT * BX;
+    static constexpr int PS = P6 ? PS0 + (48 - PS0 % 32) % 32 : PS0 + ((P == 8 && PS0 % 16 == 0) ? 8 : 0);
     static constexpr int CELLS = PT * PS;
+};
+
+// The window rows of one lane for p = 6 (lane 8 g + a, x offset a < 6): the
+// 36 rows (y offset b, z offset c) of a window split into 12 runs of three
+// planes (b, c = 3h .. 3h + 2), and group g takes the three runs with
+// 3 b + 2 h = g (mod 4).  Every lane then visits 9 points instead of the 12
+// (two planes of six rows) of the lanes that do most in a plane-wise split,
+// and where rows lie 24 banks and planes 16 banks apart (mod 32) the four
+// groups of one access touch disjoint groups of 8 banks: (3 b + 2 c) mod 4 =
+// g + 2j for the run's plane j.  Runs 0 and 1 have h = 0 and 1; run 2 the
+// h of the remaining class member (b + 4 < 6).
+struct RowsP6 {
+    int b[3];
+    bool h2;  // run 2 on planes 3..5
+    __device__ __forceinline__ explicit RowsP6(int g)
+    {
+        const int r0 = (3 * g) & 3, r1 = (3 * g + 2) & 3;
+        b[0] = r0;
+        b[1] = r1;
+        h2 = r0 >= 2;
+        b[2] = (h2 ? r1 : r0) + 4;
+    }
 };
 
 template <typename R, int P, int T>
@@ -267,24 +292,29 @@ __global__ void __launch_bounds__(32) k_spread(const int4* __restrict__ work, co
     if (!(ENUF_IN(tz, nbm + 1) && ENUF_IN(w.y, w.z) && ENUF_IN(w.z - 1, N))) return;
     __syncwarp();
 
-    // p = 8: the warp's 32 records go through shared memory (one broadcast
-    // load per particle; shuffles would share the shared-memory pipe that
-    // bounds this kernel, four per particle)
-    __shared__ RecT srecs[P == 8 ? 32 : 1];
+    // p = 8 and 6: the warp's 32 records go through shared memory (one
+    // broadcast load per particle; shuffles would share the shared-memory
+    // pipe that bounds this kernel, four per particle)
+    constexpr bool SREC = P == 8 || B::P6;
+    __shared__ RecT srecs[SREC ? 32 : 1];
+    const RowsP6 rows6(lane >> 3);  // p = 6: the lane's window rows
+    int o6[3];                      // and their offsets in the box
+#pragma unroll
+    for (int k = 0; k < 3; k++) o6[k] = (k == 1 || (k == 2 && rows6.h2) ? 3 * PS : 0) + rows6.b[k] * BX;
     for (int j0 = w.y; j0 < w.z; j0 += 32) {
         // one record per lane, handed to the warp with shuffles (or, p = 8,
         // through shared memory)
         RecT mine;
         if (j0 + lane < w.z) mine = rec[j0 + lane];
         else mine.x = mine.y = mine.z = mine.w = R(0);
-        if constexpr (P == 8) {
+        if constexpr (SREC) {
             srecs[lane] = mine;
             __syncwarp();
         }
         const int nj = min(32, w.z - j0);
         for (int jj = 0; jj < nj; jj++) {
             R rx, ry, rz, rq;
-            if constexpr (P == 8) {
+            if constexpr (SREC) {
                 const RecT rr = srecs[jj];
                 rx = rr.x;
                 ry = rr.y;
@@ -335,6 +365,34 @@ __global__ void __launch_bounds__(32) k_spread(const int4* __restrict__ work, co
                 for (int i = 0; i < 8; i++) {
                     base[i * BX] = old[i] + t0 * wy8[i];
                     base[4 * PS + i * BX] = old[8 + i] + t1 * wy8[i];
+                }
+            } else if constexpr (B::P6) {
+                // lane 8 g + a: x-offset a of the three runs of RowsP6 (9
+                // points); the y weights of its rows and the six z weights
+                // evaluated in the lane
+                R wz6[6];
+                window_weights<R, 6>(dz, wc, wz6);
+                R t[3];
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    const R uy = dy + (R)(2 - rows6.b[k]);
+                    t[k] = wx * win_exp(uy * uy, wc);
+                }
+                if (a < P) {
+                    R* base = acc + iz * PS + iy * BX + ix + B::XOFF + a;
+                    R old[9];
+#pragma unroll
+                    for (int k = 0; k < 3; k++) {
+#pragma unroll
+                        for (int j = 0; j < 3; j++) old[3 * k + j] = base[o6[k] + j * PS];
+                    }
+#pragma unroll
+                    for (int j = 0; j < 3; j++) {
+                        const R z2 = rows6.h2 ? wz6[3 + j] : wz6[j];
+                        base[o6[0] + j * PS] = old[j] + t[0] * wz6[j];
+                        base[o6[1] + j * PS] = old[3 + j] + t[1] * wz6[3 + j];
+                        base[o6[2] + j * PS] = old[6 + j] + t[2] * z2;
+                    }
                 }
             } else if constexpr (NV <= 16) {
                 R* base = acc + (iz * PS) + iy * BX + ix + B::XOFF + a;
@@ -502,20 +560,64 @@ __global__ void __launch_bounds__(NTH) k_gather(const int4* __restrict__ work, c
                                  cnorm3, F, phi, [&](int k) { return sperm[k]; }, N);
 }
 
+// Staging of one work unit of the TMA interpolation kernels (k_gather_p8,
+// k_gather_p6): one thread has the TMA engine copy the unit's box of each
+// field plane (a tensor-map box of BX x PY x PZ cells from (ox, oy, oz),
+// plane f at s + f C) and the unit's n particle records into shared memory,
+// completing on the mbarrier `bar`; cells of a box that crosses the edge of
+// the periodic grid arrive as zeros and are then filled from their periodic
+// images by the threads (16-byte copies of whole aligned groups of four
+// cells, all in flight before the wait).  Needs M >= BX (a box crosses each
+// edge at most once).  Returns false (the status word flagged) if the copies
+// did not complete within the wait's bound.
+template <int NF, int BX, int PY, int PZ, int C>
+__device__ __forceinline__ bool stage_unit_tma(float* s, f4* srec, uint64_t* bar, const CUtensorMap* tmap,
+                                               const f4* rec, int n, int ox, int oy, int oz, int M,
+                                               const float* __restrict__ fld, int* status)
+{
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(bar, (uint32_t)(NF * BX * PY * PZ * 4 + n * 16));
+#pragma unroll
+        for (int f = 0; f < NF; f++) tma_load_4d(s + f * C, tmap, ox, oy, oz, f, bar);
+        bulk_g2s(srec, rec, (uint32_t)n * 16u, bar);
+    }
+    if (!mbar_wait(bar, 0, 1 << 22)) {
+        // should not happen: report, and wait (bounded) for the copies still
+        // writing this CTA's shared memory before leaving
+        if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+        mbar_wait(bar, 0, 1 << 22);
+        return false;
+    }
+    if (ox < 0 || ox + BX > M || oy < 0 || oy + PY > M || oz < 0 || oz + PZ > M) {
+        const int mask = M - 1;
+        const size_t M3 = (size_t)M * M * M;
+        constexpr int NV = BX / 4;
+        for (int i = threadIdx.x; i < NV * PY * PZ; i += blockDim.x) {
+            const int vx = i % NV, ly = (i / NV) % PY, lz = i / (NV * PY);
+            const int gx = ox + 4 * vx, gy = oy + ly, gz = oz + lz;
+            if (gx >= 0 && gx < M && gy >= 0 && gy < M && gz >= 0 && gz < M) continue;
+            const size_t gi = ((size_t)(gz & mask) * M + (gy & mask)) * M + (gx & mask);
+            const int si = (lz * PY + ly) * BX + 4 * vx;
+            if (!ENUF_IN(gi + 3, M3)) continue;
+#pragma unroll
+            for (int f = 0; f < NF; f++) cp_async_bytes16(s + f * C + si, fld + f * M3 + gi, true);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+    }
+    return true;
+}
+
 // Interpolation for windows of p = 8 on 16-cell tiles in z-halves, single
 // precision (the configuration of the large workloads and the benchmark).
-// Staging: one thread has the TMA engine copy the unit's box of each field
-// plane (a tensor-map box of BX x PT x PZ cells) and the unit's particle
-// records into shared memory, completing on an mbarrier; cells of a box that
-// crosses the edge of the periodic grid arrive as zeros and are then filled
-// from their periodic images by the threads (16-byte loads of whole aligned
-// groups of four cells).  Compute: one warp per particle, lane (g, a) =
-// (lane / 8, lane % 8) takes x offset a of rows g and g + 4 and all eight
-// planes, and sums each of its two rows along z with the z weights before
-// applying the x and y weights, so a window point costs one shared load and
-// one FMA per field.  Needs M >= 32 (a box crosses each edge at most once).
+// Staging by stage_unit_tma (boxes of BX x PT x PZ cells).  Compute: one
+// warp per particle, lane (g, a) = (lane / 8, lane % 8) takes x offset a of
+// rows g and g + 4 and all eight planes, and sums each of its two rows
+// along z with the z weights before applying the x and y weights, so a
+// window point costs one shared load and one FMA per field.
 template <int NF> struct GatherP8 {
     using B = Box<8, 16, 8>;
+    static constexpr int PY = B::PT;                       // box rows (y)
     static constexpr int CP = (B::CELLS + 31) / 32 * 32;  // field stride in shared memory, 128-byte aligned
     static constexpr int CAP = 256;                        // particles per work item
     static constexpr size_t SMEM = (size_t)NF * CP * 4 + CAP * sizeof(f4) + 16;
@@ -547,39 +649,7 @@ __global__ void __launch_bounds__(512, 2) k_gather_p8(const int4* __restrict__ w
     const int tx = tile & nbm, ty = (tile >> lnb) & nbm, tz = tile >> (2 * lnb);
     const int ox = tx * 16 - B::XA, oy = ty * 16 - 3, oz = tz * 16 + z0 - 3;
     if (!(ENUF_IN(tz, nbm + 1) && ENUF_IN(n - 1, G8::CAP) && ENUF_IN(w.z - 1, N))) return;  // uniform for the CTA
-    if (threadIdx.x == 0) {
-        mbar_arrive_expect_tx(bar, (uint32_t)(NF * B::CELLS * 4 + n * 16));
-#pragma unroll
-        for (int f = 0; f < NF; f++) tma_load_4d(s + f * C, &tmap, ox, oy, oz, f, bar);
-        bulk_g2s(srec, rec + w.y, (uint32_t)n * 16u, bar);
-    }
-    if (!mbar_wait(bar, 0, 1 << 22)) {
-        // should not happen: report, and wait (bounded) for the copies still
-        // writing this CTA's shared memory before leaving
-        if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
-        mbar_wait(bar, 0, 1 << 22);
-        return;
-    }
-    if (ox < 0 || ox + BX > M || oy < 0 || oy + PT > M || oz < 0 || oz + PZ > M) {
-        // the box crosses the grid's edge: its outside cells came as zeros;
-        // copy them from their periodic images (asynchronous 16-byte copies,
-        // all in flight before the wait)
-        const int mask = M - 1;
-        const size_t M3 = (size_t)M * M * M;
-        constexpr int NV = BX / 4;
-        for (int i = threadIdx.x; i < NV * PT * PZ; i += 512) {
-            const int vx = i % NV, ly = (i / NV) % PT, lz = i / (NV * PT);
-            const int gx = ox + 4 * vx, gy = oy + ly, gz = oz + lz;
-            if (gx >= 0 && gx < M && gy >= 0 && gy < M && gz >= 0 && gz < M) continue;
-            const size_t gi = ((size_t)(gz & mask) * M + (gy & mask)) * M + (gx & mask);
-            const int si = (lz * PT + ly) * BX + 4 * vx;
-            if (!ENUF_IN(gi + 3, M3)) continue;
-#pragma unroll
-            for (int f = 0; f < NF; f++) cp_async_bytes16(s + f * C + si, fld + f * M3 + gi, true);
-        }
-        cp_async_wait_all();
-        __syncthreads();
-    }
+    if (!stage_unit_tma<NF, BX, PT, PZ, C>(s, srec, bar, &tmap, rec + w.y, n, ox, oy, oz, M, fld, status)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 3, a = lane & 7;
     for (int k = warp; k < n; k += 16) {
@@ -615,6 +685,102 @@ __global__ void __launch_bounds__(512, 2) k_gather_p8(const int4* __restrict__ w
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int f = 0; f < NF; f++) acc[f] = wx * fmaf(wy0, s0[f], wy1 * s1[f]);
+        // lane 8 f holds the total of field f
+        const float tot = warp_sum4(acc, lane);
+        if ((lane & 7) == 0 && ENUF_IN(oi, N)) {
+            const int f = lane >> 3;
+            if (f < 3) {
+                if (F) F[3 * (size_t)oi + f] = r.w * cnorm3 * tot;
+            } else if (NF == 4 && phi) {
+                phi[oi] = cnorm3 * tot;
+            }
+        }
+    }
+}
+
+// Interpolation for windows of p = 6 on 16-cell tiles in z-halves, single
+// precision: k_gather_p8's staging with boxes of BX x PY x PZ cells, PY one
+// row more than the window needs (PT) so that planes lie 16 banks apart
+// (mod 32) and rows 24.  Compute: one warp per particle, lane (g, a) takes
+// x offset a (< 6) of the three runs of three planes of RowsP6 and sums each
+// run along z before applying the x and y weights (9 shared loads and FMAs
+// a field; lanes a = 6, 7 read lane 5's cells, a broadcast, with weight 0).
+template <int NF> struct GatherP6 {
+    using B = Box<6, 16, 8>;
+    static constexpr int PY = B::PT + 1;                    // box rows (y)
+    static constexpr int CELLS = B::BX * PY * B::PZ;
+    static constexpr int CP = (CELLS + 31) / 32 * 32;       // field stride in shared memory, 128-byte aligned
+    static constexpr int CAP = 256;                          // particles per work item
+    static constexpr size_t SMEM = (size_t)NF * CP * 4 + CAP * sizeof(f4) + 16;
+    static_assert(B::BX == 24 && (PY * B::BX) % 32 == 16, "rows 24 and planes 16 banks apart");
+};
+
+template <int NF>
+__global__ void __launch_bounds__(512, 2) k_gather_p6(const int4* __restrict__ work, const int* __restrict__ nwork,
+                                                      const f4* __restrict__ rec, const uint32_t* __restrict__ perm,
+                                                      int M, int lnb, WinC<float> wc, float cnorm3,
+                                                      const float* __restrict__ fld,
+                                                      const __grid_constant__ CUtensorMap tmap, float* __restrict__ F,
+                                                      float* __restrict__ phi, int* __restrict__ status, int N)
+{
+    using G6 = GatherP6<NF>;
+    using B = typename G6::B;
+    constexpr int PY = G6::PY, PZ = B::PZ, BX = B::BX, C = G6::CP, XOFF = B::XOFF;
+    extern __shared__ __align__(128) unsigned char smraw_g6[];
+    float* s = reinterpret_cast<float*>(smraw_g6);
+    f4* srec = reinterpret_cast<f4*>(s + NF * C);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(srec + G6::CAP);
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    pdl_wait();
+    if ((int)blockIdx.x >= *nwork) return;  // uniform for the whole CTA
+    const int4 w = work[blockIdx.x];
+    const int n = w.z - w.y;                 // 1..CAP (the scan splits larger units)
+    const int tile = w.x >> 1, z0 = (w.x & 1) * 8;
+    const int nbm = (1 << lnb) - 1;
+    const int tx = tile & nbm, ty = (tile >> lnb) & nbm, tz = tile >> (2 * lnb);
+    const int ox = tx * 16 - B::XA, oy = ty * 16 - 2, oz = tz * 16 + z0 - 2;
+    if (!(ENUF_IN(tz, nbm + 1) && ENUF_IN(n - 1, G6::CAP) && ENUF_IN(w.z - 1, N))) return;  // uniform for the CTA
+    if (!stage_unit_tma<NF, BX, PY, PZ, C>(s, srec, bar, &tmap, rec + w.y, n, ox, oy, oz, M, fld, status)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int a = lane & 7, ax = a < 6 ? a : 5;
+    const RowsP6 rows(lane >> 3);
+    // the lane's three runs: offsets of their first cells from the window's corner
+    const int o0 = rows.b[0] * BX, o1 = (3 * PY + rows.b[1]) * BX, o2 = ((rows.h2 ? 3 * PY : 0) + rows.b[2]) * BX;
+    for (int k = warp; k < n; k += 16) {
+        const uint32_t oi = perm[w.y + k];
+        const f4 r = srec[k];
+        int ix, iy, iz;
+        float dx, dy, dz;
+        split_offset<float, 16>(r.x, ix, dx);
+        split_offset<float, 16>(r.y, iy, dy);
+        split_offset<float, 16>(r.z, iz, dz);
+        iz -= z0;
+        if (!(ENUF_IN(ix, 16) && ENUF_IN(iy, 16) && ENUF_IN(iz, 8))) continue;  // uniform for the warp
+        const float ux = dx + (float)(2 - ax);
+        const float uy0 = dy + (float)(2 - rows.b[0]), uy1 = dy + (float)(2 - rows.b[1]),
+                    uy2 = dy + (float)(2 - rows.b[2]);
+        const float wx = a < 6 ? win_exp(ux * ux, wc) : 0.f;
+        const float wy0 = win_exp(uy0 * uy0, wc), wy1 = win_exp(uy1 * uy1, wc), wy2 = win_exp(uy2 * uy2, wc);
+        float wz[6];
+        window_weights<float, 6>(dz, wc, wz);
+        const float* base = s + (iz * PY + iy) * BX + ix + XOFF + ax;
+        float s0[NF], s1[NF], s2[NF];
+#pragma unroll
+        for (int f = 0; f < NF; f++) s0[f] = s1[f] = s2[f] = 0.f;
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const float z2 = rows.h2 ? wz[3 + j] : wz[j];
+#pragma unroll
+            for (int f = 0; f < NF; f++) {
+                s0[f] = fmaf(wz[j], base[f * C + o0 + j * PY * BX], s0[f]);
+                s1[f] = fmaf(wz[3 + j], base[f * C + o1 + j * PY * BX], s1[f]);
+                s2[f] = fmaf(z2, base[f * C + o2 + j * PY * BX], s2[f]);
+            }
+        }
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int f = 0; f < NF; f++) acc[f] = wx * fmaf(wy0, s0[f], fmaf(wy1, s1[f], wy2 * s2[f]));
         // lane 8 f holds the total of field f
         const float tot = warp_sum4(acc, lane);
         if ((lane & 7) == 0 && ENUF_IN(oi, N)) {
