@@ -329,6 +329,38 @@ __device__ __forceinline__ const V* stage_twiddles(V* dst, const V* __restrict__
     return dst;
 }
 
+// Row of a batch served by row slot r of the x pass of k_iyx (NTX threads
+// a row, RB rows a batch).  A half-warp (the unit of a 64-bit
+// shared-memory access) holds 16 / NTX row slots; within each full block of
+// 16 slots they take rows NTX apart instead of consecutive ones, so that
+// the half-warp's accesses to one kx column of the plane buffer (element kx
+// LD + pidx(y)) fall on 16 distinct bank pairs: LD tx + y mod 16 is distinct
+// for tx < NTX and y = h + NTX i (i < 16 / NTX) whenever LD is odd, where
+// consecutive rows (LD = 1 mod 16 at M = 256) gave only NTX + 1 values.
+// The blocks must start on multiples of 16 rows (pidx pads after every 16),
+// so a batch covers RBU = RB rounded down to whole blocks where that takes
+// no more batches (slots RBU.. then stay idle), else RB rows with the slots
+// past the last full block on their own row.  (Measured: k_iyx 19.8 -> 18.4
+// us at M = 128, 129.0 -> 124.9 us at 256; the same order in the x pass of
+// k_fxy, whose plane accesses are stores, made it slower, 12.5 -> 14.0 us.)
+__device__ __forceinline__ int batch_rows(int RB, int M)
+{
+    const int RBU = RB & ~15;
+    return (RBU > 0 && (M + RBU - 1) / RBU == (M + RB - 1) / RB) ? RBU : RB;
+}
+template <int NTX> __device__ __forceinline__ int batch_row(int r, int RB)
+{
+    static_assert(NTX >= 1 && (NTX & (NTX - 1)) == 0, "a power of two");
+    if constexpr (NTX >= 16) {
+        return r;  // a half-warp serves one row
+    } else {
+        constexpr int Q = 16 / NTX;
+        if (r >= (RB & ~15)) return r;
+        const int s = r & 15;
+        return (r & ~15) + s / Q + NTX * (s % Q);
+    }
+}
+
 // ---------------------------------------------------------------- geometry
 struct FftGeom {
     int nc;    // retained cutoff
@@ -893,9 +925,10 @@ __global__ void __launch_bounds__(IyxBounds<R, M>::T, IyxBounds<R, M>::B) k_iyx(
     // plane and stores its outputs straight to the field row
     V* out = reinterpret_cast<V*>(fld + ((size_t)f * M + z) * M * M);
     const int r0 = threadIdx.x / NTX, tx = threadIdx.x % NTX, r = ENUF_CLAMP(r0, RB);
-    for (int y0 = 0; y0 < M; y0 += RB) {
-        const int y = y0 + r;
-        const bool live = y < M;
+    const int RBU = batch_rows(RB, M), yr = batch_row<NTX>(r, RBU);
+    for (int y0 = 0; y0 < M; y0 += RBU) {
+        const int y = y0 + yr;
+        const bool live = r < RBU && y < M;
         const int yy = live ? y : 0;
         V v[1][EX];
 #pragma unroll

@@ -411,10 +411,12 @@ def test_persistent_interpolation_forces_only(p, monkeypatch):
         assert rel_rms(F, Fk) < 1e-5
 
 
-def test_rpm_1e4_forces_only_full_size():
+@pytest.mark.parametrize("workload", ["rpm_1e4", "rpm"])
+def test_rpm_1e4_forces_only_full_size(workload):
     """The benchmark's call (k-space energy and forces, no potential) on its
-    workload at full size: forces element by element against the oracle."""
-    d = W.rpm_1e4()
+    workload at full size, and on the RPM system's stated p = 6 settings that
+    it times beside it: forces element by element against the oracle."""
+    d = getattr(W, workload)()
     pos, q = W.as_fp32(d["pos"], d["q"])
     parts, F, Wv, _ = run(pos, q, d["L"], d["alpha"], d["r_c"], d["M"], d["p"], d["n_c"], "mixed", phi=False,
                           kspace_only=True)
