@@ -571,8 +571,10 @@ int launch_gather_t(Launcher& L, enuf_plan* pl, int nf, R* F, R* phi)
 }
 
 // Interpolation of the potential grid with the window gradient (forces by
-// analytic differentiation); 512 threads for the 16-cell tiles (the box of
-// one grid lets several CTAs share an SM), 256 for the smaller tiles.
+// analytic differentiation); k_gather_ad_p6 for p = 6 in single precision
+// on 16-cell tiles, else k_gather_ad: 512 threads for the 16-cell
+// tiles (the box of one grid lets several CTAs share an SM), 256 for the
+// smaller tiles.
 template <typename R, int P, int T>
 int launch_gather_ad_t(Launcher& L, enuf_plan* pl, R* F, R* phi)
 {
@@ -589,6 +591,17 @@ int launch_gather_ad_t(Launcher& L, enuf_plan* pl, R* F, R* phi)
                     at<const typename Rec<R>::T>(pl, y.rec), at<const uint32_t>(pl, y.tile_of),
                     at<const uint32_t>(pl, y.perm), r.prm.M, pl->lnb, pl->lnb, winc<R>(pl), cn, fa[0], fa[1], fa[2],
                     at<const R>(pl, y.fld), F, phi);
+    }
+    if constexpr (T == 16 && P == 6 && sizeof(R) == 4) {
+        if (pl->gather_tma) {
+            // p = 6 in single precision: the potential's boxes staged by the
+            // TMA engine, z-accumulated window runs
+            return L.go("gather", k_gather_ad_p6, dim3(r.max_work), dim3(512), GatherP6<1>::SMEM,
+                        at<const int4>(pl, y.work), at<const int>(pl, y.nwork), at<const f4>(pl, y.rec),
+                        at<const uint32_t>(pl, y.perm), r.prm.M, pl->lnb, winc<float>(pl), (float)cn, (float)fa[0],
+                        (float)fa[1], (float)fa[2], at<const float>(pl, y.fld), pl->fld_tmap, (float*)F, (float*)phi,
+                        at<int>(pl, y.status), (int)r.prm.N);
+        }
     }
     using RecT = typename Rec<R>::T;
     constexpr int NTH = T == 16 ? 512 : 256;

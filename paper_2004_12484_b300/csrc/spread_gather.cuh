@@ -913,6 +913,98 @@ __global__ void __launch_bounds__(NTH) k_gather_ad(const int4* __restrict__ work
     }
 }
 
+// The analytic-differentiation interpolation of k_gather_ad for p = 6 on
+// 16-cell tiles in z-halves, single precision: the potential grid's box
+// staged by stage_unit_tma (the geometry of k_gather_p6, field plane 0 of
+// the same tensor map) and the three-plane runs of RowsP6, each summed
+// along z twice, with the z weights and with u_z times them, before the x
+// and y weights are applied.  (The same staging for p = 8, with the rows of
+// k_gather_p8, was slower than k_gather_ad's: 26.0 -> 28.7 us at RPM size.)
+__global__ void __launch_bounds__(512, 2) k_gather_ad_p6(const int4* __restrict__ work, const int* __restrict__ nwork,
+                                                         const f4* __restrict__ rec, const uint32_t* __restrict__ perm,
+                                                         int M, int lnb, WinC<float> wc, float cnorm3, float fa0,
+                                                         float fa1, float fa2, const float* __restrict__ fld,
+                                                         const __grid_constant__ CUtensorMap tmap,
+                                                         float* __restrict__ F, float* __restrict__ phi,
+                                                         int* __restrict__ status, int N)
+{
+    using G = GatherP6<1>;
+    using B = typename G::B;
+    constexpr int PY = G::PY, PZ = B::PZ, BX = B::BX, C = G::CP, XOFF = B::XOFF;
+    extern __shared__ __align__(128) unsigned char smraw_ga[];
+    float* s = reinterpret_cast<float*>(smraw_ga);
+    f4* srec = reinterpret_cast<f4*>(s + C);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(srec + G::CAP);
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    pdl_wait();
+    if ((int)blockIdx.x >= *nwork) return;  // uniform for the whole CTA
+    const int4 w = work[blockIdx.x];
+    const int n = w.z - w.y;                 // 1..CAP (the scan splits larger units)
+    const int tile = w.x >> 1, z0 = (w.x & 1) * 8;
+    const int nbm = (1 << lnb) - 1;
+    const int tx = tile & nbm, ty = (tile >> lnb) & nbm, tz = tile >> (2 * lnb);
+    const int ox = tx * 16 - B::XA, oy = ty * 16 - 2, oz = tz * 16 + z0 - 2;
+    if (!(ENUF_IN(tz, nbm + 1) && ENUF_IN(n - 1, G::CAP) && ENUF_IN(w.z - 1, N))) return;  // uniform for the CTA
+    if (!stage_unit_tma<1, BX, PY, PZ, C>(s, srec, bar, &tmap, rec + w.y, n, ox, oy, oz, M, fld, status)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int a = lane & 7, ax = a < 6 ? a : 5;  // lanes 6, 7 read lane 5's cells with weight 0
+    const RowsP6 rows(lane >> 3);
+    // the lane's three runs: offsets of their first cells from the window's corner
+    const int o0 = rows.b[0] * BX, o1 = (3 * PY + rows.b[1]) * BX, o2 = ((rows.h2 ? 3 * PY : 0) + rows.b[2]) * BX;
+    for (int k = warp; k < n; k += 16) {
+        const uint32_t oi = perm[w.y + k];
+        const f4 r = srec[k];
+        int ix, iy, iz;
+        float dx, dy, dz;
+        split_offset<float, 16>(r.x, ix, dx);
+        split_offset<float, 16>(r.y, iy, dy);
+        split_offset<float, 16>(r.z, iz, dz);
+        iz -= z0;
+        if (!(ENUF_IN(ix, 16) && ENUF_IN(iy, 16) && ENUF_IN(iz, 8))) continue;  // uniform for the warp
+        const float ux = dx + (float)(2 - ax);
+        const float wx = a < 6 ? win_exp(ux * ux, wc) : 0.f;
+        const float* base = s + (iz * PY + iy) * BX + ix + XOFF + ax;
+        float wz[6];
+        window_weights<float, 6>(dz, wc, wz);
+        float sk[3] = {0.f, 0.f, 0.f}, dk[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            // planes j (runs with h = 0) and 3 + j (h = 1); u_z = dz + 2 - c
+            const float z2w = rows.h2 ? wz[3 + j] : wz[j];
+            const float u0 = dz + (float)(2 - j), u1 = dz - (float)(1 + j), u2 = rows.h2 ? u1 : u0;
+            const float v0 = base[o0 + j * PY * BX], v1 = base[o1 + j * PY * BX], v2 = base[o2 + j * PY * BX];
+            sk[0] = fmaf(wz[j], v0, sk[0]);
+            dk[0] = fmaf(wz[j] * u0, v0, dk[0]);
+            sk[1] = fmaf(wz[3 + j], v1, sk[1]);
+            dk[1] = fmaf(wz[3 + j] * u1, v1, dk[1]);
+            sk[2] = fmaf(z2w, v2, sk[2]);
+            dk[2] = fmaf(z2w * u2, v2, dk[2]);
+        }
+        float ss = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            const float uy = dy + (float)(2 - rows.b[q]);
+            const float wy = win_exp(uy * uy, wc);
+            ss = fmaf(wy, sk[q], ss);
+            sy = fmaf(wy * uy, sk[q], sy);
+            sz = fmaf(wy, dk[q], sz);
+        }
+        // (s, g_x, g_y, g_z) partials of this lane; lane 8 f holds total f
+        float acc[4] = {wx * ss, 0.f, wx * sy, wx * sz};
+        acc[1] = ux * acc[0];
+        const float tot = warp_sum4(acc, lane);
+        if ((lane & 7) == 0 && ENUF_IN(oi, N)) {
+            const int f = lane >> 3;
+            if (f == 0) {
+                if (phi) phi[oi] = cnorm3 * tot;
+            } else if (F) {
+                F[3 * (size_t)oi + f - 1] = r.w * (f == 1 ? fa0 : (f == 2 ? fa1 : fa2)) * tot;
+            }
+        }
+    }
+}
+
 // Interpolation without staging, for grids whose field planes stay resident
 // in L2 (the whole set is at most a few tens of MB): one group of G lanes per
 // particle in sorted order, reading each window row of p consecutive cells
