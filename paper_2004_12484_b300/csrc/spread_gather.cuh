@@ -15,8 +15,9 @@
 // aligned rows).  Spreading gives each warp one sub-tile and a private box,
 // updated without atomics and flushed with one global vector atomic per
 // non-zero aligned group of four cells (scalar atomics in double).
-// Interpolation gives each CTA one tile, stages the box of every field with
-// 16-byte loads and then reads only shared memory.  In both, a group of G >=
+// Interpolation gives each CTA one tile (or one z-half of it), stages the
+// box of every field -- by the TMA engine for p = 8 and 6 in single
+// precision, else with 16-byte loads -- and then reads only shared memory.  In both, a group of G >=
 // p lanes serves one particle: lane a takes the x-offset a, so a group reads
 // or writes p consecutive cells of one grid row per step; the partial sums
 // are combined with shuffles.
@@ -302,8 +303,8 @@ __global__ void __launch_bounds__(32) k_spread(const int4* __restrict__ work, co
 #pragma unroll
     for (int k = 0; k < 3; k++) o6[k] = (k == 1 || (k == 2 && rows6.h2) ? 3 * PS : 0) + rows6.b[k] * BX;
     for (int j0 = w.y; j0 < w.z; j0 += 32) {
-        // one record per lane, handed to the warp with shuffles (or, p = 8,
-        // through shared memory)
+        // one record per lane, handed to the warp with shuffles (or, p = 8
+        // and 6, through shared memory)
         RecT mine;
         if (j0 + lane < w.z) mine = rec[j0 + lane];
         else mine.x = mine.y = mine.z = mine.w = R(0);
