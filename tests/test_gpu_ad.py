@@ -149,6 +149,41 @@ def test_ad_rpm_1e4_kspace_full_size():
     check(d["pos"], d["q"], d["L"], d["alpha"], d["r_c"], d["M"], d["p"], d["n_c"], "mixed", kspace_only=True)
 
 
+@pytest.mark.parametrize("workload", ["rpm", "polyelectrolyte"])
+def test_ad_p6_kspace_full_size(workload):
+    """The p = 6 workloads at full size (the RPM electrolyte at its stated
+    settings, N = 65,536, grid 128^3; the polyelectrolyte, N = 1,572,864,
+    grid 256^3), where the variant's interpolation stages its boxes by TMA:
+    reciprocal part element by element against the oracle.
+
+    The window's p points start at the particle's cell, floor(u), and the
+    gradient of the truncated window jumps where u crosses a cell face (the
+    edge point's derivative term enters or leaves).  The library decides the
+    cell from the particle's offset inside its tile, held in single
+    precision; the oracle from u in double.  A particle within that rounding
+    of a face (a few in 10^6) may land on different sides of the jump, and
+    either side is a correct evaluation: such particles are compared only
+    against the size of the jump, every other particle element by element."""
+    d = getattr(W, workload)()
+    pos, q = W.as_fp32(d["pos"], d["q"])
+    L, M = np.asarray(d["L"], dtype=np.float64), d["M"]
+    plan = make_plan(L, len(q), d["alpha"], d["r_c"], M, d["p"], d["n_c"], "mixed")
+    parts, F, Wv, ph = run(plan, pos, q, "mixed", kspace_only=True)
+    Ek, Fk, phik, Wk = O.kspace_nfft_ad(pos, q, L, d["alpha"], M, d["p"], d["n_c"])
+    u = np.mod(pos, L) / (L / M)
+    # within 1e-5 cells of a face (the offsets' rounding is 2^-20 cells);
+    # uniform coordinates put 6e-5 of the particles there
+    face = (np.abs(u - np.rint(u)) < 1e-5).any(axis=1)
+    assert face.sum() <= 2e-4 * len(q)
+    t = TOL["mixed"]
+    assert abs(parts["E"] / Ek - 1) < t["E"]
+    assert rel_rms(F[~face], Fk[~face]) < t["F"]
+    assert rel_rms(ph, phik) < t["phi"]
+    assert np.abs(Wv - Wk).max() < t["W"] * np.abs(Wk).max()
+    fn = np.sqrt((Fk[face] ** 2).sum(axis=1))
+    assert (np.sqrt(((F[face] - Fk[face]) ** 2).sum(axis=1)) < 0.1 * fn + 1e-6).all()
+
+
 def test_ad_forces_are_the_gradient_of_the_device_energy():
     """FP64 plan: a central difference of the library's own reciprocal
     energy reproduces its analytic-differentiation forces (the ik forces of
